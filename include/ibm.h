@@ -1,0 +1,225 @@
+/*
+ * ibm.h -- C ABI of the GB300 ghost-cell immersed-boundary solver library
+ * (libibm.so). Plain C types only: host or device pointers and sizes.
+ *
+ * The library advances the incompressible Navier-Stokes equations in
+ * conservative form (Eq. 1 of the paper) on a non-uniform Cartesian grid
+ * with a sharp-interface ghost-cell immersed body (Section 2.2), by the
+ * fractional-step method (Section 2.1): an Adams-Bashforth-2 convection /
+ * Crank-Nicolson diffusion predictor, a pressure Poisson solve with
+ * ghost-cell-modified boundary rows, and a projection.
+ *
+ * Conventions used by every call below:
+ *   - cells are stored structure-of-arrays with x the unit-stride axis:
+ *     linear index c = i + nx*(j + ny*k); 2D grids have nz = 1;
+ *   - x-face arrays hold (nx+1)*ny*nz values, index i + (nx+1)*(j + ny*k);
+ *     y-face arrays nx*(ny+1)*nz values, index i + nx*(j + (ny+1)*k);
+ *     z-face arrays nx*ny*(nz+1) values, index i + nx*(j + ny*k);
+ *   - cell types are bytes: IBM_FLUID, IBM_GHOST, IBM_DEAD;
+ *   - every call returns an ibm_status; none aborts, traps or exits. A
+ *     per-context message is kept for ibm_last_error();
+ *   - every call enqueues its GPU work on the stream given at creation and
+ *     returns after synchronising that stream, so a device-side error is
+ *     reported by the call that caused it;
+ *   - host arrays passed in are copied before the call returns; device
+ *     pointers passed in are borrowed for the duration of the call only.
+ *   - a context may be used by one host thread at a time.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_ctx ibm_ctx;
+
+typedef enum {
+    IBM_OK = 0,
+    IBM_ERR_ARG = 1,           /* invalid argument (null pointer, size, range) */
+    IBM_ERR_OOM = 2,           /* device or host allocation failed */
+    IBM_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    IBM_ERR_MESH = 4,          /* body mesh not closed/manifold, or degenerate */
+    IBM_ERR_STATE = 5,         /* call order violated (e.g. step before classify) */
+    IBM_ERR_NOT_CONVERGED = 6, /* iteration limit reached before the tolerance */
+    IBM_ERR_DIVERGED = 7,      /* NaN or Inf met in a residual */
+    IBM_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} ibm_status;
+
+enum { IBM_FLUID = 0, IBM_GHOST = 1, IBM_DEAD = 2 };
+
+/* outer boundary conditions, per face in the order x-, x+, y-, y+, z-, z+ */
+enum {
+    IBM_BC_INFLOW = 0,  /* Dirichlet u = u_inf on every component */
+    IBM_BC_OUTFLOW = 1, /* zero normal gradient; outflow face velocities get one
+                           uniform correction so the net boundary flux is zero */
+    IBM_BC_SLIP = 2     /* normal component 0, tangential zero gradient */
+};
+
+/* arithmetic of the Poisson solver's inner multigrid-preconditioned CG */
+enum { IBM_FP64 = 0, IBM_MIXED = 1 };
+
+typedef struct {
+    int ndim;              /* 2 or 3 */
+    int nx, ny, nz;        /* cells per axis, each >= 2 (nz = 1 when ndim == 2) */
+    const double *xf;      /* host, nx+1 increasing face coordinates (copied) */
+    const double *yf;      /* host, ny+1 increasing face coordinates (copied) */
+    const double *zf;      /* host, nz+1 increasing face coordinates; ignored in 2D */
+    double Re;             /* Reynolds number (> 0) */
+    double dt;             /* time step (> 0) */
+    double u_inf[3];       /* inflow velocity */
+    int bc[6];             /* IBM_BC_* per outer face */
+    int precision;         /* IBM_FP64 or IBM_MIXED */
+    void *stream;          /* cudaStream_t to run on (borrowed); NULL = default stream */
+    /* optional device allocator; both NULL = cudaMalloc/cudaFree. The
+       context frees everything it allocated through the same hook. */
+    void *(*alloc)(size_t bytes, void *alloc_ctx);
+    void (*free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+} ibm_grid_desc;
+
+typedef struct {
+    double rtol;        /* Poisson: relative residual ||P(b-A phi)||/||P b|| target */
+    int max_outer;      /* Poisson: FGMRES iteration limit over all restarts */
+    int restart;        /* Poisson: FGMRES restart length (1..32) */
+    int inner_iters;    /* Poisson: MG-PCG iterations per preconditioner call */
+    int nu1, nu2;       /* multigrid pre/post red-black Gauss-Seidel sweeps */
+    int coarse_sweeps;  /* red-black sweep pairs on the coarsest level */
+    double helm_rtol;   /* Crank-Nicolson Helmholtz: relative residual target */
+    int helm_maxit;     /* Helmholtz: sweep limit */
+    double ghost_tol;   /* velocity ghost refresh: max relative change */
+    int ghost_maxit;    /* velocity ghost refresh: Jacobi pass limit */
+    int precision;      /* IBM_FP64 or IBM_MIXED */
+} ibm_solver_opts;
+
+typedef struct {
+    int64_t n_fluid, n_ghost, n_dead;
+    int64_t n_kind[3];  /* ghosts per stencil kind: 0 eight fluid/ghost corners,
+                           1 the ghost itself is a corner (boundary row), 2 fallback */
+} ibm_table_info;
+
+typedef struct {
+    int outer_iters;         /* FGMRES iterations */
+    int inner_iters;         /* MG-PCG iterations summed over preconditioner calls */
+    double rel_residual;     /* final ||P(b - A phi)|| / ||P b||, in FP64 */
+    double lambda_est;       /* not used; 0 */
+    double ms;               /* device time of the solve */
+} ibm_solve_stats;
+
+typedef struct {
+    int steps;               /* steps taken by this call */
+    int poisson_outer;       /* FGMRES iterations, summed over steps */
+    int poisson_inner;       /* MG-PCG iterations, summed */
+    int helm_sweeps;         /* Helmholtz red-black sweeps, summed over components */
+    double rel_residual;     /* Poisson relative residual of the last step */
+    double max_div;          /* max |div U| over FLUID cells after the last projection,
+                                minus its volume-weighted FLUID mean */
+    double ms_total, ms_predictor, ms_poisson, ms_projection;
+} ibm_step_stats;
+
+/* Per-ghost tables, host destinations; any pointer may be NULL (skipped).
+   Sizes: type N; gidx, dist, base, kind, cmask, bv, bp n_ghost;
+   bi, nrm, ip 3*n_ghost; sidx, wv, wp 8*n_ghost (row per ghost). */
+typedef struct {
+    uint8_t *type;
+    int64_t *gidx;
+    double *bi, *nrm, *ip, *dist;
+    int64_t *base;
+    uint8_t *kind, *cmask;
+    int64_t *sidx;
+    double *wv, *wp, *bv, *bp;
+} ibm_tables_host;
+
+/* fields for ibm_get_field / ibm_set_field (element type and count) */
+enum {
+    IBM_FIELD_U = 0, IBM_FIELD_V = 1, IBM_FIELD_W = 2,   /* cell velocity, double, N */
+    IBM_FIELD_P = 3,                                      /* pressure, double, N */
+    IBM_FIELD_FACE_U = 4, IBM_FIELD_FACE_V = 5, IBM_FIELD_FACE_W = 6, /* face velocity, double */
+    IBM_FIELD_NOLD_U = 7, IBM_FIELD_NOLD_V = 8, IBM_FIELD_NOLD_W = 9, /* previous convective term */
+    IBM_FIELD_TYPE = 10,                                  /* uint8, N */
+    IBM_FIELD_USTAR_U = 11, IBM_FIELD_USTAR_V = 12, IBM_FIELD_USTAR_W = 13, /* last predictor */
+    IBM_FIELD_RHS = 14,                                   /* last Poisson right-hand side, N */
+    IBM_FIELD_STEP = 15                                   /* int64 step counter, 1 value */
+};
+
+/* Defaults: rtol 1e-10, max_outer 200, restart 8, inner_iters 2, nu1 = nu2 = 2,
+   coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
+   ghost_maxit 100, precision IBM_FP64. */
+ibm_status ibm_default_opts(ibm_solver_opts *opts);
+
+/* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).
+   Validates the descriptor (IBM_ERR_ARG), copies the face coordinates to
+   the device, allocates every field and solver buffer (IBM_ERR_OOM) and
+   builds the multigrid hierarchy of the grid. *out is NULL on failure. */
+ibm_status ibm_create_grid(const ibm_grid_desc *desc, ibm_ctx **out);
+
+/* Replace solver options (validated: IBM_ERR_ARG). May be called at any time
+   after creation; switching to IBM_MIXED allocates the FP32 buffers. */
+ibm_status ibm_set_opts(ibm_ctx *ctx, const ibm_solver_opts *opts);
+
+/* Add one closed immersed body (Section 2.2: the unstructured surface mesh
+   immersed in the Cartesian grid). verts: host, nv*3 doubles (z ignored in
+   2D). elems: host int32, 3D triangles ne*3 counter-clockwise seen from
+   outside, 2D segments ne*2 counter-clockwise around the body. Both are
+   copied. Several calls add several bodies (their union; they must not
+   overlap). IBM_ERR_MESH if an edge (3D) or vertex (2D) is not shared by
+   exactly two elements in opposite directions, or an index is out of range.
+   Invalidates earlier classification (IBM_ERR_STATE until re-classified). */
+ibm_status ibm_set_body(ibm_ctx *ctx, const double *verts, int64_t nv,
+                        const int32_t *elems, int64_t ne);
+
+/* Classify cells and build the ghost-cell tables (Section 2.2: ray tracing
+   to blank dead cells, ghost = dead cell with a fluid face neighbour, body
+   intercept, image point, the 8 surrounding cells and the weights of Eq. 2
+   from the Vandermonde system of Eq. 3). All on the GPU. Then resets the
+   flow to an impulsive start: u = u_inf on FLUID cells, Dirichlet ghost
+   values, 0 in DEAD cells, face velocities from those, p = 0, step 0.
+   out may be NULL. IBM_ERR_STATE if no body was set. */
+ibm_status ibm_classify_cells(ibm_ctx *ctx, ibm_table_info *out);
+
+/* Advance nsteps fractional steps (Section 2.1): convective term, AB2 + CN
+   right-hand side, CN Helmholtz solve with Dirichlet ghost rows, face
+   velocities and divergence, pressure Poisson solve (FGMRES in FP64
+   around multigrid-preconditioned CG on the staircase operator), projection,
+   velocity ghost refresh. out may be NULL. Returns IBM_ERR_NOT_CONVERGED
+   when a solve hit its iteration limit (the step is still completed),
+   IBM_ERR_DIVERGED on NaN/Inf (state then undefined). */
+ibm_status ibm_step(ibm_ctx *ctx, int nsteps, ibm_step_stats *out);
+
+/* Solve the ghost-cell pressure Poisson system A phi = P b (Section 2.1
+   pressure equation; Section 2.2 Neumann ghost rows) on the classified
+   grid. rhs_dev: device, N doubles; only FLUID rows are read, and their
+   volume-weighted mean is removed (compatibility). phi_dev: device, N
+   doubles; in: initial guess, out: solution with zero volume-weighted mean
+   over FLUID cells (DEAD cells 0). rhs_dev and phi_dev must not overlap.
+   rtol <= 0 or maxit <= 0 take the context options. stats may be NULL. */
+ibm_status ibm_poisson_solve(ibm_ctx *ctx, const double *rhs_dev, double *phi_dev,
+                             double rtol, int maxit, ibm_solve_stats *stats);
+
+/* Copy the classification and ghost tables to host arrays (tests, tools). */
+ibm_status ibm_get_tables(ibm_ctx *ctx, const ibm_tables_host *dst);
+
+/* Copy a field out of / into the context (checkpoint and restart, tests).
+   dst/src: host pointer when is_device == 0, device pointer otherwise;
+   bytes must equal the field's size exactly (IBM_ERR_ARG otherwise). */
+ibm_status ibm_get_field(ibm_ctx *ctx, int field, void *dst, int is_device, size_t bytes);
+ibm_status ibm_set_field(ibm_ctx *ctx, int field, const void *src, int is_device, size_t bytes);
+
+/* Number of N-sized cells and of ghost cells (after classification). */
+ibm_status ibm_sizes(ibm_ctx *ctx, int64_t *n_cells, int64_t *n_ghost);
+
+/* Release every allocation of the context. NULL is accepted. */
+ibm_status ibm_destroy(ibm_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none); ctx NULL gives the
+   message of the last failed ibm_create_grid on this thread. */
+const char *ibm_last_error(ibm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H */

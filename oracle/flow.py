@@ -1,0 +1,467 @@
+"""Oracle discrete operators and one fractional step, numpy + scipy, FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Follows Section 2.1 of the paper: the conservative incompressible
+Navier-Stokes equations (Eq. 1) on a non-uniform Cartesian grid, split by the
+fractional-step (Chorin) method into an advection-diffusion predictor and a
+pressure Poisson equation, central differences in space, Adams-Bashforth
+convection; and Section 2.2 for the ghost-cell rows (Eq. 2, Eq. 3).
+
+Readings where the paper is silent (each listed in the design notes):
+  * collocated cell-centred u, v, w, p plus face-normal velocities U, V, W;
+  * convection AB2 (Euler on the first step), diffusion Crank-Nicolson,
+    non-incremental projection, p^{n+1} = phi;
+  * outer boundaries per face: INFLOW (Dirichlet u = u_inf), OUTFLOW
+    (zero gradient, then one uniform correction of the outflow face
+    velocities so the net boundary flux vanishes), SLIP (normal component
+    0, tangential zero gradient); the pressure is homogeneous Neumann
+    everywhere;
+  * velocity ghost rows (Dirichlet, body at rest):
+        u_G + sum_m wv_m u_m = (2 - bv) u_BI = 0,
+    pressure ghost rows (Neumann, dp/dn = 0):  p_G - sum_m wp_m p_m = 0;
+  * the Poisson system A phi = b is singular (constants); b is made
+    compatible by removing its volume-weighted fluid mean, and the solution
+    is the one with A phi = b - lam * 1_fluid for the scalar lam that makes
+    the system consistent, normalised to zero volume-weighted fluid mean.
+
+Every linear system here is solved by scipy's sparse direct LU: the
+solution is then the plain definition, reached by no iteration.
+
+Array layout: cell arrays are [nz, ny, nx] (x fastest); x-face arrays are
+[nz, ny, nx+1], y-face [nz, ny+1, nx], z-face [nz+1, ny, nx]. In 2D nz = 1,
+there are no z fluxes and only u, v are advanced.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+FLUID, GHOST, DEAD = 0, 1, 2
+INFLOW, OUTFLOW, SLIP = 0, 1, 2
+DEFAULT_BC = (INFLOW, OUTFLOW, SLIP, SLIP, SLIP, SLIP)
+
+
+@dataclass
+class Grid:
+    ndim: int
+    xf: np.ndarray
+    yf: np.ndarray
+    zf: np.ndarray
+
+    def __post_init__(self):
+        self.xf = np.asarray(self.xf, dtype=np.float64)
+        self.yf = np.asarray(self.yf, dtype=np.float64)
+        self.zf = np.asarray(self.zf, dtype=np.float64)
+        if self.ndim == 2:
+            self.zf = np.array([0.0, 1.0])
+        self.nx, self.ny, self.nz = len(self.xf) - 1, len(self.yf) - 1, len(self.zf) - 1
+        self.shape = (self.nz, self.ny, self.nx)
+        self.N = self.nx * self.ny * self.nz
+        f = (self.xf, self.yf, self.zf)
+        self.h = [np.diff(a) for a in f]                      # cell widths
+        self.c = [0.5 * (a[:-1] + a[1:]) for a in f]          # centres
+        self.hc = [np.diff(c) for c in self.c]                # centre spacing
+        dx, dy, dz = (a for a in self.h)
+        self.vol = dz[:, None, None] * dy[None, :, None] * dx[None, None, :]
+        # face areas broadcast to the face arrays
+        self.area = [np.broadcast_to(dz[:, None, None] * dy[None, :, None], (self.nz, self.ny, 1)),
+                     np.broadcast_to(dz[:, None, None] * dx[None, None, :], (self.nz, 1, self.nx)),
+                     np.broadcast_to(dy[None, :, None] * dx[None, None, :], (1, self.ny, self.nx))]
+
+    @property
+    def ncomp(self):
+        return self.ndim
+
+    def bshape(self, axis):
+        """shape that broadcasts a 1D array along `axis` (0=x, 1=y, 2=z)."""
+        return [(1, 1, -1), (1, -1, 1), (-1, 1, 1)][axis]
+
+    def face_shape(self, axis):
+        s = list(self.shape)
+        s[2 - axis] += 1
+        return tuple(s)
+
+
+def _sl(axis, lo, hi):
+    """slice object over cell array axis `axis` (0=x ... 2=z)."""
+    s = [slice(None)] * 3
+    s[2 - axis] = slice(lo, hi)
+    return tuple(s)
+
+
+def axes(g: Grid):
+    return range(g.ndim)
+
+
+# ---------------------------------------------------------------------------
+# Boundary data
+# ---------------------------------------------------------------------------
+
+def bc_dirichlet(bc, axis, side, comp, u_inf):
+    """(is_dirichlet, value) of component `comp` on the outer face (axis, side)."""
+    code = bc[2 * axis + side]
+    if code == INFLOW:
+        return True, float(u_inf[comp])
+    if code == SLIP and comp == axis:
+        return True, 0.0
+    return False, 0.0
+
+
+# ---------------------------------------------------------------------------
+# Face velocities, divergence, convective and viscous terms
+# ---------------------------------------------------------------------------
+
+def face_velocity(g: Grid, typ, u, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
+    """Face-normal velocities from cell-centred ones (step P4 of the
+    predictor): interior faces with a FLUID side and no DEAD side take the
+    mean of the two neighbours, other interior faces 0; INFLOW faces u_inf,
+    SLIP faces 0, OUTFLOW faces the adjacent FLUID cell value, after which
+    every OUTFLOW face over a FLUID cell gets one uniform correction making
+    the net outer-boundary flux zero."""
+    F = []
+    for a in axes(g):
+        Ua = np.zeros(g.face_shape(a))
+        L, R = typ[_sl(a, 0, -1)], typ[_sl(a, 1, None)]
+        uL, uR = u[a][_sl(a, 0, -1)], u[a][_sl(a, 1, None)]
+        ok = (L != DEAD) & (R != DEAD) & ((L == FLUID) | (R == FLUID))
+        Ua[_sl(a, 1, -1)] = np.where(ok, 0.5 * (uL + uR), 0.0)
+        F.append(Ua)
+    # outer faces
+    net = 0.0
+    out_area = 0.0
+    for a in axes(g):
+        A = np.broadcast_to(g.area[a], g.face_shape(a))
+        for side in (0, 1):
+            fs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a], None)
+            cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+            code = bc[2 * a + side]
+            if code == INFLOW:
+                F[a][fs] = u_inf[a]
+            elif code == SLIP:
+                F[a][fs] = 0.0
+            else:
+                F[a][fs] = np.where(typ[cs] == FLUID, u[a][cs], 0.0)
+                out_area += float(np.sum(np.where(typ[cs] == FLUID, A[fs], 0.0)))
+            sign = 1.0 if side == 0 else -1.0
+            net += sign * float(np.sum(A[fs] * F[a][fs]))
+    if out_area > 0.0:
+        corr = net / out_area
+        for a in axes(g):
+            for side in (0, 1):
+                if bc[2 * a + side] != OUTFLOW:
+                    continue
+                fs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a], None)
+                cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+                sign = -1.0 if side == 0 else 1.0
+                F[a][fs] = np.where(typ[cs] == FLUID, F[a][fs] + sign * corr, F[a][fs])
+    return F
+
+
+def divergence(g: Grid, F):
+    """(1/vol) * sum over faces of the outward flux A_f * U_f."""
+    d = np.zeros(g.shape)
+    for a in axes(g):
+        A = g.area[a]
+        d += A * (F[a][_sl(a, 1, None)] - F[a][_sl(a, 0, -1)])
+    return d / g.vol
+
+
+def convection(g: Grid, typ, u, F, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
+    """Conservative central convective term of Eq. 1 on FLUID cells:
+    N_c = (1/vol) sum_faces (+-) A_f U_f ubar_f, ubar_f the mean of the two
+    neighbouring centres (ghost values included); outer faces use the
+    Dirichlet value or the cell's own value (zero gradient)."""
+    out = []
+    for comp in range(g.ncomp):
+        flux_div = np.zeros(g.shape)
+        for a in axes(g):
+            fv = np.zeros(g.face_shape(a))
+            fv[_sl(a, 1, -1)] = 0.5 * (u[comp][_sl(a, 0, -1)] + u[comp][_sl(a, 1, None)])
+            for side in (0, 1):
+                fs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a], None)
+                cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+                isd, val = bc_dirichlet(bc, a, side, comp, u_inf)
+                fv[fs] = val if isd else u[comp][cs]
+            flx = g.area[a] * F[a] * fv
+            flux_div += flx[_sl(a, 1, None)] - flx[_sl(a, 0, -1)]
+        out.append(np.where(typ == FLUID, flux_div / g.vol, 0.0))
+    return out
+
+
+def laplacian(g: Grid, typ, u, comp, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
+    """Viscous operator on FLUID cells (boundary values included):
+    (1/vol) [ sum_interior A (u_nb - u_c)/hc + sum_Dirichlet A (ub - u_c)/(h/2) ]."""
+    acc = np.zeros(g.shape)
+    uc = u
+    for a in axes(g):
+        A = g.area[a]
+        hc = g.hc[a].reshape(g.bshape(a))
+        flx = A * (uc[_sl(a, 1, None)] - uc[_sl(a, 0, -1)]) / hc  # interior face gradients
+        acc[_sl(a, 0, -1)] += flx
+        acc[_sl(a, 1, None)] -= flx
+        for side in (0, 1):
+            isd, val = bc_dirichlet(bc, a, side, comp, u_inf)
+            if not isd:
+                continue
+            cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+            hh = 0.5 * g.h[a][0 if side == 0 else -1]
+            acc[cs] += A * (val - uc[cs]) / hh
+    return np.where(typ == FLUID, acc / g.vol, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Sparse matrices (rows over all N cells, linear index i + nx (j + ny k))
+# ---------------------------------------------------------------------------
+
+def _lin(g: Grid):
+    return np.arange(g.N).reshape(g.shape)
+
+
+def _face_pairs(g: Grid, a):
+    ids = _lin(g)
+    return ids[_sl(a, 0, -1)].ravel(), ids[_sl(a, 1, None)].ravel()
+
+
+def poisson_matrix(g: Grid, typ, tabs):
+    """Full pressure operator A (Section 2.2 rows included):
+    FLUID rows  (1/vol) sum_faces (A/hc)(phi_nb - phi_c), outer faces zero flux;
+    GHOST rows  phi_G - sum_m wp_m phi_m  (Neumann, dp/dn = 0);
+    DEAD rows   identity."""
+    t = typ.ravel()
+    vol = g.vol.ravel()
+    rows, cols, vals = [], [], []
+    for a in axes(g):
+        L, R = _face_pairs(g, a)
+        T = (np.broadcast_to(g.area[a], g.face_shape(a))[_sl(a, 1, -1)]
+             / g.hc[a].reshape(g.bshape(a))).ravel()
+        for c, nb in ((L, R), (R, L)):
+            m = t[c] == FLUID
+            rows += [c[m], c[m]]
+            cols += [nb[m], c[m]]
+            vals += [T[m] / vol[c[m]], -T[m] / vol[c[m]]]
+    gi = tabs["gidx"]
+    rows += [gi, np.repeat(gi, 8)]
+    cols += [gi, tabs["sidx"].ravel()]
+    vals += [np.ones(gi.size), -tabs["wp"].ravel()]
+    dead = np.nonzero(t == DEAD)[0]
+    rows.append(dead)
+    cols.append(dead)
+    vals.append(np.ones(dead.size))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(g.N, g.N))
+
+
+def helmholtz_matrix(g: Grid, typ, tabs, comp, alpha, bc=DEFAULT_BC):
+    """Crank-Nicolson velocity operator (I - alpha L0) on FLUID rows (L0 the
+    viscous operator without its boundary values), Dirichlet ghost rows
+    u_G + sum_m wv_m u_m, identity DEAD rows."""
+    t = typ.ravel()
+    vol = g.vol.ravel()
+    diag = np.ones(g.N)
+    rows, cols, vals = [], [], []
+    for a in axes(g):
+        L, R = _face_pairs(g, a)
+        T = (np.broadcast_to(g.area[a], g.face_shape(a))[_sl(a, 1, -1)]
+             / g.hc[a].reshape(g.bshape(a))).ravel()
+        for c, nb in ((L, R), (R, L)):
+            m = t[c] == FLUID
+            rows.append(c[m])
+            cols.append(nb[m])
+            vals.append(-alpha * T[m] / vol[c[m]])
+            np.add.at(diag, c[m], alpha * T[m] / vol[c[m]])
+        for side in (0, 1):
+            isd, _ = bc_dirichlet(bc, a, side, comp, (0.0, 0.0, 0.0))
+            if not isd:
+                continue
+            cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+            ids = _lin(g)[cs].ravel()
+            A = np.broadcast_to(g.area[a], g.face_shape(a))[_sl(a, 0, 1)].ravel()
+            hh = 0.5 * g.h[a][0 if side == 0 else -1]
+            m = t[ids] == FLUID
+            np.add.at(diag, ids[m], alpha * A[m] / (hh * vol[ids[m]]))
+    gi = tabs["gidx"]
+    rows += [np.repeat(gi, 8)]
+    cols += [tabs["sidx"].ravel()]
+    vals += [tabs["wv"].ravel()]
+    rows.append(np.arange(g.N))
+    cols.append(np.arange(g.N))
+    vals.append(diag)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(g.N, g.N))
+
+
+def bc_source(g: Grid, typ, comp, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
+    """The boundary-value part of the viscous operator: L u = L0 u + bc_source."""
+    acc = np.zeros(g.shape)
+    for a in axes(g):
+        A = g.area[a]
+        for side in (0, 1):
+            isd, val = bc_dirichlet(bc, a, side, comp, u_inf)
+            if not isd:
+                continue
+            cs = _sl(a, 0, 1) if side == 0 else _sl(a, g.shape[2 - a] - 1, None)
+            hh = 0.5 * g.h[a][0 if side == 0 else -1]
+            acc[cs] += A * val / hh
+    return np.where(typ == FLUID, acc / g.vol, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Poisson: compatibility, residual, direct solve
+# ---------------------------------------------------------------------------
+
+def fluid_mean(g: Grid, typ, x):
+    m = typ == FLUID
+    return float(np.sum(np.where(m, g.vol * x, 0.0)) / np.sum(np.where(m, g.vol, 0.0)))
+
+
+def project_rhs(g: Grid, typ, b):
+    """Remove the volume-weighted FLUID mean on FLUID rows; zero elsewhere."""
+    return np.where(typ == FLUID, b - fluid_mean(g, typ, b), 0.0)
+
+
+def poisson_residual(g: Grid, typ, A, b, phi):
+    """P(b - A phi): FLUID rows lose their volume-weighted mean; GHOST rows
+    as they are; DEAD rows 0. Returns (residual field, relative 2-norm)."""
+    r = (b.ravel() - A @ phi.ravel()).reshape(g.shape)
+    rf = np.where(typ == FLUID, r - fluid_mean(g, typ, r), 0.0)
+    r = np.where(typ == GHOST, r, rf)
+    bn = np.linalg.norm(np.where(typ == DEAD, 0.0, b))
+    return r, (np.linalg.norm(r) / bn if bn > 0 else 0.0)
+
+
+def normalise(g: Grid, typ, phi):
+    """Shift FLUID and GHOST values to zero volume-weighted FLUID mean."""
+    return np.where(typ == DEAD, 0.0, phi - fluid_mean(g, typ, phi))
+
+
+def solve_poisson(g: Grid, typ, tabs, b, A=None, cache=None):
+    """Solve A phi + lam 1_FLUID = b with sum_FLUID vol phi = 0 (bordered
+    system, sparse LU). Returns (phi [nz,ny,nx], lam). `cache` (a dict) keeps
+    the factorisation of the bordered matrix between calls on one grid."""
+    t = typ.ravel()
+    lu = None if cache is None else cache.get("poisson")
+    if lu is None:
+        if A is None:
+            A = poisson_matrix(g, typ, tabs)
+        f = (t == FLUID).astype(np.float64)
+        w = np.where(t == FLUID, g.vol.ravel(), 0.0)
+        w = w / w.sum()
+        K = sp.bmat([[A, sp.csr_matrix(f[:, None])], [sp.csr_matrix(w[None, :]), None]], format="csc")
+        lu = spla.splu(K)
+        if cache is not None:
+            cache["poisson"] = lu
+    rhs = np.concatenate([np.where(t == DEAD, 0.0, b.ravel()), [0.0]])
+    x = lu.solve(rhs)
+    return x[:-1].reshape(g.shape), float(x[-1])
+
+
+# ---------------------------------------------------------------------------
+# Ghost refresh and state
+# ---------------------------------------------------------------------------
+
+def refresh_velocity_ghosts(g: Grid, typ, tabs, u, u_bi=0.0):
+    """Solve the Dirichlet ghost rows for the ghost values with the FLUID
+    values fixed: u_G + sum_m wv_m u_m = (2 - bv) u_BI."""
+    gi = tabs["gidx"]
+    if gi.size == 0:
+        return u
+    pos = -np.ones(g.N, dtype=np.int64)
+    pos[gi] = np.arange(gi.size)
+    out = []
+    for c in u:
+        flat = c.ravel().copy()
+        sidx, wv = tabs["sidx"], tabs["wv"]
+        isg = pos[sidx] >= 0
+        rhs = (2.0 - tabs["bv"]) * u_bi - np.sum(np.where(isg, 0.0, wv * flat[sidx]), axis=1)
+        r, cc = np.nonzero(isg & (wv != 0.0))
+        G = sp.csr_matrix((wv[r, cc], (r, pos[sidx[r, cc]])), shape=(gi.size, gi.size)) + sp.identity(gi.size)
+        flat[gi] = spla.spsolve(G.tocsc(), rhs)
+        out.append(flat.reshape(g.shape))
+    return out
+
+
+@dataclass
+class State:
+    u: list           # ncomp cell arrays
+    F: list           # ndim face arrays
+    p: np.ndarray
+    Nold: list | None
+    nstep: int = 0
+
+
+def initial_state(g: Grid, typ, tabs, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
+    """Impulsive start: u = u_inf on FLUID, Dirichlet ghost values, 0 in
+    DEAD; faces from those cell values; p = 0."""
+    u = [np.where(typ == FLUID, float(u_inf[c]), 0.0) for c in range(g.ncomp)]
+    u = refresh_velocity_ghosts(g, typ, tabs, u)
+    F = face_velocity(g, typ, u, bc, u_inf)
+    return State(u, F, np.zeros(g.shape), None, 0)
+
+
+def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0),
+         A=None, keep=False, cache=None):
+    """One fractional step (rows P1-P4, S, C1). Returns the new State; with
+    keep=True also a dict of the intermediate fields. `cache` (a dict)
+    keeps matrix factorisations between steps of one run."""
+    alpha = dt / (2.0 * Re)
+    N = convection(g, typ, st.u, st.F, bc, u_inf)
+    Nold = N if st.Nold is None else st.Nold
+    ustar = []
+    rhs_all = []
+    for c in range(g.ncomp):
+        Lu = laplacian(g, typ, st.u[c], c, bc, u_inf)
+        rhs = st.u[c] - dt * (1.5 * N[c] - 0.5 * Nold[c]) + alpha * Lu + alpha * bc_source(g, typ, c, bc, u_inf)
+        rhs = np.where(typ == FLUID, rhs, 0.0)
+        lu = None if cache is None else cache.get(("helm", c, alpha))
+        if lu is None:
+            lu = spla.splu(helmholtz_matrix(g, typ, tabs, c, alpha, bc).tocsc())
+            if cache is not None:
+                cache[("helm", c, alpha)] = lu
+        x = lu.solve(rhs.ravel()).reshape(g.shape)
+        ustar.append(x)
+        rhs_all.append(rhs)
+    Fs = face_velocity(g, typ, ustar, bc, u_inf)
+    braw = np.where(typ == FLUID, divergence(g, Fs) / dt, 0.0)
+    b = project_rhs(g, typ, braw)
+    if A is None:
+        A = poisson_matrix(g, typ, tabs)
+    phi, lam = solve_poisson(g, typ, tabs, b, A, cache)
+    Fn, un = project(g, typ, ustar, Fs, phi, dt)
+    un = refresh_velocity_ghosts(g, typ, tabs, un)
+    new = State(un, Fn, phi, N, st.nstep + 1)
+    if keep:
+        return new, dict(N=N, rhs=rhs_all, ustar=ustar, Fstar=Fs, braw=braw, b=b, phi=phi, lam=lam)
+    return new
+
+
+def project(g: Grid, typ, ustar, Fs, phi, dt):
+    """Projection (row C1): faces with a FLUID side lose dt * dphi/dn; FLUID
+    cells lose dt times the mean of their two face gradients per axis (outer
+    faces have zero gradient)."""
+    Fn = [f.copy() for f in Fs]
+    un = [c.copy() for c in ustar]
+    for a in axes(g):
+        hc = g.hc[a].reshape(g.bshape(a))
+        grad = (phi[_sl(a, 1, None)] - phi[_sl(a, 0, -1)]) / hc
+        L, R = typ[_sl(a, 0, -1)], typ[_sl(a, 1, None)]
+        m = (L == FLUID) | (R == FLUID)
+        Fn[a][_sl(a, 1, -1)] = np.where(m, Fs[a][_sl(a, 1, -1)] - dt * grad, Fs[a][_sl(a, 1, -1)])
+        gf = np.zeros(g.face_shape(a))
+        gf[_sl(a, 1, -1)] = grad
+        gc = 0.5 * (gf[_sl(a, 0, -1)] + gf[_sl(a, 1, None)])
+        un[a] = np.where(typ == FLUID, un[a] - dt * gc, un[a])
+    return Fn, un
+
+
+def run(g: Grid, typ, tabs, nsteps, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0), st=None):
+    if st is None:
+        st = initial_state(g, typ, tabs, bc, u_inf)
+    A = poisson_matrix(g, typ, tabs)
+    cache = {}
+    for _ in range(nsteps):
+        st = step(g, typ, tabs, st, Re, dt, bc, u_inf, A, cache=cache)
+    return st
