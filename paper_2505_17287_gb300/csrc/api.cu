@@ -1,0 +1,515 @@
+// C ABI of libibm.so (declared in include/ibm.h): context lifetime, argument
+// validation, host<->device copies and the call order of the solver phases.
+#include "ctx.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <utility>
+
+using namespace ibm;
+
+struct ibm_ctx : public Ctx {};
+
+static thread_local std::string g_create_error;
+
+namespace ibm {
+
+void *dev_alloc(Ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->desc.alloc) {
+        p = c->desc.alloc(bytes, c->desc.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dev_free(Ctx *c, void *p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it == c->allocs.end()) return;
+    c->allocs.erase(it);
+    if (c->desc.free) c->desc.free(p, c->desc.alloc_ctx);
+    else cudaFree(p);
+}
+
+}  // namespace ibm
+
+static void release_all(Ctx *c) {
+    if (c->s) cudaStreamSynchronize(c->s);
+    std::vector<void *> a = c->allocs;
+    for (void *p : a) dev_free(c, p);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    cudaEvent_t ev[4] = {c->ev0, c->ev1, c->ev2, c->ev3};
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+}
+
+extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
+    if (!o) return IBM_ERR_ARG;
+    o->rtol = 1e-10;
+    o->max_outer = 200;
+    o->restart = 8;
+    o->inner_iters = 2;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->coarse_sweeps = 32;
+    o->helm_rtol = 1e-12;
+    o->helm_maxit = 500;
+    o->ghost_tol = 1e-15;
+    o->ghost_maxit = 100;
+    o->precision = IBM_FP64;
+    return IBM_OK;
+}
+
+static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
+    if (!(o->rtol > 0.0 && o->rtol < 1.0)) { why = "rtol must be in (0, 1)"; return false; }
+    if (o->max_outer < 1) { why = "max_outer must be >= 1"; return false; }
+    if (o->restart < 1 || o->restart > 16) { why = "restart must be in [1, 16]"; return false; }
+    if (o->inner_iters < 1 || o->inner_iters > 64) { why = "inner_iters must be in [1, 64]"; return false; }
+    if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 != o->nu2) { why = "nu1 = nu2 >= 1 is required (symmetric V-cycle)"; return false; }
+    if (o->coarse_sweeps < 1) { why = "coarse_sweeps must be >= 1"; return false; }
+    if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1) { why = "bad Helmholtz tolerance or limit"; return false; }
+    if (!(o->ghost_tol > 0.0) || o->ghost_maxit < 1) { why = "bad ghost refresh tolerance or limit"; return false; }
+    if (o->precision != IBM_FP64 && o->precision != IBM_MIXED) { why = "precision must be IBM_FP64 or IBM_MIXED"; return false; }
+    return true;
+}
+
+static ibm_status alloc_krylov(Ctx *c, int m) {
+    if (m <= c->m_cap) return IBM_OK;
+    for (double *p : c->V) dev_free(c, p);
+    for (double *p : c->Z) dev_free(c, p);
+    c->V.assign(m + 1, nullptr);
+    c->Z.assign(m, nullptr);
+    for (int i = 0; i <= m; ++i)
+        if (!(c->V[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "FGMRES basis allocation failed");
+    for (int i = 0; i < m; ++i)
+        if (!(c->Z[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "FGMRES basis allocation failed");
+    if (!c->Vdev) c->Vdev = (double **)dev_alloc(c, sizeof(double *) * 17);
+    if (!c->Zdev) c->Zdev = (double **)dev_alloc(c, sizeof(double *) * 17);
+    if (!c->Vdev || !c->Zdev) return c->fail(IBM_ERR_OOM, "pointer table allocation failed");
+    IBM_CUDA(c, cudaMemcpyAsync(c->Vdev, c->V.data(), sizeof(double *) * (m + 1), cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaMemcpyAsync(c->Zdev, c->Z.data(), sizeof(double *) * m, cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    c->m_cap = m;
+    return IBM_OK;
+}
+
+static double *upload(Ctx *c, const std::vector<double> &h) {
+    double *d = (double *)dev_alloc(c, sizeof(double) * (h.size() ? h.size() : 1));
+    if (d && h.size()) cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->s);
+    return d;
+}
+
+static void axis_arrays(const std::vector<double> &f, std::vector<double> &cc, std::vector<double> &w,
+                        std::vector<double> &h) {
+    const size_t n = f.size() - 1;
+    cc.resize(n);
+    w.resize(n);
+    h.assign(n + 1, 0.0);
+    for (size_t i = 0; i < n; ++i) {
+        cc[i] = 0.5 * (f[i] + f[i + 1]);
+        w[i] = f[i + 1] - f[i];
+    }
+    for (size_t i = 1; i < n; ++i) h[i] = cc[i] - cc[i - 1];
+}
+
+static ibm_status build_levels(Ctx *c) {
+    c->lg.clear();
+    LevelGeom L0{c->nx, c->ny, c->nz, 1, 1, 1, c->hxf, c->hyf, c->hzf};
+    c->lg.push_back(L0);
+    while ((int)c->lg.size() < 24) {
+        const LevelGeom &L = c->lg.back();
+        const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+        if (n <= 64 || (L.nx <= 2 && L.ny <= 2 && L.nz <= 2)) break;
+        LevelGeom C;
+        C.fx = L.nx > 2 ? 2 : 1;
+        C.fy = L.ny > 2 ? 2 : 1;
+        C.fz = L.nz > 2 ? 2 : 1;
+        C.nx = (L.nx + C.fx - 1) / C.fx;
+        C.ny = (L.ny + C.fy - 1) / C.fy;
+        C.nz = (L.nz + C.fz - 1) / C.fz;
+        auto coarsen = [](const std::vector<double> &f, int nfine, int fac, int ncoarse) {
+            if (fac == 1) return f;
+            std::vector<double> o(ncoarse + 1);
+            for (int k = 0; k < ncoarse; ++k) o[k] = f[2 * k];
+            o[ncoarse] = f[nfine];
+            return o;
+        };
+        C.xf = coarsen(L.xf, L.nx, C.fx, C.nx);
+        C.yf = coarsen(L.yf, L.ny, C.fy, C.ny);
+        C.zf = coarsen(L.zf, L.nz, C.fz, C.nz);
+        c->lg.push_back(C);
+    }
+    for (auto &L : c->lg) {
+        std::vector<double> cc, w, h;
+        axis_arrays(L.xf, cc, w, h);
+        c->lhx.push_back(upload(c, h));
+        axis_arrays(L.yf, cc, w, h);
+        c->lhy.push_back(upload(c, h));
+        axis_arrays(L.zf, cc, w, h);
+        c->lhz.push_back(upload(c, h));
+        if (!c->lhx.back() || !c->lhy.back() || !c->lhz.back()) return c->fail(IBM_ERR_OOM, "level geometry allocation failed");
+    }
+    return IBM_OK;
+}
+
+static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
+    c->desc = *d;
+    c->desc.xf = c->desc.yf = c->desc.zf = nullptr;
+    c->s = (cudaStream_t)d->stream;
+    ibm_default_opts(&c->opts);
+    c->opts.precision = d->precision;
+    c->ndim = d->ndim;
+    c->nx = d->nx;
+    c->ny = d->ny;
+    c->nz = d->ndim == 2 ? 1 : d->nz;
+    c->N = (int64_t)c->nx * c->ny * c->nz;
+    c->NFx = (int64_t)(c->nx + 1) * c->ny * c->nz;
+    c->NFy = (int64_t)c->nx * (c->ny + 1) * c->nz;
+    c->NFz = (int64_t)c->nx * c->ny * (c->nz + 1);
+    c->hxf.assign(d->xf, d->xf + c->nx + 1);
+    c->hyf.assign(d->yf, d->yf + c->ny + 1);
+    if (c->ndim == 3) c->hzf.assign(d->zf, d->zf + c->nz + 1);
+    else c->hzf = {0.0, 1.0};
+    axis_arrays(c->hxf, c->hxc, c->hdx, c->hhx);
+    axis_arrays(c->hyf, c->hyc, c->hdy, c->hhy);
+    axis_arrays(c->hzf, c->hzc, c->hdz, c->hhz);
+    IBM_CUDA(c, cudaEventCreate(&c->ev0));
+    IBM_CUDA(c, cudaEventCreate(&c->ev1));
+    IBM_CUDA(c, cudaEventCreate(&c->ev2));
+    IBM_CUDA(c, cudaEventCreate(&c->ev3));
+    IBM_CUDA(c, cudaMallocHost((void **)&c->hscal, sizeof(double) * 64));
+    c->xf = upload(c, c->hxf); c->yf = upload(c, c->hyf); c->zf = upload(c, c->hzf);
+    c->xc = upload(c, c->hxc); c->yc = upload(c, c->hyc); c->zc = upload(c, c->hzc);
+    c->dx = upload(c, c->hdx); c->dy = upload(c, c->hdy); c->dz = upload(c, c->hdz);
+    c->hx = upload(c, c->hhx); c->hy = upload(c, c->hhy); c->hz = upload(c, c->hhz);
+    if (!c->xf || !c->yf || !c->zf || !c->xc || !c->yc || !c->zc || !c->dx || !c->dy || !c->dz || !c->hx || !c->hy || !c->hz)
+        return c->fail(IBM_ERR_OOM, "grid allocation failed");
+    c->g = GridDev{c->nx, c->ny, c->nz, c->ndim, c->N, c->xf, c->yf, c->zf, c->xc, c->yc, c->zc,
+                   c->dx, c->dy, c->dz, c->hx, c->hy, c->hz};
+    const size_t nb = sizeof(double) * c->N;
+    c->type = (uint8_t *)dev_alloc(c, c->N);
+    c->inside = (uint8_t *)dev_alloc(c, c->N);
+    if (!c->type || !c->inside) return c->fail(IBM_ERR_OOM, "cell arrays allocation failed");
+    const int64_t nf[3] = {c->NFx, c->NFy, c->NFz};
+    for (int q = 0; q < 3; ++q) {
+        const bool used = q < c->ndim;
+        const size_t cb = used ? nb : 8;
+        c->u[q] = (double *)dev_alloc(c, cb);
+        c->Nold[q] = (double *)dev_alloc(c, cb);
+        c->Nnew[q] = (double *)dev_alloc(c, cb);
+        c->ustar[q] = (double *)dev_alloc(c, cb);
+        c->rhs[q] = (double *)dev_alloc(c, q < 2 ? nb : cb);
+        c->F[q] = (double *)dev_alloc(c, used ? sizeof(double) * nf[q] : 8);
+        if (!c->u[q] || !c->Nold[q] || !c->Nnew[q] || !c->ustar[q] || !c->rhs[q] || !c->F[q])
+            return c->fail(IBM_ERR_OOM, "flow field allocation failed");
+    }
+    c->p = (double *)dev_alloc(c, nb);
+    c->b = (double *)dev_alloc(c, nb);
+    c->w = (double *)dev_alloc(c, nb);
+    c->rr = (double *)dev_alloc(c, nb);
+    c->part = (double *)dev_alloc(c, sizeof(double) * RED_BLOCKS * 40);
+    c->scal = (double *)dev_alloc(c, sizeof(double) * 64);
+    if (!c->p || !c->b || !c->w || !c->rr || !c->part || !c->scal) return c->fail(IBM_ERR_OOM, "solver vector allocation failed");
+    IBM_CUDA(c, cudaMemsetAsync(c->p, 0, nb, c->s));
+    IBM_CUDA(c, cudaMemsetAsync(c->scal, 0, sizeof(double) * 64, c->s));
+    IBM_TRY(alloc_krylov(c, c->opts.restart));
+    IBM_TRY(build_levels(c));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
+static bool increasing(const double *f, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!(f[i + 1] > f[i]) || !isfinite(f[i]) || !isfinite(f[i + 1])) return false;
+    return true;
+}
+
+extern "C" ibm_status ibm_create_grid(const ibm_grid_desc *d, ibm_ctx **out) {
+    if (!out) { g_create_error = "out is NULL"; return IBM_ERR_ARG; }
+    *out = nullptr;
+    if (!d) { g_create_error = "descriptor is NULL"; return IBM_ERR_ARG; }
+    if (d->ndim != 2 && d->ndim != 3) { g_create_error = "ndim must be 2 or 3"; return IBM_ERR_ARG; }
+    if (d->nx < 2 || d->ny < 2 || (d->ndim == 3 && d->nz < 2) || (d->ndim == 2 && d->nz != 1)) {
+        g_create_error = "cell counts must be >= 2 (nz = 1 in 2D)";
+        return IBM_ERR_ARG;
+    }
+    if (!d->xf || !d->yf || (d->ndim == 3 && !d->zf)) { g_create_error = "face coordinates are NULL"; return IBM_ERR_ARG; }
+    if (!increasing(d->xf, d->nx) || !increasing(d->yf, d->ny) || (d->ndim == 3 && !increasing(d->zf, d->nz))) {
+        g_create_error = "face coordinates must be finite and strictly increasing";
+        return IBM_ERR_ARG;
+    }
+    if (!(d->Re > 0.0) || !(d->dt > 0.0)) { g_create_error = "Re and dt must be positive"; return IBM_ERR_ARG; }
+    for (int f = 0; f < 6; ++f)
+        if (d->bc[f] < IBM_BC_INFLOW || d->bc[f] > IBM_BC_SLIP) { g_create_error = "unknown boundary code"; return IBM_ERR_ARG; }
+    if (d->precision != IBM_FP64 && d->precision != IBM_MIXED) { g_create_error = "bad precision"; return IBM_ERR_ARG; }
+    if ((d->alloc == nullptr) != (d->free == nullptr)) { g_create_error = "alloc and free hooks must be given together"; return IBM_ERR_ARG; }
+    const double ncell = (double)d->nx * d->ny * (d->ndim == 3 ? d->nz : 1);
+    if (ncell > 9.0e18 / 64) { g_create_error = "grid too large"; return IBM_ERR_ARG; }
+    ibm_ctx *c = new (std::nothrow) ibm_ctx();
+    if (!c) { g_create_error = "host allocation failed"; return IBM_ERR_OOM; }
+    ibm_status s = create_impl(c, d);
+    if (s != IBM_OK) {
+        g_create_error = c->err.msg;
+        release_all(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_set_opts(ibm_ctx *c, const ibm_solver_opts *o) {
+    if (!c || !o) return IBM_ERR_ARG;
+    std::string why;
+    if (!opts_ok(o, why)) return c->fail(IBM_ERR_ARG, why);
+    const bool to_mixed = o->precision == IBM_MIXED && !c->mg32.built;
+    c->opts = *o;
+    IBM_TRY(alloc_krylov(c, o->restart));
+    if (to_mixed && c->classified) IBM_TRY(mg_build(c));
+    return IBM_OK;
+}
+
+// closed, consistently oriented surface: every directed edge (3D) appears
+// once and its reverse once; in 2D every vertex starts one and ends one segment
+static bool mesh_closed(int ndim, const double *v, int64_t nv, const int32_t *e, int64_t ne, std::string &why) {
+    for (int64_t q = 0; q < nv * 3; ++q)
+        if (!isfinite(v[q])) { why = "non-finite vertex coordinate"; return false; }
+    const int k = ndim == 3 ? 3 : 2;
+    for (int64_t q = 0; q < ne * k; ++q)
+        if (e[q] < 0 || e[q] >= nv) { why = "element index out of range"; return false; }
+    if (ndim == 2) {
+        std::vector<int> outd(nv, 0), ind(nv, 0);
+        for (int64_t q = 0; q < ne; ++q) {
+            if (e[2 * q] == e[2 * q + 1]) { why = "degenerate segment"; return false; }
+            outd[e[2 * q]]++;
+            ind[e[2 * q + 1]]++;
+        }
+        for (int64_t q = 0; q < nv; ++q)
+            if (outd[q] != ind[q] || outd[q] > 1) { why = "polyline is not closed and simple"; return false; }
+        return true;
+    }
+    std::vector<std::pair<int64_t, int64_t>> ed;
+    ed.reserve((size_t)ne * 3);
+    for (int64_t q = 0; q < ne; ++q)
+        for (int r = 0; r < 3; ++r) {
+            const int64_t a = e[3 * q + r], b = e[3 * q + (r + 1) % 3];
+            if (a == b) { why = "degenerate triangle"; return false; }
+            ed.emplace_back(a, b);
+        }
+    std::sort(ed.begin(), ed.end());
+    for (size_t q = 1; q < ed.size(); ++q)
+        if (ed[q] == ed[q - 1]) { why = "an edge is used twice in the same direction"; return false; }
+    for (auto &x : ed)
+        if (!std::binary_search(ed.begin(), ed.end(), std::make_pair(x.second, x.first))) {
+            why = "surface is not closed (an edge has no opposite edge)";
+            return false;
+        }
+    return true;
+}
+
+extern "C" ibm_status ibm_set_body(ibm_ctx *c, const double *verts, int64_t nv, const int32_t *elems, int64_t ne) {
+    if (!c) return IBM_ERR_ARG;
+    if (!verts || !elems || nv < 3 || ne < (c->ndim == 3 ? 4 : 3)) return c->fail(IBM_ERR_ARG, "empty or NULL mesh");
+    std::string why;
+    if (!mesh_closed(c->ndim, verts, nv, elems, ne, why)) return c->fail(IBM_ERR_MESH, why);
+    const int k = c->ndim == 3 ? 3 : 2;
+    const int64_t base = c->nv;
+    if (base + nv > INT32_MAX) return c->fail(IBM_ERR_ARG, "too many vertices");
+    c->verts.insert(c->verts.end(), verts, verts + nv * 3);
+    for (int64_t q = 0; q < ne * k; ++q) c->elems.push_back((int32_t)(elems[q] + base));
+    c->nv += nv;
+    c->ne += ne;
+    dev_free(c, c->d_verts);
+    dev_free(c, c->d_elems);
+    c->d_verts = (double *)dev_alloc(c, sizeof(double) * c->verts.size());
+    c->d_elems = (int32_t *)dev_alloc(c, sizeof(int32_t) * c->elems.size());
+    if (!c->d_verts || !c->d_elems) return c->fail(IBM_ERR_OOM, "mesh allocation failed");
+    IBM_CUDA(c, cudaMemcpyAsync(c->d_verts, c->verts.data(), sizeof(double) * c->verts.size(), cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaMemcpyAsync(c->d_elems, c->elems.data(), sizeof(int32_t) * c->elems.size(), cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    c->classified = false;
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
+    if (!c) return IBM_ERR_ARG;
+    if (c->ne == 0) return c->fail(IBM_ERR_STATE, "ibm_set_body must be called before ibm_classify_cells");
+    IBM_TRY(geom_classify(c));
+    if (c->n_fluid == 0) return c->fail(IBM_ERR_ARG, "no fluid cells");
+    // FLUID volume
+    double vol = 0.0;
+    {
+        const double saved = c->fluid_vol;
+        c->fluid_vol = 1.0;
+        ibm_status s = fluid_mean(c, nullptr, false, &vol);
+        c->fluid_vol = saved;
+        IBM_TRY(s);
+    }
+    c->fluid_vol = vol;
+    IBM_TRY(mg_build(c));
+    IBM_TRY(flow_init(c));
+    c->classified = true;
+    if (out) {
+        out->n_fluid = c->n_fluid;
+        out->n_ghost = c->ng;
+        out->n_dead = c->n_dead;
+        for (int q = 0; q < 3; ++q) out->n_kind[q] = c->n_kind[q];
+    }
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_step(ibm_ctx *c, int nsteps, ibm_step_stats *out) {
+    if (!c) return IBM_ERR_ARG;
+    if (nsteps < 0) return c->fail(IBM_ERR_ARG, "nsteps must be >= 0");
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_step");
+    ibm_step_stats st{};
+    ibm_status status = IBM_OK;
+    for (int q = 0; q < nsteps; ++q) {
+        ibm_status s = flow_step(c, &st);
+        if (s == IBM_ERR_NOT_CONVERGED) status = s;
+        else if (s != IBM_OK) {
+            if (out) *out = st;
+            return s;
+        }
+    }
+    if (nsteps > 0) IBM_TRY(div_stat(c, &st.max_div));
+    if (out) *out = st;
+    return status;
+}
+
+extern "C" ibm_status ibm_poisson_solve(ibm_ctx *c, const double *rhs, double *phi, double rtol, int maxit,
+                                        ibm_solve_stats *st) {
+    if (!c) return IBM_ERR_ARG;
+    if (!rhs || !phi) return c->fail(IBM_ERR_ARG, "rhs and phi must be device pointers");
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_poisson_solve");
+    const char *a0 = (const char *)rhs, *b0 = (const char *)phi;
+    const size_t nb = sizeof(double) * c->N;
+    if (a0 < b0 + nb && b0 < a0 + nb) return c->fail(IBM_ERR_ARG, "rhs and phi overlap");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, rhs) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+        cudaPointerGetAttributes(&at, phi) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return c->fail(IBM_ERR_ARG, "rhs and phi must be device memory");
+    }
+    return poisson_solve(c, rhs, phi, rtol > 0 ? rtol : c->opts.rtol, maxit > 0 ? maxit : c->opts.max_outer, st);
+}
+
+extern "C" ibm_status ibm_get_tables(ibm_ctx *c, const ibm_tables_host *t) {
+    if (!c || !t) return IBM_ERR_ARG;
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "no tables before ibm_classify_cells");
+    const int64_t g = c->ng;
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> ibm_status {
+        if (!dst || bytes == 0) return IBM_OK;
+        IBM_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->s));
+        return IBM_OK;
+    };
+    IBM_TRY(cp(t->type, c->type, c->N));
+    IBM_TRY(cp(t->gidx, c->gidx, 8 * g));
+    IBM_TRY(cp(t->bi, c->bi, 24 * g));
+    IBM_TRY(cp(t->nrm, c->nrm, 24 * g));
+    IBM_TRY(cp(t->ip, c->ipt, 24 * g));
+    IBM_TRY(cp(t->dist, c->dist, 8 * g));
+    IBM_TRY(cp(t->base, c->base, 8 * g));
+    IBM_TRY(cp(t->kind, c->kind, g));
+    IBM_TRY(cp(t->cmask, c->cmask, g));
+    IBM_TRY(cp(t->sidx, c->sidx, 64 * g));
+    IBM_TRY(cp(t->wv, c->wv, 64 * g));
+    IBM_TRY(cp(t->wp, c->wp, 64 * g));
+    IBM_TRY(cp(t->bv, c->bv, 8 * g));
+    IBM_TRY(cp(t->bp, c->bp, 8 * g));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
+static ibm_status field_ptr(Ctx *c, int field, void **p, size_t *bytes) {
+    const size_t nb = sizeof(double) * c->N;
+    const int nd = c->ndim;
+    switch (field) {
+    case IBM_FIELD_U: case IBM_FIELD_V: case IBM_FIELD_W:
+        if (field - IBM_FIELD_U >= nd) return c->fail(IBM_ERR_ARG, "no w component in 2D");
+        *p = c->u[field - IBM_FIELD_U]; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_P: *p = c->p; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_FACE_U: *p = c->F[0]; *bytes = sizeof(double) * c->NFx; return IBM_OK;
+    case IBM_FIELD_FACE_V: *p = c->F[1]; *bytes = sizeof(double) * c->NFy; return IBM_OK;
+    case IBM_FIELD_FACE_W:
+        if (nd < 3) return c->fail(IBM_ERR_ARG, "no z faces in 2D");
+        *p = c->F[2]; *bytes = sizeof(double) * c->NFz; return IBM_OK;
+    case IBM_FIELD_NOLD_U: case IBM_FIELD_NOLD_V: case IBM_FIELD_NOLD_W:
+        if (field - IBM_FIELD_NOLD_U >= nd) return c->fail(IBM_ERR_ARG, "no w component in 2D");
+        *p = c->Nold[field - IBM_FIELD_NOLD_U]; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_TYPE: *p = c->type; *bytes = c->N; return IBM_OK;
+    case IBM_FIELD_USTAR_U: case IBM_FIELD_USTAR_V: case IBM_FIELD_USTAR_W:
+        if (field - IBM_FIELD_USTAR_U >= nd) return c->fail(IBM_ERR_ARG, "no w component in 2D");
+        *p = c->ustar[field - IBM_FIELD_USTAR_U]; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_RHS: *p = c->b; *bytes = nb; return IBM_OK;
+    default: return c->fail(IBM_ERR_ARG, "unknown field id");
+    }
+}
+
+extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_device, size_t bytes) {
+    if (!c || !dst) return IBM_ERR_ARG;
+    if (field == IBM_FIELD_STEP) {
+        if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
+        int64_t v = c->nstep + (c->have_nold ? 0 : 0);
+        if (is_device) IBM_CUDA(c, cudaMemcpy(dst, &v, 8, cudaMemcpyHostToDevice));
+        else memcpy(dst, &v, 8);
+        return IBM_OK;
+    }
+    void *p = nullptr;
+    size_t nb = 0;
+    IBM_TRY(field_ptr(c, field, &p, &nb));
+    if (bytes != nb) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
+    IBM_CUDA(c, cudaMemcpyAsync(dst, p, nb, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_set_field(ibm_ctx *c, int field, const void *src, int is_device, size_t bytes) {
+    if (!c || !src) return IBM_ERR_ARG;
+    if (field == IBM_FIELD_STEP) {
+        if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
+        int64_t v = 0;
+        if (is_device) IBM_CUDA(c, cudaMemcpy(&v, src, 8, cudaMemcpyDeviceToHost));
+        else memcpy(&v, src, 8);
+        if (v < 0) return c->fail(IBM_ERR_ARG, "negative step counter");
+        c->nstep = v;
+        c->have_nold = v > 0;
+        return IBM_OK;
+    }
+    if (field == IBM_FIELD_TYPE) return c->fail(IBM_ERR_ARG, "cell types are set by ibm_classify_cells");
+    void *p = nullptr;
+    size_t nb = 0;
+    IBM_TRY(field_ptr(c, field, &p, &nb));
+    if (bytes != nb) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
+    IBM_CUDA(c, cudaMemcpyAsync(p, src, nb, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_sizes(ibm_ctx *c, int64_t *n_cells, int64_t *n_ghost) {
+    if (!c) return IBM_ERR_ARG;
+    if (n_cells) *n_cells = c->N;
+    if (n_ghost) *n_ghost = c->ng;
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_destroy(ibm_ctx *c) {
+    if (!c) return IBM_OK;
+    release_all(c);
+    delete c;
+    return IBM_OK;
+}
+
+extern "C" const char *ibm_last_error(ibm_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.msg.c_str();
+}

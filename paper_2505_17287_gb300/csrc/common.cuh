@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libibm.so.
+// Not part of the public ABI (include/ibm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+
+namespace ibm {
+
+constexpr uint8_t FLUID = IBM_FLUID, GHOST = IBM_GHOST, DEAD = IBM_DEAD;
+
+// Deterministic reductions: every reduction kernel runs on a fixed grid of
+// RED_BLOCKS blocks of RED_THREADS threads, writes one partial per block,
+// and a single block then adds the partials in a fixed order.
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 152 * 4;   // 4 blocks per SM on a 152-SM GB300
+
+// host-side status carrier: message + code
+struct Err {
+    ibm_status code = IBM_OK;
+    std::string msg;
+};
+
+// Failure helpers used by every host function of the library.
+#define IBM_CUDA(ctx, call)                                                          \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            return (ctx)->fail(IBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                            \
+    } while (0)
+#define IBM_LAUNCHED(ctx) IBM_CUDA(ctx, cudaGetLastError())
+#define IBM_TRY(expr)                          \
+    do {                                       \
+        ibm_status s_ = (expr);                \
+        if (s_ != IBM_OK) return s_;           \
+    } while (0)
+
+// device view of a grid level (coordinates and extents)
+struct GridDev {
+    int nx, ny, nz, ndim;
+    int64_t n;            // nx*ny*nz
+    const double *xf, *yf, *zf;   // faces
+    const double *xc, *yc, *zc;   // centres
+    const double *dx, *dy, *dz;   // widths
+    const double *hx, *hy, *hz;   // centre spacing; h?[i] = c[i]-c[i-1] for i>=1, [0] unused
+};
+
+// per-ghost tables (device, structure of arrays)
+struct GhostDev {
+    int64_t ng;
+    const int64_t *gidx;      // ascending
+    const int64_t *sidx;      // 8 per ghost
+    const double *wv, *wp;    // 8 per ghost
+    const double *bv, *bp;    // 1 per ghost
+};
+
+// one multigrid level of the staircase operator K = sum_open T (x_c - x_nb)
+template <typename T>
+struct MGLevel {
+    int nx, ny, nz;
+    int64_t n;
+    T *tx, *ty, *tz;   // coefficient of the face on the low side of each cell
+    T *x, *f, *r;      // correction, right-hand side, scratch
+};
+
+struct Ctx;
+
+// allocation through the user hook or cudaMalloc; tracked for release
+void *dev_alloc(Ctx *c, size_t bytes);
+void dev_free(Ctx *c, void *p);
+
+// reduction helper: block partials to one value (device function kernels in solver.cu)
+ibm_status reduce_sum(Ctx *c, const double *partials, int nparts, double *out_dev);
+
+}  // namespace ibm
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+namespace ibm {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum in a fixed order; result valid in thread 0
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < NT / 32 ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace ibm

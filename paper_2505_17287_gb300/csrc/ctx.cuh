@@ -1,0 +1,109 @@
+// Context of one grid: every device allocation of the library hangs here.
+#pragma once
+
+#include "common.cuh"
+
+namespace ibm {
+
+template <typename T>
+struct MGHier {
+    std::vector<MGLevel<T>> lv;
+    T *d0 = nullptr;        // diagonal of level 0 (per level diagonals in dg)
+    std::vector<T *> dg;    // diagonal per level
+    // PCG vectors on level 0
+    T *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
+    bool built = false;
+};
+
+// 1D coordinates of one multigrid level (host) and the axis coarsening flags
+struct LevelGeom {
+    int nx, ny, nz;
+    int fx, fy, fz;   // coarsening factor from the level above (1 or 2)
+    std::vector<double> xf, yf, zf;
+};
+
+struct Ctx {
+    Err err;
+    ibm_grid_desc desc{};
+    ibm_solver_opts opts{};
+    cudaStream_t s = nullptr;
+    std::vector<void *> allocs;
+
+    // grid
+    int ndim = 0, nx = 0, ny = 0, nz = 0;
+    int64_t N = 0, NFx = 0, NFy = 0, NFz = 0;  // cells and faces per axis
+    std::vector<double> hxf, hyf, hzf, hxc, hyc, hzc, hdx, hdy, hdz, hhx, hhy, hhz;
+    double *xf = nullptr, *yf = nullptr, *zf = nullptr, *xc = nullptr, *yc = nullptr, *zc = nullptr;
+    double *dx = nullptr, *dy = nullptr, *dz = nullptr, *hx = nullptr, *hy = nullptr, *hz = nullptr;
+    GridDev g{};
+
+    // immersed bodies (host accumulation of all set_body calls)
+    std::vector<double> verts;
+    std::vector<int32_t> elems;
+    int64_t nv = 0, ne = 0;
+    bool classified = false;
+    double *d_verts = nullptr;
+    int32_t *d_elems = nullptr;
+    int64_t *d_vq = nullptr;
+
+    // cells and ghost tables
+    uint8_t *type = nullptr, *inside = nullptr;
+    double fluid_vol = 0.0;
+    int64_t n_fluid = 0, n_dead = 0, ng = 0, n_kind[3] = {0, 0, 0};
+    int64_t *gidx = nullptr, *base = nullptr, *sidx = nullptr;
+    double *bi = nullptr, *nrm = nullptr, *ipt = nullptr, *dist = nullptr;
+    double *wv = nullptr, *wp = nullptr, *bv = nullptr, *bp = nullptr;
+    uint8_t *kind = nullptr, *cmask = nullptr;
+    int64_t ng_cap = 0;
+    GhostDev gh{};
+
+    // flow state
+    double *u[3] = {nullptr, nullptr, nullptr}, *F[3] = {nullptr, nullptr, nullptr};
+    double *p = nullptr, *Nold[3] = {nullptr, nullptr, nullptr}, *Nnew[3] = {nullptr, nullptr, nullptr};
+    double *ustar[3] = {nullptr, nullptr, nullptr}, *rhs[3] = {nullptr, nullptr, nullptr};
+    double *b = nullptr, *gtmp = nullptr;
+    int64_t nstep = 0;
+    bool have_nold = false;
+
+    // reductions and scalars
+    double *part = nullptr;      // partials: RED_BLOCKS * 32
+    double *scal = nullptr;      // device scalars (64)
+    double *hscal = nullptr;     // pinned host mirror (64)
+
+    // Poisson (FP64 FGMRES)
+    int m_cap = 0;
+    std::vector<double *> V, Z;
+    double **Vdev = nullptr, **Zdev = nullptr;   // device arrays of the V / Z pointers
+    double *w = nullptr, *rr = nullptr;
+    std::vector<LevelGeom> lg;
+    std::vector<double *> lhx, lhy, lhz;   // per level centre spacing (device)
+    MGHier<double> mg64;
+    MGHier<float> mg32;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+
+    ibm_status fail(ibm_status code, const std::string &m) {
+        err.code = code;
+        err.msg = m;
+        return code;
+    }
+};
+
+// solver.cu
+ibm_status mg_build(Ctx *c);
+ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, int maxit,
+                         ibm_solve_stats *st);
+ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_host);
+ibm_status sync_scalars(Ctx *c, int n);
+ibm_status finalize(Ctx *c, const double *part, int nparts, int ncols, double scale, double *out_dev);
+
+// geom.cu
+ibm_status geom_classify(Ctx *c);
+
+// flow.cu
+ibm_status flow_init(Ctx *c);
+ibm_status flow_step(Ctx *c, ibm_step_stats *st);
+ibm_status ghost_refresh_velocity(Ctx *c, int comp, int *iters);
+ibm_status div_stat(Ctx *c, double *out);
+
+}  // namespace ibm

@@ -1,0 +1,659 @@
+// Fractional step around the Poisson solve (Section 2.1 of the paper):
+// conservative central convection (Eq. 1) with Adams-Bashforth-2, Crank-
+// Nicolson diffusion solved by red-black Gauss-Seidel with the Dirichlet
+// ghost-cell rows of Section 2.2, face velocities and their divergence, and
+// the projection that makes the face velocities divergence-free. All FP64.
+#include "ctx.cuh"
+
+#include <math.h>
+
+namespace ibm {
+
+enum { F_NET = 0, F_AREA = 1 };
+
+// per component, per outer face: Dirichlet flag and value
+struct BCInfo {
+    int dir[3][6];
+    double val[3][6];
+    int code[6];
+    double uinf[3];
+};
+
+static BCInfo make_bc(const Ctx *c) {
+    BCInfo b{};
+    for (int f = 0; f < 6; ++f) b.code[f] = c->desc.bc[f];
+    for (int a = 0; a < 3; ++a) b.uinf[a] = c->desc.u_inf[a];
+    for (int comp = 0; comp < 3; ++comp)
+        for (int f = 0; f < 6; ++f) {
+            const int axis = f / 2, code = c->desc.bc[f];
+            if (code == IBM_BC_INFLOW) { b.dir[comp][f] = 1; b.val[comp][f] = c->desc.u_inf[comp]; }
+            else if (code == IBM_BC_SLIP && comp == axis) { b.dir[comp][f] = 1; b.val[comp][f] = 0.0; }
+            else { b.dir[comp][f] = 0; b.val[comp][f] = 0.0; }
+        }
+    return b;
+}
+
+__device__ __forceinline__ void ijk(int64_t c, int nx, int ny, int &i, int &j, int &k) {
+    const int64_t t = c / nx;
+    i = (int)(c - t * nx);
+    j = (int)(t % ny);
+    k = (int)(t / ny);
+}
+
+// face indices of the low face of cell (i,j,k) along each axis
+__device__ __forceinline__ int64_t fx_lo(const GridDev &g, int i, int j, int k) {
+    return (int64_t)i + (int64_t)(g.nx + 1) * (j + (int64_t)g.ny * k);
+}
+__device__ __forceinline__ int64_t fy_lo(const GridDev &g, int i, int j, int k) {
+    return (int64_t)i + (int64_t)g.nx * (j + (int64_t)(g.ny + 1) * k);
+}
+__device__ __forceinline__ int64_t fz_lo(const GridDev &g, int i, int j, int k) {
+    return (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+}
+
+struct Fields3 {
+    double *p[3];
+};
+struct CFields3 {
+    const double *p[3];
+};
+
+// Convective term N^n, explicit viscous term and the AB2 + CN right-hand side
+// on FLUID cells; other cells get rhs = 0 and N = 0.
+__global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3 u, CFields3 F, CFields3 Nold,
+                           int first, Fields3 Nnew, Fields3 rhs, BCInfo bc, double dt, double alpha, int ncomp) {
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (type[c] != FLUID) {
+            for (int q = 0; q < ncomp; ++q) { Nnew.p[q][c] = 0.0; rhs.p[q][c] = 0.0; }
+            continue;
+        }
+        int i, j, k;
+        ijk(c, g.nx, g.ny, i, j, k);
+        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
+        const double A[3] = {g.dy[j] * g.dz[k], g.dx[i] * g.dz[k], g.dx[i] * g.dy[j]};
+        const int idx[3] = {i, j, k};
+        const int nn[3] = {g.nx, g.ny, g.nz};
+        const int64_t st[3] = {1, sy, sz};
+        const double *hh[3] = {g.hx, g.hy, g.hz};
+        const double *hw[3] = {g.dx, g.dy, g.dz};
+        double Flo[3], Fhi[3];
+        Flo[0] = F.p[0][fx_lo(g, i, j, k)];
+        Fhi[0] = F.p[0][fx_lo(g, i, j, k) + 1];
+        Flo[1] = F.p[1][fy_lo(g, i, j, k)];
+        Fhi[1] = F.p[1][fy_lo(g, i, j, k) + g.nx];
+        if (g.ndim == 3) {
+            Flo[2] = F.p[2][fz_lo(g, i, j, k)];
+            Fhi[2] = F.p[2][fz_lo(g, i, j, k) + sz];
+        } else {
+            Flo[2] = Fhi[2] = 0.0;
+        }
+        for (int q = 0; q < ncomp; ++q) {
+            const double *uq = u.p[q];
+            const double uc = uq[c];
+            double flux = 0.0, lap = 0.0, src = 0.0;
+            for (int a = 0; a < g.ndim; ++a) {
+                double ulo, uhi;
+                // low face
+                if (idx[a] > 0) {
+                    const double un = uq[c - st[a]];
+                    ulo = 0.5 * (uc + un);
+                    lap += A[a] * (un - uc) / hh[a][idx[a]];
+                } else {
+                    const int f = 2 * a;
+                    if (bc.dir[q][f]) {
+                        ulo = bc.val[q][f];
+                        const double hb = 0.5 * hw[a][0];
+                        lap += A[a] * (bc.val[q][f] - uc) / hb;
+                        src += A[a] * bc.val[q][f] / hb;
+                    } else {
+                        ulo = uc;
+                    }
+                }
+                // high face
+                if (idx[a] < nn[a] - 1) {
+                    const double un = uq[c + st[a]];
+                    uhi = 0.5 * (uc + un);
+                    lap += A[a] * (un - uc) / hh[a][idx[a] + 1];
+                } else {
+                    const int f = 2 * a + 1;
+                    if (bc.dir[q][f]) {
+                        uhi = bc.val[q][f];
+                        const double hb = 0.5 * hw[a][nn[a] - 1];
+                        lap += A[a] * (bc.val[q][f] - uc) / hb;
+                        src += A[a] * bc.val[q][f] / hb;
+                    } else {
+                        uhi = uc;
+                    }
+                }
+                flux += A[a] * Fhi[a] * uhi - A[a] * Flo[a] * ulo;
+            }
+            const double N = flux / vol;
+            const double No = first ? N : Nold.p[q][c];
+            Nnew.p[q][c] = N;
+            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * (lap / vol) + alpha * (src / vol);
+        }
+    }
+}
+
+// Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
+__global__ void k_helm_rb(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+                          double *__restrict__ u, BCInfo bc, int q, double alpha, int col) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
+    if (i >= g.nx) return;
+    const int64_t c = row * g.nx + i;
+    if (type[c] != FLUID) return;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const double vol = g.dx[i] * g.dy[j] * g.dz[k];
+    const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
+    double d = 0.0, s = 0.0, t;
+    if (i > 0) { t = ax / g.hx[i]; d += t; s += t * u[c - 1]; } else if (bc.dir[q][0]) d += ax / (0.5 * g.dx[0]);
+    if (i < g.nx - 1) { t = ax / g.hx[i + 1]; d += t; s += t * u[c + 1]; } else if (bc.dir[q][1]) d += ax / (0.5 * g.dx[g.nx - 1]);
+    if (j > 0) { t = ay / g.hy[j]; d += t; s += t * u[c - sy]; } else if (bc.dir[q][2]) d += ay / (0.5 * g.dy[0]);
+    if (j < g.ny - 1) { t = ay / g.hy[j + 1]; d += t; s += t * u[c + sy]; } else if (bc.dir[q][3]) d += ay / (0.5 * g.dy[g.ny - 1]);
+    if (g.ndim == 3) {
+        if (k > 0) { t = az / g.hz[k]; d += t; s += t * u[c - sz]; } else if (bc.dir[q][4]) d += az / (0.5 * g.dz[0]);
+        if (k < g.nz - 1) { t = az / g.hz[k + 1]; d += t; s += t * u[c + sz]; } else if (bc.dir[q][5]) d += az / (0.5 * g.dz[g.nz - 1]);
+    }
+    const double a = alpha / vol;
+    u[c] = (rhs[c] + a * s) / (1.0 + a * d);
+}
+
+// residual of the Helmholtz system: FLUID rows rhs - H u; GHOST rows
+// -(u_G + sum wv u_m) (rhs 0). partial columns: |r|^2, |rhs|^2
+__global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+                             const double *__restrict__ u, BCInfo bc, int q, double alpha, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double rr = 0.0, bb = 0.0;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (type[c] != FLUID) continue;
+        int i, j, k;
+        ijk(c, g.nx, g.ny, i, j, k);
+        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
+        const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
+        const double uc = u[c];
+        double s = 0.0;
+        if (i > 0) s += ax / g.hx[i] * (u[c - 1] - uc); else if (bc.dir[q][0]) s -= ax / (0.5 * g.dx[0]) * uc;
+        if (i < g.nx - 1) s += ax / g.hx[i + 1] * (u[c + 1] - uc); else if (bc.dir[q][1]) s -= ax / (0.5 * g.dx[g.nx - 1]) * uc;
+        if (j > 0) s += ay / g.hy[j] * (u[c - sy] - uc); else if (bc.dir[q][2]) s -= ay / (0.5 * g.dy[0]) * uc;
+        if (j < g.ny - 1) s += ay / g.hy[j + 1] * (u[c + sy] - uc); else if (bc.dir[q][3]) s -= ay / (0.5 * g.dy[g.ny - 1]) * uc;
+        if (g.ndim == 3) {
+            if (k > 0) s += az / g.hz[k] * (u[c - sz] - uc); else if (bc.dir[q][4]) s -= az / (0.5 * g.dz[0]) * uc;
+            if (k < g.nz - 1) s += az / g.hz[k + 1] * (u[c + sz] - uc); else if (bc.dir[q][5]) s -= az / (0.5 * g.dz[g.nz - 1]) * uc;
+        }
+        const double r = rhs[c] - (uc - (alpha / vol) * s);
+        rr += r * r;
+        bb += rhs[c] * rhs[c];
+    }
+    rr = block_sum<RED_THREADS>(rr, sh);
+    bb = block_sum<RED_THREADS>(bb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = rr;
+        part[gridDim.x + blockIdx.x] = bb;
+    }
+}
+
+// Dirichlet ghost rows for up to three components at once:
+// tmp[q*ng + g] = (2 - bv) u_BI - sum_m wv_m u_m, u_BI = 0 (body at rest)
+__global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, double *__restrict__ tmp,
+                                 double *__restrict__ res, int want_res) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ double sh[32];
+    double r2 = 0.0;
+    if (q < gh.ng) {
+        for (int cq = 0; cq < ncomp; ++cq) {
+            const double *uu = u.p[cq];
+            double s = 0.0;
+            for (int m = 0; m < 8; ++m) s -= gh.wv[8 * q + m] * uu[gh.sidx[8 * q + m]];
+            tmp[cq * gh.ng + q] = s;
+            const double d = s - uu[gh.gidx[q]];
+            r2 = fmax(r2, fabs(d));
+        }
+    }
+    if (want_res) {
+        r2 = warp_max(r2);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+            t = warp_max(t);
+            if (threadIdx.x == 0) res[blockIdx.x] = t;
+        }
+    }
+}
+__global__ void k_vghost_scatter(GhostDev gh, Fields3 u, int ncomp, const double *__restrict__ tmp) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= gh.ng) return;
+    for (int cq = 0; cq < ncomp; ++cq) u.p[cq][gh.gidx[q]] = tmp[cq * gh.ng + q];
+}
+__global__ void k_max_final(const double *__restrict__ part, int n, double *__restrict__ out) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, part[i]);
+    m = warp_max(m);
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+// face velocities of axis a from cell values (interior and outer faces)
+__global__ void k_faces(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ ua, int a,
+                        BCInfo bc, double *__restrict__ Fa) {
+    const int nfx = g.nx + (a == 0), nfy = g.ny + (a == 1), nfz = g.nz + (a == 2);
+    const int64_t nf = (int64_t)nfx * nfy * nfz;
+    const int64_t st = a == 0 ? 1 : (a == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny);
+    const int nax = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = f / nfx;
+        const int fi = (int)(f - t * nfx), fj = (int)(t % nfy), fk = (int)(t / nfy);
+        const int fa = a == 0 ? fi : (a == 1 ? fj : fk);
+        // cell on the high side (index fa along a) and on the low side (fa-1)
+        const int ci = fi, cj = fj, ck = fk;
+        double v;
+        if (fa == 0 || fa == nax) {
+            const int side = fa == 0 ? 0 : 1;
+            const int code = bc.code[2 * a + side];
+            if (code == IBM_BC_INFLOW) v = bc.uinf[a];
+            else if (code == IBM_BC_SLIP) v = 0.0;
+            else {
+                const int64_t cc = side == 0 ? (int64_t)ci + (int64_t)g.nx * (cj + (int64_t)g.ny * ck)
+                                             : (int64_t)(a == 0 ? ci - 1 : ci) +
+                                                   (int64_t)g.nx * ((a == 1 ? cj - 1 : cj) + (int64_t)g.ny * (a == 2 ? ck - 1 : ck));
+                v = type[cc] == FLUID ? ua[cc] : 0.0;
+            }
+        } else {
+            const int64_t cR = (int64_t)ci + (int64_t)g.nx * (cj + (int64_t)g.ny * ck);
+            const int64_t cL = cR - st;
+            const uint8_t tL = type[cL], tR = type[cR];
+            const bool ok = tL != DEAD && tR != DEAD && (tL == FLUID || tR == FLUID);
+            v = ok ? 0.5 * (ua[cL] + ua[cR]) : 0.0;
+        }
+        Fa[f] = v;
+    }
+}
+
+// net inflow through the outer faces and the FLUID outflow area
+__global__ void k_bnd_flux(GridDev g, const uint8_t *__restrict__ type, CFields3 F, BCInfo bc, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double net = 0.0, area = 0.0;
+    const int64_t nyz = (int64_t)g.ny * g.nz, nxz = (int64_t)g.nx * g.nz, nxy = (int64_t)g.nx * g.ny;
+    const int64_t tot = 2 * nyz + 2 * nxz + (g.ndim == 3 ? 2 * nxy : 0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int a, side;
+        int64_t r = e;
+        if (r < 2 * nyz) { a = 0; side = (int)(r / nyz); r %= nyz; }
+        else if ((r -= 2 * nyz) < 2 * nxz) { a = 1; side = (int)(r / nxz); r %= nxz; }
+        else { r -= 2 * nxz; a = 2; side = (int)(r / nxy); r %= nxy; }
+        int i, j, k;
+        int64_t fidx, cidx;
+        double A;
+        if (a == 0) {
+            j = (int)(r % g.ny); k = (int)(r / g.ny); i = side ? g.nx - 1 : 0;
+            fidx = (int64_t)(side ? g.nx : 0) + (int64_t)(g.nx + 1) * (j + (int64_t)g.ny * k);
+            A = g.dy[j] * g.dz[k];
+        } else if (a == 1) {
+            i = (int)(r % g.nx); k = (int)(r / g.nx); j = side ? g.ny - 1 : 0;
+            fidx = (int64_t)i + (int64_t)g.nx * ((side ? g.ny : 0) + (int64_t)(g.ny + 1) * k);
+            A = g.dx[i] * g.dz[k];
+        } else {
+            i = (int)(r % g.nx); j = (int)(r / g.nx); k = side ? g.nz - 1 : 0;
+            fidx = (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * (side ? g.nz : 0));
+            A = g.dx[i] * g.dy[j];
+        }
+        cidx = (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+        const double v = F.p[a][fidx];
+        net += (side == 0 ? 1.0 : -1.0) * (A * v);
+        if (bc.code[2 * a + side] == IBM_BC_OUTFLOW && type[cidx] == FLUID) area += A;
+    }
+    net = block_sum<RED_THREADS>(net, sh);
+    area = block_sum<RED_THREADS>(area, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = net;
+        part[gridDim.x + blockIdx.x] = area;
+    }
+}
+
+// uniform correction of OUTFLOW faces over FLUID cells: corr = net / area
+__global__ void k_outflow_corr(GridDev g, const uint8_t *__restrict__ type, Fields3 F, BCInfo bc,
+                               const double *__restrict__ sums) {
+    const double area = sums[F_AREA];
+    if (!(area > 0.0)) return;
+    const double corr = sums[F_NET] / area;
+    const int64_t nyz = (int64_t)g.ny * g.nz, nxz = (int64_t)g.nx * g.nz, nxy = (int64_t)g.nx * g.ny;
+    const int64_t tot = 2 * nyz + 2 * nxz + (g.ndim == 3 ? 2 * nxy : 0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int a, side;
+        int64_t r = e;
+        if (r < 2 * nyz) { a = 0; side = (int)(r / nyz); r %= nyz; }
+        else if ((r -= 2 * nyz) < 2 * nxz) { a = 1; side = (int)(r / nxz); r %= nxz; }
+        else { r -= 2 * nxz; a = 2; side = (int)(r / nxy); r %= nxy; }
+        if (bc.code[2 * a + side] != IBM_BC_OUTFLOW) continue;
+        int i, j, k;
+        int64_t fidx;
+        if (a == 0) {
+            j = (int)(r % g.ny); k = (int)(r / g.ny); i = side ? g.nx - 1 : 0;
+            fidx = (int64_t)(side ? g.nx : 0) + (int64_t)(g.nx + 1) * (j + (int64_t)g.ny * k);
+        } else if (a == 1) {
+            i = (int)(r % g.nx); k = (int)(r / g.nx); j = side ? g.ny - 1 : 0;
+            fidx = (int64_t)i + (int64_t)g.nx * ((side ? g.ny : 0) + (int64_t)(g.ny + 1) * k);
+        } else {
+            i = (int)(r % g.nx); j = (int)(r / g.nx); k = side ? g.nz - 1 : 0;
+            fidx = (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * (side ? g.nz : 0));
+        }
+        const int64_t cidx = (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+        if (type[cidx] == FLUID) F.p[a][fidx] += (side == 0 ? -corr : corr);
+    }
+}
+
+// b_raw = div(F) / dt on FLUID cells, 0 elsewhere
+__global__ void k_divergence(GridDev g, const uint8_t *__restrict__ type, CFields3 F, double inv_dt,
+                             double *__restrict__ out) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (type[c] != FLUID) { out[c] = 0.0; continue; }
+        int i, j, k;
+        ijk(c, g.nx, g.ny, i, j, k);
+        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
+        double d = g.dy[j] * g.dz[k] * (F.p[0][fx_lo(g, i, j, k) + 1] - F.p[0][fx_lo(g, i, j, k)]);
+        d += g.dx[i] * g.dz[k] * (F.p[1][fy_lo(g, i, j, k) + g.nx] - F.p[1][fy_lo(g, i, j, k)]);
+        if (g.ndim == 3)
+            d += g.dx[i] * g.dy[j] * (F.p[2][fz_lo(g, i, j, k) + (int64_t)g.nx * g.ny] - F.p[2][fz_lo(g, i, j, k)]);
+        out[c] = (d / vol) * inv_dt;
+    }
+}
+
+// projection of the interior faces of axis a that have a FLUID side
+__global__ void k_project_faces(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ phi, int a,
+                                double dt, double *__restrict__ Fa) {
+    const int nfx = g.nx + (a == 0), nfy = g.ny + (a == 1), nfz = g.nz + (a == 2);
+    const int64_t nf = (int64_t)nfx * nfy * nfz;
+    const int64_t st = a == 0 ? 1 : (a == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny);
+    const int nax = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+    const double *hc = a == 0 ? g.hx : (a == 1 ? g.hy : g.hz);
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = f / nfx;
+        const int fi = (int)(f - t * nfx), fj = (int)(t % nfy), fk = (int)(t / nfy);
+        const int fa = a == 0 ? fi : (a == 1 ? fj : fk);
+        if (fa == 0 || fa == nax) continue;
+        const int64_t cR = (int64_t)fi + (int64_t)g.nx * (fj + (int64_t)g.ny * fk);
+        const int64_t cL = cR - st;
+        if (type[cL] != FLUID && type[cR] != FLUID) continue;
+        Fa[f] -= dt * (phi[cR] - phi[cL]) / hc[fa];
+    }
+}
+
+// cell velocities on FLUID cells: u_a -= dt * mean of the two face gradients
+__global__ void k_project_cells(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ phi,
+                                CFields3 us, Fields3 u, double dt) {
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t t = type[c];
+        if (t != FLUID) {
+            for (int a = 0; a < g.ndim; ++a) u.p[a][c] = us.p[a][c];
+            continue;
+        }
+        int i, j, k;
+        ijk(c, g.nx, g.ny, i, j, k);
+        const double pc = phi[c];
+        double glo, ghi;
+        glo = i > 0 ? (pc - phi[c - 1]) / g.hx[i] : 0.0;
+        ghi = i < g.nx - 1 ? (phi[c + 1] - pc) / g.hx[i + 1] : 0.0;
+        u.p[0][c] = us.p[0][c] - dt * (0.5 * (glo + ghi));
+        glo = j > 0 ? (pc - phi[c - sy]) / g.hy[j] : 0.0;
+        ghi = j < g.ny - 1 ? (phi[c + sy] - pc) / g.hy[j + 1] : 0.0;
+        u.p[1][c] = us.p[1][c] - dt * (0.5 * (glo + ghi));
+        if (g.ndim == 3) {
+            glo = k > 0 ? (pc - phi[c - sz]) / g.hz[k] : 0.0;
+            ghi = k < g.nz - 1 ? (phi[c + sz] - pc) / g.hz[k + 1] : 0.0;
+            u.p[2][c] = us.p[2][c] - dt * (0.5 * (glo + ghi));
+        }
+    }
+}
+
+__global__ void k_init_cells(int64_t n, const uint8_t *__restrict__ type, Fields3 u, double u0, double u1, double u2,
+                             int ncomp, double *__restrict__ p) {
+    const double v[3] = {u0, u1, u2};
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const bool fl = type[c] == FLUID;
+        for (int q = 0; q < ncomp; ++q) u.p[q][c] = fl ? v[q] : 0.0;
+        p[c] = 0.0;
+    }
+}
+
+// max |div F - mean| over FLUID cells, in two passes
+__global__ void k_div_stats(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ div,
+                            const double *__restrict__ mean, double *__restrict__ part) {
+    const double m = mean ? *mean : 0.0;
+    double mx = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x)
+        if (type[c] == FLUID) mx = fmax(mx, fabs(div[c] - m));
+    __shared__ double sh[32];
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+static inline dim3 rb_grid(const Ctx *c) {
+    const int64_t rows = (int64_t)c->ny * c->nz;
+    const int xs = (c->nx + 1) / 2;
+    return dim3((unsigned)rows, (unsigned)((xs + 127) / 128), 1);
+}
+
+static ibm_status faces_from(Ctx *c, double *const *ucell) {
+    const BCInfo bc = make_bc(c);
+    for (int a = 0; a < c->ndim; ++a) {
+        const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
+        const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
+        k_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, ucell[a], a, bc, c->F[a]);
+        IBM_LAUNCHED(c);
+    }
+    CFields3 F{{c->F[0], c->F[1], c->F[2]}};
+    k_bnd_flux<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, F, bc, c->part);
+    IBM_LAUNCHED(c);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 56));
+    Fields3 Fw{{c->F[0], c->F[1], c->F[2]}};
+    k_outflow_corr<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, Fw, bc, c->scal + 56);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+// velocity ghost refresh by Jacobi passes over the ghost rows (all
+// components at once) until the largest change is below ghost_tol (relative
+// to max(1, |u_inf|)) or ghost_maxit passes
+static ibm_status ghost_refresh_all(Ctx *c, double *const *ucell, int *passes) {
+    *passes = 0;
+    if (c->ng == 0) return IBM_OK;
+    const int nc = c->ndim;
+    Fields3 U{{ucell[0], ucell[1], nc == 3 ? ucell[2] : ucell[1]}};
+    const unsigned gb = (unsigned)((c->ng + 255) / 256);
+    double scale = 1.0;
+    for (int a = 0; a < 3; ++a) scale = fmax(scale, fabs(c->desc.u_inf[a]));
+    const int check_every = 4;
+    for (int it = 0; it < c->opts.ghost_maxit; ++it) {
+        const int want = ((it + 1) % check_every == 0) || it + 1 == c->opts.ghost_maxit;
+        k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, want);
+        k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
+        IBM_LAUNCHED(c);
+        ++*passes;
+        if (want) {
+            k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
+            IBM_LAUNCHED(c);
+            IBM_TRY(sync_scalars(c, 41));
+            const double d = c->hscal[40];
+            if (!isfinite(d)) return c->fail(IBM_ERR_DIVERGED, "velocity ghost refresh produced a non-finite value");
+            if (d <= c->opts.ghost_tol * scale) return IBM_OK;
+        }
+    }
+    return IBM_OK;
+}
+
+ibm_status ghost_refresh_velocity(Ctx *c, int comp, int *iters) {
+    (void)comp;
+    return ghost_refresh_all(c, c->u, iters);
+}
+
+ibm_status flow_init(Ctx *c) {
+    Fields3 U{{c->u[0], c->u[1], c->u[2]}};
+    const unsigned nb = 152 * 16;
+    k_init_cells<<<nb, 256, 0, c->s>>>(c->N, c->type, U, c->desc.u_inf[0], c->desc.u_inf[1], c->desc.u_inf[2],
+                                      c->ndim, c->p);
+    IBM_LAUNCHED(c);
+    int passes = 0;
+    IBM_TRY(ghost_refresh_all(c, c->u, &passes));
+    IBM_TRY(faces_from(c, c->u));
+    c->nstep = 0;
+    c->have_nold = false;
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
+// Helmholtz solve for component q, u = ustar (initial guess u^n)
+static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
+    const BCInfo bc = make_bc(c);
+    const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    double *u = c->ustar[q];
+    const double *rhs = c->rhs[q];
+    const int check_every = 4;
+    *sweeps = 0;
+    double rhs2 = -1.0;
+    const unsigned gb = (unsigned)((c->ng + 255) / 256);
+    Fields3 U{{u, u, u}};
+    for (int it = 0; it < c->opts.helm_maxit; ++it) {
+        k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 0);
+        k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 1);
+        IBM_LAUNCHED(c);
+        if (c->ng > 0) {
+            k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
+            k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
+            IBM_LAUNCHED(c);
+        }
+        ++*sweeps;
+        if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
+            k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, c->part);
+            IBM_LAUNCHED(c);
+            IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 48));
+            double gmax = 0.0;
+            if (c->ng > 0) {
+                // ghost-row residual: largest change a further Jacobi pass would make
+                k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
+                k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
+                IBM_LAUNCHED(c);
+            }
+            IBM_TRY(sync_scalars(c, 51));
+            const double r2 = c->hscal[48];
+            if (rhs2 < 0) rhs2 = c->hscal[49];
+            if (c->ng > 0) gmax = c->hscal[50];
+            if (!isfinite(r2)) return c->fail(IBM_ERR_DIVERGED, "Helmholtz residual is not finite");
+            const double bn = sqrt(rhs2) > 0 ? sqrt(rhs2) : 1.0;
+            double scale = 1.0;
+            for (int a = 0; a < 3; ++a) scale = fmax(scale, fabs(c->desc.u_inf[a]));
+            if (sqrt(r2) <= c->opts.helm_rtol * bn && gmax <= c->opts.helm_rtol * scale) return IBM_OK;
+        }
+    }
+    return IBM_ERR_NOT_CONVERGED;
+}
+
+ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
+    const int nc = c->ndim;
+    const double dt = c->desc.dt, alpha = dt / (2.0 * c->desc.Re);
+    IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
+    CFields3 u{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    CFields3 F{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
+    CFields3 No{{c->Nold[0], c->Nold[1], nc == 3 ? c->Nold[2] : c->Nold[1]}};
+    Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
+    Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
+    k_conv_rhs<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
+                                           alpha, nc);
+    IBM_LAUNCHED(c);
+    ibm_status status = IBM_OK;
+    int sweeps_total = 0;
+    for (int q = 0; q < nc; ++q) {
+        IBM_CUDA(c, cudaMemcpyAsync(c->ustar[q], c->u[q], sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->s));
+        int sw = 0;
+        ibm_status s = helmholtz(c, q, &sw);
+        sweeps_total += sw;
+        if (s == IBM_ERR_NOT_CONVERGED) status = s;
+        else if (s != IBM_OK) return s;
+    }
+    IBM_TRY(faces_from(c, c->ustar));
+    CFields3 Fs{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
+    double *braw = c->rhs[0];
+    k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
+    IBM_LAUNCHED(c);
+    IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
+    ibm_solve_stats ps{};
+    ibm_status s = poisson_solve(c, braw, c->p, c->opts.rtol, c->opts.max_outer, &ps);
+    if (s == IBM_ERR_NOT_CONVERGED) status = s;
+    else if (s != IBM_OK) return s;
+    IBM_CUDA(c, cudaEventRecord(c->ev3, c->s));
+    for (int a = 0; a < nc; ++a) {
+        const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
+        const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
+        k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
+    }
+    IBM_LAUNCHED(c);
+    CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
+    Fields3 un{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    k_project_cells<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
+    IBM_LAUNCHED(c);
+    int passes = 0;
+    IBM_TRY(ghost_refresh_all(c, c->u, &passes));
+    for (int q = 0; q < 3; ++q) {
+        double *t = c->Nold[q];
+        c->Nold[q] = c->Nnew[q];
+        c->Nnew[q] = t;
+    }
+    c->have_nold = true;
+    c->nstep += 1;
+    IBM_CUDA(c, cudaEventRecord(c->ev1, c->s));
+    IBM_CUDA(c, cudaEventSynchronize(c->ev1));
+    if (st) {
+        float a = 0, b = 0, t = 0;
+        cudaEventElapsedTime(&t, c->ev0, c->ev1);
+        cudaEventElapsedTime(&a, c->ev0, c->ev2);
+        cudaEventElapsedTime(&b, c->ev3, c->ev1);
+        st->steps += 1;
+        st->poisson_outer += ps.outer_iters;
+        st->poisson_inner += ps.inner_iters;
+        st->helm_sweeps += sweeps_total;
+        st->rel_residual = ps.rel_residual;
+        st->ms_total += t;
+        st->ms_predictor += a;
+        st->ms_poisson += ps.ms;
+        st->ms_projection += b;
+    }
+    if (status == IBM_ERR_NOT_CONVERGED) c->fail(status, "a solve in the step reached its iteration limit");
+    return status;
+}
+
+// max |div U - mean| over FLUID cells of the current face field
+ibm_status div_stat(Ctx *c, double *out) {
+    CFields3 F{{c->F[0], c->F[1], c->ndim == 3 ? c->F[2] : c->F[1]}};
+    double *d = c->rhs[1];
+    k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, F, 1.0, d);
+    IBM_LAUNCHED(c);
+    IBM_TRY(fluid_mean(c, d, false, nullptr));
+    k_div_stats<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, d, c->scal + 5, c->part);
+    k_max_final<<<1, 256, 0, c->s>>>(c->part, RED_BLOCKS, c->scal + 52);
+    IBM_LAUNCHED(c);
+    IBM_TRY(sync_scalars(c, 53));
+    *out = c->hscal[52];
+    return IBM_OK;
+}
+
+}  // namespace ibm

@@ -1,0 +1,337 @@
+"""Thin ctypes binding of libibm.so (include/ibm.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the solver runs in the
+library's CUDA kernels. PyTorch supplies the device memory (the library's
+allocator hooks call PyTorch's caching allocator) and the CUDA stream. The
+library must be built (``paper_2505_17287_gb300.build.build()``); importing
+this module without it fails loudly, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (CFUNCTYPE, POINTER, Structure, byref, c_char_p, c_double, c_int, c_int64,
+                    c_size_t, c_uint8, c_void_p)
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibm.so")
+
+IBM_OK, IBM_ERR_ARG, IBM_ERR_OOM, IBM_ERR_CUDA, IBM_ERR_MESH = 0, 1, 2, 3, 4
+IBM_ERR_STATE, IBM_ERR_NOT_CONVERGED, IBM_ERR_DIVERGED, IBM_ERR_TIMEOUT = 5, 6, 7, 8
+STATUS_NAMES = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_OOM", 3: "IBM_ERR_CUDA", 4: "IBM_ERR_MESH",
+                5: "IBM_ERR_STATE", 6: "IBM_ERR_NOT_CONVERGED", 7: "IBM_ERR_DIVERGED", 8: "IBM_ERR_TIMEOUT"}
+IBM_FLUID, IBM_GHOST, IBM_DEAD = 0, 1, 2
+IBM_BC_INFLOW, IBM_BC_OUTFLOW, IBM_BC_SLIP = 0, 1, 2
+IBM_FP64, IBM_MIXED = 0, 1
+FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "face_u": 4, "face_v": 5, "face_w": 6, "nold_u": 7, "nold_v": 8,
+          "nold_w": 9, "type": 10, "ustar_u": 11, "ustar_v": 12, "ustar_w": 13, "rhs": 14, "step": 15}
+
+ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+FREE_FN = CFUNCTYPE(None, c_void_p, c_void_p)
+
+
+class ibm_grid_desc(Structure):
+    _fields_ = [("ndim", c_int), ("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("xf", c_void_p), ("yf", c_void_p), ("zf", c_void_p),
+                ("Re", c_double), ("dt", c_double), ("u_inf", c_double * 3), ("bc", c_int * 6),
+                ("precision", c_int), ("stream", c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", c_void_p)]
+
+
+class ibm_solver_opts(Structure):
+    _fields_ = [("rtol", c_double), ("max_outer", c_int), ("restart", c_int), ("inner_iters", c_int),
+                ("nu1", c_int), ("nu2", c_int), ("coarse_sweeps", c_int), ("helm_rtol", c_double),
+                ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int)]
+
+
+class ibm_table_info(Structure):
+    _fields_ = [("n_fluid", c_int64), ("n_ghost", c_int64), ("n_dead", c_int64), ("n_kind", c_int64 * 3)]
+
+
+class ibm_solve_stats(Structure):
+    _fields_ = [("outer_iters", c_int), ("inner_iters", c_int), ("rel_residual", c_double),
+                ("lambda_est", c_double), ("ms", c_double)]
+
+
+class ibm_step_stats(Structure):
+    _fields_ = [("steps", c_int), ("poisson_outer", c_int), ("poisson_inner", c_int), ("helm_sweeps", c_int),
+                ("rel_residual", c_double), ("max_div", c_double), ("ms_total", c_double),
+                ("ms_predictor", c_double), ("ms_poisson", c_double), ("ms_projection", c_double)]
+
+
+class ibm_tables_host(Structure):
+    _fields_ = [(n, c_void_p) for n in ("type", "gidx", "bi", "nrm", "ip", "dist", "base", "kind", "cmask",
+                                        "sidx", "wv", "wp", "bv", "bp")]
+
+
+EXPORTS = ["ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
+           "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
+           "ibm_destroy", "ibm_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libibm.so and declare the signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run paper_2505_17287_gb300.build.build() on a machine "
+                           "with nvcc; there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    P = c_void_p
+    L.ibm_default_opts.argtypes = [POINTER(ibm_solver_opts)]
+    L.ibm_create_grid.argtypes = [POINTER(ibm_grid_desc), POINTER(c_void_p)]
+    L.ibm_set_opts.argtypes = [P, POINTER(ibm_solver_opts)]
+    L.ibm_set_body.argtypes = [P, P, c_int64, P, c_int64]
+    L.ibm_classify_cells.argtypes = [P, POINTER(ibm_table_info)]
+    L.ibm_step.argtypes = [P, c_int, POINTER(ibm_step_stats)]
+    L.ibm_poisson_solve.argtypes = [P, P, P, c_double, c_int, POINTER(ibm_solve_stats)]
+    L.ibm_get_tables.argtypes = [P, POINTER(ibm_tables_host)]
+    L.ibm_get_field.argtypes = [P, c_int, P, c_int, c_size_t]
+    L.ibm_set_field.argtypes = [P, c_int, P, c_int, c_size_t]
+    L.ibm_sizes.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
+    L.ibm_destroy.argtypes = [P]
+    L.ibm_last_error.argtypes = [P]
+    L.ibm_last_error.restype = c_char_p
+    for name in EXPORTS:
+        if name != "ibm_last_error":
+            getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+class IBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _p(a):
+    return a.ctypes.data_as(c_void_p)
+
+
+def _check(status, ctx=None, ok=(IBM_OK,)):
+    if status not in ok:
+        msg = load_library().ibm_last_error(ctx)
+        raise IBMError(status, msg.decode() if msg else "")
+    return status
+
+
+# --------------------------------------------------------------------------
+# C-ABI names
+# --------------------------------------------------------------------------
+
+def ibm_default_opts():
+    o = ibm_solver_opts()
+    _check(load_library().ibm_default_opts(byref(o)))
+    return o
+
+
+def ibm_create_grid(desc: ibm_grid_desc):
+    ctx = c_void_p()
+    _check(load_library().ibm_create_grid(byref(desc), byref(ctx)))
+    return ctx
+
+
+def ibm_set_opts(ctx, opts: ibm_solver_opts):
+    return _check(load_library().ibm_set_opts(ctx, byref(opts)), ctx)
+
+
+def ibm_set_body(ctx, verts: np.ndarray, elems: np.ndarray):
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    e = np.ascontiguousarray(elems, dtype=np.int32)
+    return _check(load_library().ibm_set_body(ctx, _p(v), v.shape[0], _p(e), e.shape[0]), ctx)
+
+
+def ibm_classify_cells(ctx):
+    info = ibm_table_info()
+    _check(load_library().ibm_classify_cells(ctx, byref(info)), ctx)
+    return info
+
+
+def ibm_step(ctx, nsteps: int):
+    st = ibm_step_stats()
+    status = _check(load_library().ibm_step(ctx, nsteps, byref(st)), ctx, ok=(IBM_OK, IBM_ERR_NOT_CONVERGED))
+    return st, status
+
+
+def ibm_poisson_solve(ctx, rhs_ptr: int, phi_ptr: int, rtol: float = 0.0, maxit: int = 0):
+    st = ibm_solve_stats()
+    status = _check(load_library().ibm_poisson_solve(ctx, c_void_p(rhs_ptr), c_void_p(phi_ptr), rtol, maxit,
+                                                     byref(st)), ctx, ok=(IBM_OK, IBM_ERR_NOT_CONVERGED))
+    return st, status
+
+
+def ibm_get_tables(ctx, dst: ibm_tables_host):
+    return _check(load_library().ibm_get_tables(ctx, byref(dst)), ctx)
+
+
+def ibm_get_field(ctx, field: int, dst_ptr: int, is_device: int, nbytes: int):
+    return _check(load_library().ibm_get_field(ctx, field, c_void_p(dst_ptr), is_device, nbytes), ctx)
+
+
+def ibm_set_field(ctx, field: int, src_ptr: int, is_device: int, nbytes: int):
+    return _check(load_library().ibm_set_field(ctx, field, c_void_p(src_ptr), is_device, nbytes), ctx)
+
+
+def ibm_sizes(ctx):
+    n, g = c_int64(), c_int64()
+    _check(load_library().ibm_sizes(ctx, byref(n), byref(g)), ctx)
+    return n.value, g.value
+
+
+def ibm_destroy(ctx):
+    return _check(load_library().ibm_destroy(ctx))
+
+
+def ibm_last_error(ctx=None):
+    m = load_library().ibm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper used by the tests and the benchmark
+# --------------------------------------------------------------------------
+
+class Solver:
+    """One grid context. `case` is a paper_2505_17287_gb300.synth.Case (or any
+    object with ndim, xf, yf, zf, Re, dt, u_inf). Device memory comes from
+    PyTorch's caching allocator; work runs on `stream` (default: PyTorch's
+    current stream of cuda:0)."""
+
+    def __init__(self, case, precision=IBM_FP64, bc=(0, 1, 2, 2, 2, 2), stream=None, torch_alloc=True):
+        import torch
+        self._torch = torch
+        load_library()
+        self.case = case
+        self.ndim = case.ndim
+        nx, ny = len(case.xf) - 1, len(case.yf) - 1
+        nz = len(case.zf) - 1 if case.ndim == 3 else 1
+        self.shape = (nz, ny, nx)
+        self._xf = np.ascontiguousarray(case.xf, dtype=np.float64)
+        self._yf = np.ascontiguousarray(case.yf, dtype=np.float64)
+        self._zf = np.ascontiguousarray(case.zf if case.ndim == 3 else [0.0, 1.0], dtype=np.float64)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        d = ibm_grid_desc()
+        d.ndim, d.nx, d.ny, d.nz = case.ndim, nx, ny, nz
+        d.xf, d.yf, d.zf = _p(self._xf), _p(self._yf), _p(self._zf)
+        d.Re, d.dt = float(case.Re), float(case.dt)
+        d.u_inf = (c_double * 3)(*[float(x) for x in case.u_inf])
+        d.bc = (c_int * 6)(*bc)
+        d.precision = precision
+        d.stream = c_void_p(self.stream.cuda_stream)
+        if torch_alloc:
+            st = self.stream
+
+            def _alloc(nbytes, _ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+
+            def _free(ptr, _ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+            d.alloc, d.free = self._hooks
+        self.ctx = ibm_create_grid(d)
+        self.N = nx * ny * nz
+        self.info = None
+
+    # lifecycle --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            ibm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opts(self, **kw):
+        o = ibm_default_opts() if not hasattr(self, "_opts") else self._opts
+        for k, v in kw.items():
+            setattr(o, k, v)
+        ibm_set_opts(self.ctx, o)
+        self._opts = o
+        return o
+
+    def set_body(self, verts, elems):
+        return ibm_set_body(self.ctx, verts, elems)
+
+    def classify(self):
+        self.info = ibm_classify_cells(self.ctx)
+        return dict(n_fluid=self.info.n_fluid, n_ghost=self.info.n_ghost, n_dead=self.info.n_dead,
+                    n_kind=list(self.info.n_kind))
+
+    def step(self, n=1):
+        st, status = ibm_step(self.ctx, n)
+        out = {k: getattr(st, k) for k, _ in ibm_step_stats._fields_}
+        out["status"] = status
+        return out
+
+    def poisson_solve(self, rhs, phi, rtol=0.0, maxit=0):
+        """rhs, phi: torch float64 CUDA tensors with N elements."""
+        torch = self._torch
+        assert rhs.is_cuda and phi.is_cuda and rhs.dtype == torch.float64 and phi.dtype == torch.float64
+        assert rhs.numel() == self.N and phi.numel() == self.N and rhs.is_contiguous() and phi.is_contiguous()
+        st, status = ibm_poisson_solve(self.ctx, rhs.data_ptr(), phi.data_ptr(), rtol, maxit)
+        out = {k: getattr(st, k) for k, _ in ibm_solve_stats._fields_}
+        out["status"] = status
+        return out
+
+    # host access -------------------------------------------------------------
+    def tables(self):
+        n, ng = ibm_sizes(self.ctx)
+        t = dict(type=np.zeros(n, np.uint8), gidx=np.zeros(ng, np.int64), bi=np.zeros((ng, 3)),
+                 nrm=np.zeros((ng, 3)), ip=np.zeros((ng, 3)), dist=np.zeros(ng), base=np.zeros(ng, np.int64),
+                 kind=np.zeros(ng, np.uint8), cmask=np.zeros(ng, np.uint8), sidx=np.zeros((ng, 8), np.int64),
+                 wv=np.zeros((ng, 8)), wp=np.zeros((ng, 8)), bv=np.zeros(ng), bp=np.zeros(ng))
+        h = ibm_tables_host(**{k: _p(v) for k, v in t.items()})
+        ibm_get_tables(self.ctx, h)
+        t["type"] = t["type"].reshape(self.shape)
+        return t
+
+    def field_size(self, name):
+        nz, ny, nx = self.shape
+        if name == "face_u":
+            return (nz, ny, nx + 1)
+        if name == "face_v":
+            return (nz, ny + 1, nx)
+        if name == "face_w":
+            return (nz + 1, ny, nx)
+        return self.shape
+
+    def get(self, name):
+        if name == "step":
+            v = np.zeros(1, np.int64)
+            ibm_get_field(self.ctx, FIELDS[name], v.ctypes.data, 0, 8)
+            return int(v[0])
+        dt = np.uint8 if name == "type" else np.float64
+        a = np.zeros(self.field_size(name), dt)
+        ibm_get_field(self.ctx, FIELDS[name], a.ctypes.data, 0, a.nbytes)
+        return a
+
+    def set(self, name, arr):
+        if name == "step":
+            v = np.array([int(arr)], np.int64)
+            return ibm_set_field(self.ctx, FIELDS[name], v.ctypes.data, 0, 8)
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.field_size(name))
+        return ibm_set_field(self.ctx, FIELDS[name], a.ctypes.data, 0, a.nbytes)
+
+    def state_names(self):
+        names = ["u", "v", "p", "face_u", "face_v", "nold_u", "nold_v"]
+        if self.ndim == 3:
+            names += ["w", "face_w", "nold_w"]
+        return names + ["step"]
+
+    def get_state(self):
+        return {k: self.get(k) for k in self.state_names()}
+
+    def set_state(self, st):
+        for k in self.state_names():
+            self.set(k, st[k])

@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every function that include/ibm.h declares, and the ctypes
+structures of the binding have the C layout (sizes and field offsets
+printed by a C program compiled against the header)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ibm.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ibm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_17287_gb300 import build
+    build.build()
+    from paper_2505_17287_gb300 import ibm
+    return ibm.load_library()
+
+
+def test_exports_every_declared_function(lib):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2505_17287_gb300", "libibm.so")],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (ibm_\w+)", out))
+    assert set(names) <= exported
+    from paper_2505_17287_gb300 import ibm
+    assert set(ibm.EXPORTS) == set(names)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    from paper_2505_17287_gb300 import ibm
+    structs = {"ibm_grid_desc": ibm.ibm_grid_desc, "ibm_solver_opts": ibm.ibm_solver_opts,
+               "ibm_table_info": ibm.ibm_table_info, "ibm_solve_stats": ibm.ibm_solve_stats,
+               "ibm_step_stats": ibm.ibm_step_stats, "ibm_tables_host": ibm.ibm_tables_host}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for s, cls in structs.items():
+        lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-o", str(exe), str(c)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for s, cls in structs.items():
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
+
+
+def test_create_rejects_bad_descriptor_without_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_2505_17287_gb300 import ibm
+    d = ibm.ibm_grid_desc()
+    d.ndim = 4
+    ctx = ctypes.c_void_p()
+    assert lib.ibm_create_grid(ctypes.byref(d), ctypes.byref(ctx)) == ibm.IBM_ERR_ARG
+    assert ctx.value is None
+    assert b"ndim" in lib.ibm_last_error(None)
+    assert lib.ibm_destroy(None) == ibm.IBM_OK
+    o = ibm.ibm_solver_opts()
+    assert lib.ibm_default_opts(ctypes.byref(o)) == ibm.IBM_OK
+    assert o.rtol == 1e-10 and o.restart == 8
