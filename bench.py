@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the ghost-cell immersed-boundary fractional step on GB300.
+
+Workload (default): the 3D finite-wing case - NACA0012 section, chord 1,
+aspect ratio 2, square tips, 15 degrees incidence, ~20k-triangle surface,
+stretched 384x256x256 grid (25.2M cells), Re 1000, dt 0.002, Poisson solved
+to a 1e-10 relative residual - in FP64, with the mixed-precision Poisson
+path measured on the same state beside it. Inputs are synthetic (seeded
+generators); every field is resident in HBM during the timed steps, and the
+25.2M-cell FP64 fields (201 MB each) exceed the 129 MB L2, so no L2 flush is
+needed between steps.
+
+One bench "step" = one fractional step of the whole grid (predictor,
+Poisson solve, projection, ghost refresh) through ibm_step.
+
+Multi-GPU: the solver does not shard across GPUs (one grid per GPU); with
+N > 1 every rank runs an independent replica of the workload ("replicas
+only"), value = cells * steps * N / max-over-ranks time.
+
+--impl reference times the CPU oracle (the plain FP64 reference of the
+method) on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s per GB300, mixed vs FP64 at 1e-10 residual; serve p50/p99 latency"
+UNIT = "Mcell-steps/s"
+
+# algorithmic bytes per cell of one launch of the timed kernels
+# (FP64 s = 8, FP32 s = 4, cell type 1 byte); see the design notes
+def rbgs_pass_bytes(ncells, s, stored_coeffs=True):
+    # one colour pass: read all x (neighbours), read f and write x for half
+    # the cells, plus the operator: stored face coefficients (3 arrays) and
+    # the diagonal of the updated half
+    b = ncells * s * (1.0 + 0.5 + 0.5)
+    if stored_coeffs:
+        b += ncells * s * (3.0 + 0.5)
+    return b
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--size", default="384,256,256", help="nx,ny,nz of the wing grid")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-kernels", action="store_true", help="also report every timed kernel")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def wing_case(size):
+    from paper_2505_17287_gb300 import synth
+    nx, ny, nz = (int(x) for x in size.split(","))
+    return synth.wing_case(nx, ny, nz)
+
+
+def run_reference(args):
+    """CPU oracle on a bounded sample of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from oracle import flow, geom
+    from paper_2505_17287_gb300 import synth
+    case = synth.wing_case(32, 24, 24)
+    cores = 1
+    T = geom.body_tables(3, case.xf, case.yf, case.zf, case.verts, case.elems)
+    g = flow.Grid(3, case.xf, case.yf, case.zf)
+    per = []
+    nrep = max(1, min(args.steps, 3))
+    for r in range(nrep):
+        t0 = time.perf_counter()
+        flow.run(g, T["type"], T, 2, case.Re, case.dt)
+        per.append(time.perf_counter() - t0)
+    val = g.N * 2 / statistics.median(per) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": nrep, "warmup": 0, "ms_per_step": statistics.median(per) * 1e3 / 2,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "wing NACA0012 AR2 15deg, oracle sample 32x24x24",
+                                            "full_workload": "384x256x256 stretched, Re 1000, dt 0.002"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "plain FP64 oracle (sparse direct solves), wing case on a 32x24x24 grid "
+                                       "(18,432 cells), 2 fractional steps per run including the matrix "
+                                       "factorisations, median of runs"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    from oracle import flow, geom
+    from paper_2505_17287_gb300 import synth
+    case = synth.wing_case(32, 24, 24)
+    T = geom.body_tables(3, case.xf, case.yf, case.zf, case.verts, case.elems)
+    g = flow.Grid(3, case.xf, case.yf, case.zf)
+    t0 = time.perf_counter()
+    flow.run(g, T["type"], T, 2, case.Re, case.dt)
+    dt = time.perf_counter() - t0
+    return {"value": g.N * 2 / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "plain FP64 oracle (sparse direct solves), wing case on a 32x24x24 grid (18,432 cells), "
+                      "one run of 2 fractional steps including the matrix factorisations"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2505_17287_gb300 import build, ibm
+    if rank == 0 or not os.path.exists(ibm.LIB_PATH):
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    case = wing_case(args.size)
+    stream = torch.cuda.current_stream()
+    s = ibm.Solver(case, precision=ibm.IBM_FP64)
+    t0 = time.perf_counter()
+    s.set_body(case.verts, case.elems)
+    info = s.classify()
+    setup_s = time.perf_counter() - t0
+    N = s.N
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def timed(nsteps, kernel_timer=False):
+        if kernel_timer:
+            ibm.ibm_kernel_timer(s.ctx, 1)
+        sync_all()
+        l0 = ibm.ibm_launch_count(s.ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = []
+        for _ in range(nsteps):
+            stats.append(s.step(1))
+        e1.record(stream)
+        sync_all()
+        ms = e0.elapsed_time(e1)
+        launches = ibm.ibm_launch_count(s.ctx) - l0
+        kt = {}
+        if kernel_timer:
+            for name, kid in ibm.KERNEL_IDS.items():
+                kt[name] = ibm.ibm_kernel_time(s.ctx, kid)
+            ibm.ibm_kernel_timer(s.ctx, 0)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, launches, kt
+
+    for _ in range(args.warmup):
+        s.step(1)
+    saved = s.get_state() if not args.no_mixed else None
+    with Clocks(local) as clk:
+        ms, stats, launches, _ = timed(args.steps)
+    clocks = clk.summary()
+    value = N * args.steps * world / (ms / 1e3) / 1e6
+    poisson_ms64 = sum(x["ms_poisson"] for x in stats)
+    # roofline of the dominant kernel: a second pass over the same number of
+    # steps with the event timer on (the timer adds host work per launch, so
+    # the headline above is measured without it)
+    ms_kt, stats_kt, _, kt = timed(args.steps, kernel_timer=True)
+    rb_ms, rb_n = kt["rbgs0"]
+    rb_bytes = rbgs_pass_bytes(N, 8)
+    achieved = rb_bytes / (rb_ms / rb_n / 1e3) / 1e9 if rb_n else None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"wing NACA0012 AR2 15deg, stretched {args.size.replace(',', 'x')} grid "
+                               f"({N} cells), Re 1000, dt 0.002, Poisson rtol 1e-10, FP64",
+                   "cells": N, "n_ghost": info["n_ghost"], "n_dead": info["n_dead"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": "k_rbgs<double> (finest level, one colour pass)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                     "launches": rb_n, "avg_ms": rb_ms / rb_n if rb_n else None,
+                     "algorithmic_bytes_per_launch": rb_bytes},
+        "stats": {"setup_s": setup_s, "poisson_outer_per_step": sum(x["poisson_outer"] for x in stats) / args.steps,
+                  "poisson_inner_per_step": sum(x["poisson_inner"] for x in stats) / args.steps,
+                  "helm_sweeps_per_step": sum(x["helm_sweeps"] for x in stats) / args.steps,
+                  "rel_residual_last": stats[-1]["rel_residual"],
+                  "ms_poisson_per_step": poisson_ms64 / args.steps,
+                  "ms_predictor_per_step": sum(x["ms_predictor"] for x in stats) / args.steps},
+    }
+    if args.profile_kernels:
+        result["kernels"] = {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()}
+        result["kernels_step_ms"] = ms_kt / args.steps
+    if not args.no_mixed:
+        s.set_state(saved)
+        s.set_opts(precision=ibm.IBM_MIXED)
+        ms_m, stats_m, _, _ = timed(args.steps)
+        poisson_ms32 = sum(x["ms_poisson"] for x in stats_m)
+        result["mixed"] = {"value": N * args.steps * world / (ms_m / 1e3) / 1e6, "unit": UNIT,
+                           "ms_per_step": ms_m / args.steps,
+                           "poisson_ms_per_step": poisson_ms32 / args.steps,
+                           "poisson_speedup_vs_fp64": poisson_ms64 / poisson_ms32 if poisson_ms32 else None,
+                           "step_speedup_vs_fp64": ms / ms_m,
+                           "poisson_outer_per_step": sum(x["poisson_outer"] for x in stats_m) / args.steps,
+                           "rel_residual_last": stats_m[-1]["rel_residual"],
+                           "same_inputs": "both runs start from the same saved state"}
+        s.set_opts(precision=ibm.IBM_FP64)
+    if not args.no_e2e:
+        # end to end through the C ABI with pinned host buffers: every step
+        # copies its input state host->device, steps, and reads u, v, w, p back
+        names_in = ["u", "v", "w", "p", "face_u", "face_v", "face_w", "nold_u", "nold_v", "nold_w"]
+        names_out = ["u", "v", "w", "p"]
+        st = s.get_state()
+        host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in names_in}
+        host_out = {k: torch.empty(host_in[k].shape, dtype=torch.float64).pin_memory() for k in names_out}
+        h2d = sum(t.numel() * 8 for t in host_in.values()) + 8
+        d2h = sum(t.numel() * 8 for t in host_out.values())
+        ne2e = max(1, min(args.steps, 5))
+        sync_all()
+        t0 = time.perf_counter()
+        for _ in range(ne2e):
+            for k in names_in:
+                ibm.ibm_set_field(s.ctx, ibm.FIELDS[k], host_in[k].data_ptr(), 0, host_in[k].numel() * 8)
+            ibm.ibm_set_field(s.ctx, ibm.FIELDS["step"], np.array([st["step"]], np.int64).ctypes.data, 0, 8)
+            s.step(1)
+            for k in names_out:
+                ibm.ibm_get_field(s.ctx, ibm.FIELDS[k], host_out[k].data_ptr(), 0, host_out[k].numel() * 8)
+        sync_all()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        result["e2e"] = {"value": N * ne2e * world / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h, "steps": ne2e,
+                         "path": "ibm_set_field (pinned host) + ibm_step + ibm_get_field (pinned host)"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            result["cpu_baseline"] = cpu_baseline_sample()
+        except Exception as e:  # the oracle is optional on a box without it
+            result["cpu_baseline"] = {"value": None, "error": str(e)}
+    s.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -84,7 +84,7 @@ typedef struct {
 typedef struct {
     double rtol;        /* Poisson: relative residual ||P(b-A phi)||/||P b|| target */
     int max_outer;      /* Poisson: FGMRES iteration limit over all restarts */
-    int restart;        /* Poisson: FGMRES restart length (1..32) */
+    int restart;        /* Poisson: FGMRES restart length (1..16) */
     int inner_iters;    /* Poisson: MG-PCG iterations per preconditioner call */
     int nu1, nu2;       /* multigrid pre/post red-black Gauss-Seidel sweeps */
     int coarse_sweeps;  /* red-black sweep pairs on the coarsest level */
@@ -210,6 +210,23 @@ ibm_status ibm_set_field(ibm_ctx *ctx, int field, const void *src, int is_device
 
 /* Number of N-sized cells and of ghost cells (after classification). */
 ibm_status ibm_sizes(ibm_ctx *ctx, int64_t *n_cells, int64_t *n_ghost);
+
+/* Number of CUDA kernels this context has launched since creation
+   (diagnostics: lets a caller count the device work behind a call). */
+ibm_status ibm_launch_count(ibm_ctx *ctx, int64_t *count);
+
+/* Diagnostic event timer. ibm_kernel_timer(ctx, 1) starts recording a CUDA
+   event pair on the context stream around every launch of the kernels
+   listed below (and clears the totals); 0 stops. ibm_kernel_time returns the
+   summed device time (ms) and the launch count of one kernel since the
+   timer was started. Kernel ids: 0 red-black Gauss-Seidel colour pass on
+   the finest multigrid level; 1 staircase-operator product on the finest
+   level; 2 full ghost-cell pressure operator; 3 FGMRES multi-dot; 4 FGMRES
+   orthogonalisation; 5 Helmholtz colour pass; 6 convective term and
+   AB2/CN right-hand side; 7 red-black pass on coarse levels; 8 residual +
+   restriction; 9 prolongation. Recording adds host overhead per launch. */
+ibm_status ibm_kernel_timer(ibm_ctx *ctx, int enable);
+ibm_status ibm_kernel_time(ibm_ctx *ctx, int kernel, double *ms_total, int64_t *launches);
 
 /* Release every allocation of the context. NULL is accepted. */
 ibm_status ibm_destroy(ibm_ctx *ctx);

@@ -339,24 +339,43 @@ def normalise(g: Grid, typ, phi):
 
 
 def solve_poisson(g: Grid, typ, tabs, b, A=None, cache=None):
-    """Solve A phi + lam 1_FLUID = b with sum_FLUID vol phi = 0 (bordered
-    system, sparse LU). Returns (phi [nz,ny,nx], lam). `cache` (a dict) keeps
-    the factorisation of the bordered matrix between calls on one grid."""
+    """Solve A phi + lam 1_FLUID = b with sum_FLUID vol phi = 0 by sparse LU.
+
+    A is singular with the constants (on FLUID and GHOST cells) as its null
+    space. With y the left null vector (A^T y = 0), the system is consistent
+    exactly for lam = y.b / y.1_FLUID. Both y and phi come from one cell
+    pinned: the row of a reference FLUID cell r is replaced by e_r (y_r = 1
+    for A^T, phi_r = 0 for A); because the systems are consistent the
+    replaced row still holds. phi is then shifted to zero volume-weighted
+    FLUID mean. Returns (phi [nz,ny,nx], lam). `cache` (a dict) keeps the two
+    factorisations between calls on one grid."""
     t = typ.ravel()
-    lu = None if cache is None else cache.get("poisson")
-    if lu is None:
+    fac = None if cache is None else cache.get("poisson")
+    if fac is None:
         if A is None:
             A = poisson_matrix(g, typ, tabs)
-        f = (t == FLUID).astype(np.float64)
-        w = np.where(t == FLUID, g.vol.ravel(), 0.0)
-        w = w / w.sum()
-        K = sp.bmat([[A, sp.csr_matrix(f[:, None])], [sp.csr_matrix(w[None, :]), None]], format="csc")
-        lu = spla.splu(K)
+        r = int(np.nonzero(t == FLUID)[0][0])
+        def pinned(M):
+            M = M.tolil(copy=True)
+            M.rows[r] = [r]
+            M.data[r] = [1.0]
+            return spla.splu(M.tocsc())
+        luA = pinned(A)
+        luT = pinned(A.T.tocsr())
+        er = np.zeros(g.N)
+        er[r] = 1.0
+        y = luT.solve(er)
+        fac = (luA, y, r)
         if cache is not None:
-            cache["poisson"] = lu
-    rhs = np.concatenate([np.where(t == DEAD, 0.0, b.ravel()), [0.0]])
-    x = lu.solve(rhs)
-    return x[:-1].reshape(g.shape), float(x[-1])
+            cache["poisson"] = fac
+    luA, y, r = fac
+    bb = np.where(t == DEAD, 0.0, b.ravel())
+    f = (t == FLUID).astype(np.float64)
+    lam = float(y @ bb) / float(y @ f)
+    rhs = bb - lam * f
+    rhs[r] = 0.0
+    phi = luA.solve(rhs).reshape(g.shape)
+    return normalise(g, typ, phi), lam
 
 
 # ---------------------------------------------------------------------------

@@ -40,6 +40,34 @@ void dev_free(Ctx *c, void *p) {
     else cudaFree(p);
 }
 
+void kt_begin(Ctx *c, int id) {
+    if (!c->kt.on) return;
+    if (c->kt.used + 2 > (int)c->kt.pool.size()) kt_flush(c);
+    cudaEventRecord(c->kt.pool[c->kt.used], c->s);
+    c->kt.ids[c->kt.used / 2] = id;
+}
+
+void kt_end(Ctx *c, int id) {
+    (void)id;
+    if (!c->kt.on) return;
+    cudaEventRecord(c->kt.pool[c->kt.used + 1], c->s);
+    c->kt.used += 2;
+}
+
+ibm_status kt_flush(Ctx *c) {
+    if (c->kt.used == 0) return IBM_OK;
+    IBM_CUDA(c, cudaEventSynchronize(c->kt.pool[c->kt.used - 1]));
+    for (int q = 0; q < c->kt.used; q += 2) {
+        float ms = 0.f;
+        IBM_CUDA(c, cudaEventElapsedTime(&ms, c->kt.pool[q], c->kt.pool[q + 1]));
+        const int id = c->kt.ids[q / 2];
+        c->kt.ms[id] += ms;
+        c->kt.n[id] += 1;
+    }
+    c->kt.used = 0;
+    return IBM_OK;
+}
+
 }  // namespace ibm
 
 static void release_all(Ctx *c) {
@@ -50,6 +78,7 @@ static void release_all(Ctx *c) {
     cudaEvent_t ev[4] = {c->ev0, c->ev1, c->ev2, c->ev3};
     for (auto e : ev)
         if (e) cudaEventDestroy(e);
+    for (auto e : c->kt.pool) cudaEventDestroy(e);
 }
 
 extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
@@ -499,6 +528,33 @@ extern "C" ibm_status ibm_sizes(ibm_ctx *c, int64_t *n_cells, int64_t *n_ghost) 
     if (!c) return IBM_ERR_ARG;
     if (n_cells) *n_cells = c->N;
     if (n_ghost) *n_ghost = c->ng;
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_kernel_timer(ibm_ctx *c, int enable) {
+    if (!c) return IBM_ERR_ARG;
+    IBM_TRY(kt_flush(c));
+    if (enable && c->kt.pool.empty()) {
+        c->kt.pool.resize(4096);
+        c->kt.ids.resize(2048);
+        for (auto &e : c->kt.pool) IBM_CUDA(c, cudaEventCreate(&e));
+    }
+    c->kt.on = enable != 0;
+    for (int q = 0; q < K_NKERNELS; ++q) { c->kt.ms[q] = 0.0; c->kt.n[q] = 0; }
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_kernel_time(ibm_ctx *c, int kernel, double *ms_total, int64_t *launches) {
+    if (!c || !ms_total || !launches || kernel < 0 || kernel >= K_NKERNELS) return IBM_ERR_ARG;
+    IBM_TRY(kt_flush(c));
+    *ms_total = c->kt.ms[kernel];
+    *launches = c->kt.n[kernel];
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_launch_count(ibm_ctx *c, int64_t *count) {
+    if (!c || !count) return IBM_ERR_ARG;
+    *count = c->nlaunch;
     return IBM_OK;
 }
 

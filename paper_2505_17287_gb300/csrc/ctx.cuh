@@ -22,8 +22,35 @@ struct LevelGeom {
     std::vector<double> xf, yf, zf;
 };
 
+// kernel ids of the diagnostic event timer
+enum KernelId {
+    K_RBGS0 = 0,      // red-black Gauss-Seidel colour pass, finest level
+    K_SPMV0 = 1,      // staircase operator product + dot, finest level
+    K_APPLY_A = 2,    // full ghost-cell pressure operator
+    K_MDOT = 3,       // FGMRES multi-dot
+    K_ORTH = 4,       // FGMRES orthogonalisation update
+    K_HELM = 5,       // Crank-Nicolson Helmholtz colour pass
+    K_CONV = 6,       // convective term + AB2/CN right-hand side
+    K_RBGS_C = 7,     // red-black colour pass, coarse levels
+    K_RESTRICT = 8,   // residual + restriction
+    K_PROLONG = 9,    // prolongation + correction
+    K_NKERNELS = 10
+};
+
+// Records a CUDA event pair around every launch of the timed kernels on the
+// context stream; the pairs are read back at the next flush.
+struct KTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<int> ids;
+    int used = 0;
+    double ms[K_NKERNELS] = {0};
+    int64_t n[K_NKERNELS] = {0};
+};
+
 struct Ctx {
     Err err;
+    KTimer kt;
     ibm_grid_desc desc{};
     ibm_solver_opts opts{};
     cudaStream_t s = nullptr;
@@ -81,6 +108,7 @@ struct Ctx {
     MGHier<float> mg32;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    int64_t nlaunch = 0;   // kernels launched by this context so far
 
     ibm_status fail(ibm_status code, const std::string &m) {
         err.code = code;
@@ -88,6 +116,11 @@ struct Ctx {
         return code;
     }
 };
+
+// event timer (api.cu)
+void kt_begin(Ctx *c, int id);
+void kt_end(Ctx *c, int id);
+ibm_status kt_flush(Ctx *c);
 
 // solver.cu
 ibm_status mg_build(Ctx *c);

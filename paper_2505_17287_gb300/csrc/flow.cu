@@ -459,15 +459,15 @@ static ibm_status faces_from(Ctx *c, double *const *ucell) {
     for (int a = 0; a < c->ndim; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
-        k_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, ucell[a], a, bc, c->F[a]);
+        ++c->nlaunch, k_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, ucell[a], a, bc, c->F[a]);
         IBM_LAUNCHED(c);
     }
     CFields3 F{{c->F[0], c->F[1], c->F[2]}};
-    k_bnd_flux<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, F, bc, c->part);
+    ++c->nlaunch, k_bnd_flux<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, F, bc, c->part);
     IBM_LAUNCHED(c);
     IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 56));
     Fields3 Fw{{c->F[0], c->F[1], c->F[2]}};
-    k_outflow_corr<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, Fw, bc, c->scal + 56);
+    ++c->nlaunch, k_outflow_corr<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, Fw, bc, c->scal + 56);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -486,12 +486,12 @@ static ibm_status ghost_refresh_all(Ctx *c, double *const *ucell, int *passes) {
     const int check_every = 4;
     for (int it = 0; it < c->opts.ghost_maxit; ++it) {
         const int want = ((it + 1) % check_every == 0) || it + 1 == c->opts.ghost_maxit;
-        k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, want);
-        k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, want);
+        ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
         IBM_LAUNCHED(c);
         ++*passes;
         if (want) {
-            k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
+            ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
             IBM_LAUNCHED(c);
             IBM_TRY(sync_scalars(c, 41));
             const double d = c->hscal[40];
@@ -510,7 +510,7 @@ ibm_status ghost_refresh_velocity(Ctx *c, int comp, int *iters) {
 ibm_status flow_init(Ctx *c) {
     Fields3 U{{c->u[0], c->u[1], c->u[2]}};
     const unsigned nb = 152 * 16;
-    k_init_cells<<<nb, 256, 0, c->s>>>(c->N, c->type, U, c->desc.u_inf[0], c->desc.u_inf[1], c->desc.u_inf[2],
+    ++c->nlaunch, k_init_cells<<<nb, 256, 0, c->s>>>(c->N, c->type, U, c->desc.u_inf[0], c->desc.u_inf[1], c->desc.u_inf[2],
                                       c->ndim, c->p);
     IBM_LAUNCHED(c);
     int passes = 0;
@@ -534,24 +534,28 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     const unsigned gb = (unsigned)((c->ng + 255) / 256);
     Fields3 U{{u, u, u}};
     for (int it = 0; it < c->opts.helm_maxit; ++it) {
-        k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 0);
-        k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 1);
+        kt_begin(c, K_HELM);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 0);
+        kt_end(c, K_HELM);
+        kt_begin(c, K_HELM);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 1);
+        kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
-            k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
-            k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
             IBM_LAUNCHED(c);
         }
         ++*sweeps;
         if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
-            k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, c->part);
+            ++c->nlaunch, k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, c->part);
             IBM_LAUNCHED(c);
             IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 48));
             double gmax = 0.0;
             if (c->ng > 0) {
                 // ghost-row residual: largest change a further Jacobi pass would make
-                k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
-                k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
+                ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
                 IBM_LAUNCHED(c);
             }
             IBM_TRY(sync_scalars(c, 51));
@@ -577,8 +581,10 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     CFields3 No{{c->Nold[0], c->Nold[1], nc == 3 ? c->Nold[2] : c->Nold[1]}};
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
-    k_conv_rhs<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
+    kt_begin(c, K_CONV);
+    ++c->nlaunch, k_conv_rhs<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
                                            alpha, nc);
+    kt_end(c, K_CONV);
     IBM_LAUNCHED(c);
     ibm_status status = IBM_OK;
     int sweeps_total = 0;
@@ -593,7 +599,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     IBM_TRY(faces_from(c, c->ustar));
     CFields3 Fs{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
     double *braw = c->rhs[0];
-    k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
+    ++c->nlaunch, k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
     IBM_LAUNCHED(c);
     IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
     ibm_solve_stats ps{};
@@ -604,12 +610,12 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
-        k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
+        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
     }
     IBM_LAUNCHED(c);
     CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
     Fields3 un{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
-    k_project_cells<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
+    ++c->nlaunch, k_project_cells<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
     IBM_LAUNCHED(c);
     int passes = 0;
     IBM_TRY(ghost_refresh_all(c, c->u, &passes));
@@ -645,11 +651,11 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
 ibm_status div_stat(Ctx *c, double *out) {
     CFields3 F{{c->F[0], c->F[1], c->ndim == 3 ? c->F[2] : c->F[1]}};
     double *d = c->rhs[1];
-    k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, F, 1.0, d);
+    ++c->nlaunch, k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, F, 1.0, d);
     IBM_LAUNCHED(c);
     IBM_TRY(fluid_mean(c, d, false, nullptr));
-    k_div_stats<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, d, c->scal + 5, c->part);
-    k_max_final<<<1, 256, 0, c->s>>>(c->part, RED_BLOCKS, c->scal + 52);
+    ++c->nlaunch, k_div_stats<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, d, c->scal + 5, c->part);
+    ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, RED_BLOCKS, c->scal + 52);
     IBM_LAUNCHED(c);
     IBM_TRY(sync_scalars(c, 53));
     *out = c->hscal[52];

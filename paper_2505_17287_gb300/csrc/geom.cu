@@ -564,24 +564,24 @@ ibm_status geom_classify(Ctx *c) {
     const double *cen[3] = {c->xc, c->yc, c->zc};
     const int nn[3] = {c->nx, c->ny, c->nz};
     for (int a = 0; a < nd; ++a) {
-        k_quantize<<<(nn[a] + 255) / 256, 256, 0, c->s>>>(cen[a], nn[a], lo[a], s, Cq + a * nmax);
+        ++c->nlaunch, k_quantize<<<(nn[a] + 255) / 256, 256, 0, c->s>>>(cen[a], nn[a], lo[a], s, Cq + a * nmax);
         IBM_LAUNCHED(c);
     }
     // vertices: q[v*nd + a] = rint((x - lo[a]) * s)
-    k_quantize_verts<<<(unsigned)((c->nv + 255) / 256), 256, 0, c->s>>>(c->d_verts, c->nv, nd, lo[0], lo[1],
+    ++c->nlaunch, k_quantize_verts<<<(unsigned)((c->nv + 255) / 256), 256, 0, c->s>>>(c->d_verts, c->nv, nd, lo[0], lo[1],
                                                                         nd == 3 ? lo[2] : 0.0, s, vq);
     IBM_LAUNCHED(c);
     if (nd == 3) {
         dim3 grid((unsigned)c->ny, (unsigned)((c->nx + 127) / 128));
-        k_inside3d<<<grid, 128, 0, c->s>>>(c->nx, c->ny, c->nz, Cq, Cq + nmax, Cq + 2 * nmax, vq, c->ne, c->d_elems,
+        ++c->nlaunch, k_inside3d<<<grid, 128, 0, c->s>>>(c->nx, c->ny, c->nz, Cq, Cq + nmax, Cq + 2 * nmax, vq, c->ne, c->d_elems,
                                            c->inside, derr);
     } else {
         const int64_t n = (int64_t)c->nx * c->ny;
-        k_inside2d<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(c->nx, c->ny, Cq, Cq + nmax, vq, c->ne, c->d_elems,
+        ++c->nlaunch, k_inside2d<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(c->nx, c->ny, Cq, Cq + nmax, vq, c->ne, c->d_elems,
                                                                   c->inside);
     }
     IBM_LAUNCHED(c);
-    k_classify<<<(unsigned)((c->N + 255) / 256 > 152 * 64 ? 152 * 64 : (c->N + 255) / 256), 256, 0, c->s>>>(
+    ++c->nlaunch, k_classify<<<(unsigned)((c->N + 255) / 256 > 152 * 64 ? 152 * 64 : (c->N + 255) / 256), 256, 0, c->s>>>(
         c->nx, c->ny, c->nz, c->inside, c->type);
     IBM_LAUNCHED(c);
     // compaction
@@ -590,8 +590,8 @@ ibm_status geom_classify(Ctx *c) {
     int64_t *off = (int64_t *)dev_alloc(c, sizeof(int64_t) * nb);
     int64_t *tot = (int64_t *)dev_alloc(c, sizeof(int64_t) * 4);
     if (!cnt || !off || !tot) return c->fail(IBM_ERR_OOM, "compaction scratch allocation failed");
-    k_count_types<<<(unsigned)nb, 256, 0, c->s>>>(c->N, c->type, cnt);
-    k_scan_counts<<<1, 1024, 0, c->s>>>(nb, cnt, off, tot);
+    ++c->nlaunch, k_count_types<<<(unsigned)nb, 256, 0, c->s>>>(c->N, c->type, cnt);
+    ++c->nlaunch, k_scan_counts<<<1, 1024, 0, c->s>>>(nb, cnt, off, tot);
     IBM_LAUNCHED(c);
     int64_t htot[4] = {0, 0, 0, 0};
     int herr[4] = {0, 0, 0, 0};
@@ -604,19 +604,19 @@ ibm_status geom_classify(Ctx *c) {
     c->n_dead = htot[2];
     IBM_TRY(ensure_ghost_capacity(c, c->ng));
     if (c->ng > 0) {
-        k_write_ghosts<<<(unsigned)nb, CHUNK, 0, c->s>>>(c->N, c->type, off, c->gidx);
+        ++c->nlaunch, k_write_ghosts<<<(unsigned)nb, CHUNK, 0, c->s>>>(c->N, c->type, off, c->gidx);
         IBM_LAUNCHED(c);
         const unsigned gb = (unsigned)((c->ng + 127) / 128);
-        k_body_intercept<<<gb, 128, 0, c->s>>>(nd, c->nx, c->ny, c->xc, c->yc, c->zc, c->ng, c->gidx, c->d_verts,
+        ++c->nlaunch, k_body_intercept<<<gb, 128, 0, c->s>>>(nd, c->nx, c->ny, c->xc, c->yc, c->zc, c->ng, c->gidx, c->d_verts,
                                                c->ne, c->d_elems, c->bi);
         IBM_LAUNCHED(c);
         TabOut o{c->bi, c->nrm, c->ipt, c->dist, c->wv, c->wp, c->bv, c->bp, c->base, c->sidx, c->kind, c->cmask};
-        k_ghost_tables<<<(unsigned)((c->ng + 63) / 64), 64, 0, c->s>>>(nd, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
+        ++c->nlaunch, k_ghost_tables<<<(unsigned)((c->ng + 63) / 64), 64, 0, c->s>>>(nd, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
                                                                        c->dx, c->dy, c->dz, c->type, c->ng, c->gidx, o);
         IBM_LAUNCHED(c);
         unsigned long long *kc = (unsigned long long *)tot;
         IBM_CUDA(c, cudaMemsetAsync(kc, 0, sizeof(unsigned long long) * 3, c->s));
-        k_kind_counts<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->ng, c->kind, kc);
+        ++c->nlaunch, k_kind_counts<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->ng, c->kind, kc);
         IBM_LAUNCHED(c);
         unsigned long long hk[3] = {0, 0, 0};
         IBM_CUDA(c, cudaMemcpyAsync(hk, kc, sizeof(hk), cudaMemcpyDeviceToHost, c->s));

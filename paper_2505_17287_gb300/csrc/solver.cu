@@ -40,13 +40,13 @@ __global__ void k_finalize(const double *__restrict__ part, int nparts, int ncol
 }
 
 ibm_status finalize(Ctx *c, const double *part, int nparts, int ncols, double scale, double *out_dev) {
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(part, nparts, ncols, scale, out_dev);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(part, nparts, ncols, scale, out_dev);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
 
 ibm_status reduce_sum(Ctx *c, const double *partials, int nparts, double *out_dev) {
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(partials, nparts, 1, 1.0, out_dev);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(partials, nparts, 1, 1.0, out_dev);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -92,9 +92,9 @@ __global__ void k_sub_mean(int64_t n, const uint8_t *__restrict__ type, double *
 
 ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_host) {
     (void)ghosts_too;
-    k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, c->part);
+    ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, c->part);
     IBM_LAUNCHED(c);
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     if (mean_host) {
         IBM_TRY(sync_scalars(c, S_MEAN + 1));
@@ -153,15 +153,17 @@ __global__ void k_ghost_rows(GhostDev gh, const double *__restrict__ x, double s
 
 // y = P(sgn * A x + b)
 static ibm_status apply_PA(Ctx *c, const double *x, const double *b, double sgn, double *y) {
-    k_apply_A<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, b, sgn, y, c->part);
+    kt_begin(c, K_APPLY_A);
+    ++c->nlaunch, k_apply_A<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, b, sgn, y, c->part);
+    kt_end(c, K_APPLY_A);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        k_ghost_rows<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, x, sgn, y);
+        ++c->nlaunch, k_ghost_rows<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, x, sgn, y);
         IBM_LAUNCHED(c);
     }
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
-    k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, y, c->scal + S_MEAN, 0);
+    ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, y, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -519,10 +521,10 @@ static ibm_status build_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &
         M.r = nullptr;
         if (!M.tx || !M.ty || !M.tz || !H.dg[l] || (l > 0 && (!M.x || !M.f)))
             return c->fail(IBM_ERR_OOM, "multigrid level allocation failed");
-        k_level_coef<T><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, oax[l], oay[l], oaz[l], c->lhx[l], c->lhy[l],
+        ++c->nlaunch, k_level_coef<T><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, oax[l], oay[l], oaz[l], c->lhx[l], c->lhy[l],
                                                      c->lhz[l], M.tx, M.ty, M.tz);
         IBM_LAUNCHED(c);
-        k_level_diag<T><<<nblk(M.n), 256, 0, c->s>>>(M, H.dg[l]);
+        ++c->nlaunch, k_level_diag<T><<<nblk(M.n), 256, 0, c->s>>>(M, H.dg[l]);
         IBM_LAUNCHED(c);
     }
     const size_t b0 = sizeof(T) * (size_t)c->N;
@@ -548,13 +550,13 @@ ibm_status mg_build(Ctx *c) {
         oz[l] = (double *)dev_alloc(c, sizeof(double) * n);
         if (!ox[l] || !oy[l] || !oz[l]) return c->fail(IBM_ERR_OOM, "open-area allocation failed");
     }
-    k_open_area0<<<nblk(c->N), 256, 0, c->s>>>(c->g, c->type, ox[0], oy[0], oz[0]);
+    ++c->nlaunch, k_open_area0<<<nblk(c->N), 256, 0, c->s>>>(c->g, c->type, ox[0], oy[0], oz[0]);
     IBM_LAUNCHED(c);
     for (int l = 1; l < L; ++l) {
         auto &F = c->lg[l - 1];
         auto &C = c->lg[l];
         const int64_t n = (int64_t)C.nx * C.ny * C.nz;
-        k_open_area_coarsen<<<nblk(n), 256, 0, c->s>>>(F.nx, F.ny, F.nz, ox[l - 1], oy[l - 1], oz[l - 1], C.nx, C.ny,
+        ++c->nlaunch, k_open_area_coarsen<<<nblk(n), 256, 0, c->s>>>(F.nx, F.ny, F.nz, ox[l - 1], oy[l - 1], oz[l - 1], C.nx, C.ny,
                                                         C.nz, C.fx, C.fy, C.fz, ox[l], oy[l], oz[l]);
         IBM_LAUNCHED(c);
     }
@@ -562,9 +564,9 @@ ibm_status mg_build(Ctx *c) {
     else {
         for (int l = 0; l < L; ++l) {
             auto &M = c->mg64.lv[l];
-            k_level_coef<double><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
+            ++c->nlaunch, k_level_coef<double><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
                                                               c->lhy[l], c->lhz[l], M.tx, M.ty, M.tz);
-            k_level_diag<double><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg64.dg[l]);
+            ++c->nlaunch, k_level_diag<double><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg64.dg[l]);
         }
         IBM_LAUNCHED(c);
     }
@@ -573,9 +575,9 @@ ibm_status mg_build(Ctx *c) {
         else {
             for (int l = 0; l < L; ++l) {
                 auto &M = c->mg32.lv[l];
-                k_level_coef<float><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
+                ++c->nlaunch, k_level_coef<float><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
                                                                  c->lhy[l], c->lhz[l], M.tx, M.ty, M.tz);
-                k_level_diag<float><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg32.dg[l]);
+                ++c->nlaunch, k_level_diag<float><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg32.dg[l]);
             }
             IBM_LAUNCHED(c);
         }
@@ -593,7 +595,9 @@ template <typename T>
 static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col) {
     MGLevel<T> &L = H.lv[l];
     const int bx = 128;
-    k_rbgs<T><<<rows_grid(L.nx, L.ny, L.nz, 2, bx), bx, 0, c->s>>>(L, H.dg[l], f, x, col);
+    kt_begin(c, l == 0 ? K_RBGS0 : K_RBGS_C);
+    ++c->nlaunch, k_rbgs<T><<<rows_grid(L.nx, L.ny, L.nz, 2, bx), bx, 0, c->s>>>(L, H.dg[l], f, x, col);
+    kt_end(c, l == 0 ? K_RBGS0 : K_RBGS_C);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -614,8 +618,10 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         MGLevel<T> Lf = H.lv[l];
         MGLevel<T> &Cl = H.lv[l + 1];
         auto &CG = c->lg[l + 1];
-        k_resid_restrict<T><<<rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], f, x, Cl, CG.fx,
+        kt_begin(c, K_RESTRICT);
+        ++c->nlaunch, k_resid_restrict<T><<<rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], f, x, Cl, CG.fx,
                                                                                      CG.fy, CG.fz);
+        kt_end(c, K_RESTRICT);
         IBM_LAUNCHED(c);
     }
     {
@@ -636,8 +642,10 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         T *x = l == 0 ? x0 : H.lv[l].x;
         MGLevel<T> &Lf = H.lv[l];
         auto &CG = c->lg[l + 1];
-        k_prolong<T><<<rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], x, H.lv[l + 1], CG.fx, CG.fy,
+        kt_begin(c, K_PROLONG);
+        ++c->nlaunch, k_prolong<T><<<rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], x, H.lv[l + 1], CG.fx, CG.fy,
                                                                               CG.fz);
+        kt_end(c, K_PROLONG);
         IBM_LAUNCHED(c);
         for (int s = 0; s < nu2; ++s) {
             IBM_TRY(rbgs(c, H, l, f, x, 1));
@@ -656,21 +664,23 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
     IBM_CUDA(c, cudaMemsetAsync(H.px, 0, sizeof(T) * (size_t)n, c->s));
     IBM_TRY(vcycle(c, H, H.pr, H.pz));
     IBM_CUDA(c, cudaMemcpyAsync(H.pp, H.pz, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, c->s));
-    k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZ);
+    ++c->nlaunch, k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZ);
     IBM_LAUNCHED(c);
     for (int it = 0; it < iters; ++it) {
-        k_spmv_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(L0, H.dg[0], H.pp, H.pq, c->part);
-        k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_PQ);
-        k_alpha<<<1, 1, 0, c->s>>>(c->scal);
-        k_axpy2<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.px, H.pr, H.pp, H.pq, c->scal);
+        kt_begin(c, K_SPMV0);
+        ++c->nlaunch, k_spmv_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(L0, H.dg[0], H.pp, H.pq, c->part);
+        kt_end(c, K_SPMV0);
+        ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_PQ);
+        ++c->nlaunch, k_alpha<<<1, 1, 0, c->s>>>(c->scal);
+        ++c->nlaunch, k_axpy2<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.px, H.pr, H.pp, H.pq, c->scal);
         IBM_LAUNCHED(c);
         if (it + 1 < iters) {
             IBM_TRY(vcycle(c, H, H.pr, H.pz));
-            k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
-            k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZN);
-            k_beta<<<1, 1, 0, c->s>>>(c->scal);
-            k_pupd<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pp, H.pz, c->scal);
+            ++c->nlaunch, k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
+            ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZN);
+            ++c->nlaunch, k_beta<<<1, 1, 0, c->s>>>(c->scal);
+            ++c->nlaunch, k_pupd<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pp, H.pz, c->scal);
             IBM_LAUNCHED(c);
         }
     }
@@ -680,13 +690,13 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 // z = M^{-1} v : FP64 in, FP64 out
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const double *v, double *z) {
-    k_pre_in<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, v, H.pr);
+    ++c->nlaunch, k_pre_in<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     IBM_TRY(pcg(c, H, c->opts.inner_iters));
-    k_pre_out<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, H.px, z);
+    ++c->nlaunch, k_pre_out<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, H.px, z);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        k_pre_ghost<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, c->type, v, z);
+        ++c->nlaunch, k_pre_ghost<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, c->type, v, z);
         IBM_LAUNCHED(c);
     }
     return IBM_OK;
@@ -699,8 +709,8 @@ static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
 
 // ||x||^2 over all cells
 static ibm_status norm2(Ctx *c, const double *x, double *out) {
-    k_dot<double><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, x, x, c->part);
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
+    ++c->nlaunch, k_dot<double><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, x, x, c->part);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
     IBM_LAUNCHED(c);
     IBM_TRY(sync_scalars(c, S_TMP + 1));
     *out = c->hscal[S_TMP];
@@ -714,15 +724,15 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     const int m = c->opts.restart;
     IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
     // b = P rhs on FLUID rows, 0 elsewhere
-    k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, c->part);
-    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
+    ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, c->part);
+    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, c->b, c->scal + S_MEAN, 0);
+    ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, c->b, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     // GHOST rows of b are 0 (homogeneous Neumann on the body)
     if (c->ng > 0) {
-        k_zero_at<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->ng, c->gidx, c->b);
+        ++c->nlaunch, k_zero_at<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->ng, c->gidx, c->b);
         IBM_LAUNCHED(c);
     }
     double bn2;
@@ -747,7 +757,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
             if (!isfinite(rel)) { status = c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite"); break; }
             if (rel <= rtol) break;
             if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
-            k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[0], c->rr, 1.0 / beta);
+            ++c->nlaunch, k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[0], c->rr, 1.0 / beta);
             IBM_LAUNCHED(c);
             std::fill(gv.begin(), gv.end(), 0.0);
             gv[0] = beta;
@@ -761,17 +771,21 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
                 double hcol[17] = {0};
                 double wbefore2 = 0.0, wafter2 = 0.0;
                 for (int pass = 0; pass < 2; ++pass) {
-                    k_mdot<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1,
+                    kt_begin(c, K_MDOT);
+                    ++c->nlaunch, k_mdot<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1,
                                                                   c->part);
-                    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD);
+                    kt_end(c, K_MDOT);
+                    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD);
                     IBM_LAUNCHED(c);
                     IBM_TRY(sync_scalars(c, S_MD + j + 2));
                     Coef h{};
                     for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
                     wbefore2 = c->hscal[S_MD + j + 1];
-                    k_orth<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1, h,
+                    kt_begin(c, K_ORTH);
+                    ++c->nlaunch, k_orth<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1, h,
                                                                   c->part);
-                    k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
+                    kt_end(c, K_ORTH);
+                    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
                     IBM_LAUNCHED(c);
                     IBM_TRY(sync_scalars(c, S_TMP + 1));
                     wafter2 = c->hscal[S_TMP];
@@ -800,7 +814,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
                 jlast = j;
                 const double est = fabs(gv[j + 1]) / bnorm;
                 if (hn > 0.0 && j + 1 < m) {
-                    k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[j + 1], c->w, 1.0 / hn);
+                    ++c->nlaunch, k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[j + 1], c->w, 1.0 / hn);
                     IBM_LAUNCHED(c);
                 }
                 if (est <= rtol || hn == 0.0) break;
@@ -815,13 +829,13 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
             }
             Coef yc{};
             for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
-            k_xupd<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, phi, (const double *const *)c->Zdev, jlast + 1, yc);
+            ++c->nlaunch, k_xupd<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, phi, (const double *const *)c->Zdev, jlast + 1, yc);
             IBM_LAUNCHED(c);
         }
         // normalise: zero volume-weighted FLUID mean, shift ghosts too
-        k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, phi, c->part);
-        k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
-        k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, phi, c->scal + S_MEAN, 1);
+        ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, phi, c->part);
+        ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
+        ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, phi, c->scal + S_MEAN, 1);
         IBM_LAUNCHED(c);
     }
     IBM_CUDA(c, cudaEventRecord(c->ev1, c->s));

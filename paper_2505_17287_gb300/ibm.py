@@ -68,7 +68,7 @@ class ibm_tables_host(Structure):
 
 EXPORTS = ["ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
-           "ibm_destroy", "ibm_last_error"]
+           "ibm_kernel_timer", "ibm_kernel_time", "ibm_launch_count", "ibm_destroy", "ibm_last_error"]
 
 _lib = None
 
@@ -94,6 +94,9 @@ def load_library(path: str = LIB_PATH):
     L.ibm_get_field.argtypes = [P, c_int, P, c_int, c_size_t]
     L.ibm_set_field.argtypes = [P, c_int, P, c_int, c_size_t]
     L.ibm_sizes.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
+    L.ibm_launch_count.argtypes = [P, POINTER(c_int64)]
+    L.ibm_kernel_timer.argtypes = [P, c_int]
+    L.ibm_kernel_time.argtypes = [P, c_int, POINTER(c_double), POINTER(c_int64)]
     L.ibm_destroy.argtypes = [P]
     L.ibm_last_error.argtypes = [P]
     L.ibm_last_error.restype = c_char_p
@@ -182,6 +185,26 @@ def ibm_sizes(ctx):
     n, g = c_int64(), c_int64()
     _check(load_library().ibm_sizes(ctx, byref(n), byref(g)), ctx)
     return n.value, g.value
+
+
+def ibm_launch_count(ctx):
+    n = c_int64()
+    _check(load_library().ibm_launch_count(ctx, byref(n)), ctx)
+    return n.value
+
+
+KERNEL_IDS = {"rbgs0": 0, "spmv0": 1, "apply_A": 2, "mdot": 3, "orth": 4, "helm": 5, "conv": 6,
+              "rbgs_coarse": 7, "restrict": 8, "prolong": 9}
+
+
+def ibm_kernel_timer(ctx, enable: int):
+    return _check(load_library().ibm_kernel_timer(ctx, enable), ctx)
+
+
+def ibm_kernel_time(ctx, kernel: int):
+    ms, n = c_double(), c_int64()
+    _check(load_library().ibm_kernel_time(ctx, kernel, byref(ms), byref(n)), ctx)
+    return ms.value, n.value
 
 
 def ibm_destroy(ctx):
