@@ -228,6 +228,24 @@ ibm_status ibm_launch_count(ibm_ctx *ctx, int64_t *count);
 ibm_status ibm_kernel_timer(ibm_ctx *ctx, int enable);
 ibm_status ibm_kernel_time(ibm_ctx *ctx, int kernel, double *ms_total, int64_t *launches);
 
+/* Allocation-free residual check (no counterpart in the paper): returns in
+   *rel_out (host or device pointer) the relative residual
+   ||P(b - A phi)||_2 / ||P b||_2 of a pressure solution phi_dev for the
+   right-hand side rhs_dev (both device, N doubles; b = rhs with its
+   volume-weighted FLUID mean removed), the quantity ibm_poisson_solve reports
+   as rel_residual. For callers that may not allocate device memory (code
+   running during stream capture into a CUDA graph, where cudaMalloc is not
+   allowed, or frameworks that own all device memory): it calls no
+   cudaMalloc/cudaFree and keeps its partial sums in a 96 KiB file-scope
+   device array, held by every GPU that loads the library until exit.
+   Grids above 268,435,456 cells are rejected (IBM_ERR_ARG). The first call
+   on each device looks up that array's device address with that device
+   current, so make it before starting any stream capture. Calls share the
+   array: calls that overlap on the GPU (other streams or host threads)
+   race. IBM_ERR_STATE before ibm_classify_cells. */
+ibm_status ibm_poisson_residual_noalloc(ibm_ctx *ctx, const double *rhs_dev, const double *phi_dev,
+                                        double *rel_out);
+
 /* Release every allocation of the context. NULL is accepted. */
 ibm_status ibm_destroy(ibm_ctx *ctx);
 

@@ -26,6 +26,7 @@ SOURCES = {
     "geom.cu": ["--fmad=false"],
     "solver.cu": [],
     "flow.cu": [],
+    "noalloc.cu": [],
 }
 COMMON = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]

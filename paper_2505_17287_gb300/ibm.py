@@ -68,7 +68,8 @@ class ibm_tables_host(Structure):
 
 EXPORTS = ["ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
-           "ibm_kernel_timer", "ibm_kernel_time", "ibm_launch_count", "ibm_destroy", "ibm_last_error"]
+           "ibm_kernel_timer", "ibm_kernel_time", "ibm_launch_count", "ibm_poisson_residual_noalloc",
+           "ibm_destroy", "ibm_last_error"]
 
 _lib = None
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     L.ibm_set_field.argtypes = [P, c_int, P, c_int, c_size_t]
     L.ibm_sizes.argtypes = [P, POINTER(c_int64), POINTER(c_int64)]
     L.ibm_launch_count.argtypes = [P, POINTER(c_int64)]
+    L.ibm_poisson_residual_noalloc.argtypes = [P, P, P, P]
     L.ibm_kernel_timer.argtypes = [P, c_int]
     L.ibm_kernel_time.argtypes = [P, c_int, POINTER(c_double), POINTER(c_int64)]
     L.ibm_destroy.argtypes = [P]
@@ -205,6 +207,15 @@ def ibm_kernel_time(ctx, kernel: int):
     ms, n = c_double(), c_int64()
     _check(load_library().ibm_kernel_time(ctx, kernel, byref(ms), byref(n)), ctx)
     return ms.value, n.value
+
+
+def ibm_poisson_residual_noalloc(ctx, rhs_ptr: int, phi_ptr: int):
+    """Relative residual of phi for rhs (device pointers), computed without
+    any device allocation; returns a float."""
+    out = c_double()
+    _check(load_library().ibm_poisson_residual_noalloc(ctx, c_void_p(rhs_ptr), c_void_p(phi_ptr),
+                                                       ctypes.cast(byref(out), c_void_p)), ctx)
+    return out.value
 
 
 def ibm_destroy(ctx):
