@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-kernels", action="store_true", help="also report every timed kernel")
+    ap.add_argument("--no-ktimer", action="store_true", help="skip the per-kernel timing pass")
     return ap.parse_args()
 
 
@@ -234,7 +235,10 @@ def main():
     # roofline of the dominant kernel: a second pass over the same number of
     # steps with the event timer on (the timer adds host work per launch, so
     # the headline above is measured without it)
-    ms_kt, stats_kt, _, kt = timed(args.steps, kernel_timer=True)
+    if args.no_ktimer:
+        ms_kt, kt = ms, {k: (0.0, 0) for k in ibm.KERNEL_IDS}
+    else:
+        ms_kt, stats_kt, _, kt = timed(args.steps, kernel_timer=True)
     rb_ms, rb_n = kt["rbgs0"]
     rb_bytes = rbgs_pass_bytes(N, 8)
     achieved = rb_bytes / (rb_ms / rb_n / 1e3) / 1e9 if rb_n else None

@@ -62,6 +62,9 @@ enum {
 /* arithmetic of the Poisson solver's inner multigrid-preconditioned CG */
 enum { IBM_FP64 = 0, IBM_MIXED = 1 };
 
+/* outer Krylov method of the Poisson solver */
+enum { IBM_OUTER_BICGSTAB = 0, IBM_OUTER_FGMRES = 1 };
+
 typedef struct {
     int ndim;              /* 2 or 3 */
     int nx, ny, nz;        /* cells per axis, each >= 2 (nz = 1 when ndim == 2) */
@@ -83,7 +86,8 @@ typedef struct {
 
 typedef struct {
     double rtol;        /* Poisson: relative residual ||P(b-A phi)||/||P b|| target */
-    int max_outer;      /* Poisson: FGMRES iteration limit over all restarts */
+    int max_outer;      /* Poisson: outer iteration limit (BiCGStab iterations or
+                           FGMRES steps over all restarts) */
     int restart;        /* Poisson: FGMRES restart length (1..16) */
     int inner_iters;    /* Poisson: MG-PCG iterations per preconditioner call */
     int nu1, nu2;       /* multigrid pre/post red-black Gauss-Seidel sweeps */
@@ -93,6 +97,10 @@ typedef struct {
     double ghost_tol;   /* velocity ghost refresh: max relative change */
     int ghost_maxit;    /* velocity ghost refresh: Jacobi pass limit */
     int precision;      /* IBM_FP64 or IBM_MIXED */
+    int outer;          /* IBM_OUTER_BICGSTAB or IBM_OUTER_FGMRES */
+    int band_sweeps;    /* damped Jacobi sweeps of the full operator near the body, per
+                           preconditioner call (0 = none) */
+    double band_omega;  /* their damping factor, in (0, 1] */
 } ibm_solver_opts;
 
 typedef struct {
@@ -145,9 +153,10 @@ enum {
     IBM_FIELD_STEP = 15                                   /* int64 step counter, 1 value */
 };
 
-/* Defaults: rtol 1e-10, max_outer 200, restart 8, inner_iters 2, nu1 = nu2 = 2,
+/* Defaults: rtol 1e-10, max_outer 200, restart 8, inner_iters 1, nu1 = nu2 = 2,
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
-   ghost_maxit 100, precision IBM_FP64. */
+   ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_BICGSTAB, band_sweeps 4,
+   band_omega 0.7. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).
@@ -182,8 +191,8 @@ ibm_status ibm_classify_cells(ibm_ctx *ctx, ibm_table_info *out);
 
 /* Advance nsteps fractional steps (Section 2.1): convective term, AB2 + CN
    right-hand side, CN Helmholtz solve with Dirichlet ghost rows, face
-   velocities and divergence, pressure Poisson solve (FGMRES in FP64
-   around multigrid-preconditioned CG on the staircase operator), projection,
+   velocities and divergence, pressure Poisson solve (BiCGStab or FGMRES in
+   FP64 around multigrid-preconditioned CG on the staircase operator), projection,
    velocity ghost refresh. out may be NULL. Returns IBM_ERR_NOT_CONVERGED
    when a solve hit its iteration limit (the step is still completed),
    IBM_ERR_DIVERGED on NaN/Inf (state then undefined). */

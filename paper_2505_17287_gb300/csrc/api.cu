@@ -41,15 +41,14 @@ void dev_free(Ctx *c, void *p) {
 }
 
 void kt_begin(Ctx *c, int id) {
-    if (!c->kt.on) return;
+    if (!c->kt.on || id < 0) return;
     if (c->kt.used + 2 > (int)c->kt.pool.size()) kt_flush(c);
     cudaEventRecord(c->kt.pool[c->kt.used], c->s);
     c->kt.ids[c->kt.used / 2] = id;
 }
 
 void kt_end(Ctx *c, int id) {
-    (void)id;
-    if (!c->kt.on) return;
+    if (!c->kt.on || id < 0) return;
     cudaEventRecord(c->kt.pool[c->kt.used + 1], c->s);
     c->kt.used += 2;
 }
@@ -86,7 +85,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->rtol = 1e-10;
     o->max_outer = 200;
     o->restart = 8;
-    o->inner_iters = 2;
+    o->inner_iters = 1;
     o->nu1 = 2;
     o->nu2 = 2;
     o->coarse_sweeps = 32;
@@ -95,6 +94,9 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->ghost_tol = 1e-15;
     o->ghost_maxit = 100;
     o->precision = IBM_FP64;
+    o->outer = IBM_OUTER_BICGSTAB;
+    o->band_sweeps = 4;
+    o->band_omega = 0.7;
     return IBM_OK;
 }
 
@@ -108,24 +110,30 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1) { why = "bad Helmholtz tolerance or limit"; return false; }
     if (!(o->ghost_tol > 0.0) || o->ghost_maxit < 1) { why = "bad ghost refresh tolerance or limit"; return false; }
     if (o->precision != IBM_FP64 && o->precision != IBM_MIXED) { why = "precision must be IBM_FP64 or IBM_MIXED"; return false; }
+    if (o->outer != IBM_OUTER_BICGSTAB && o->outer != IBM_OUTER_FGMRES) { why = "unknown outer method"; return false; }
+    if (o->band_sweeps < 0 || o->band_sweeps > 64) { why = "band_sweeps must be in [0, 64]"; return false; }
+    if (!(o->band_omega > 0.0 && o->band_omega <= 1.0)) { why = "band_omega must be in (0, 1]"; return false; }
     return true;
 }
 
+// Krylov storage: FGMRES(m) needs m+1 basis and m preconditioned vectors;
+// BiCGStab uses six of the first and two of the second
 static ibm_status alloc_krylov(Ctx *c, int m) {
     if (m <= c->m_cap) return IBM_OK;
     for (double *p : c->V) dev_free(c, p);
     for (double *p : c->Z) dev_free(c, p);
-    c->V.assign(m + 1, nullptr);
-    c->Z.assign(m, nullptr);
-    for (int i = 0; i <= m; ++i)
-        if (!(c->V[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "FGMRES basis allocation failed");
-    for (int i = 0; i < m; ++i)
-        if (!(c->Z[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "FGMRES basis allocation failed");
+    const int nv = m + 1 > 6 ? m + 1 : 6, nz = m > 2 ? m : 2;
+    c->V.assign(nv, nullptr);
+    c->Z.assign(nz, nullptr);
+    for (int i = 0; i < nv; ++i)
+        if (!(c->V[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "Krylov vector allocation failed");
+    for (int i = 0; i < nz; ++i)
+        if (!(c->Z[i] = (double *)dev_alloc(c, sizeof(double) * c->N))) return c->fail(IBM_ERR_OOM, "Krylov vector allocation failed");
     if (!c->Vdev) c->Vdev = (double **)dev_alloc(c, sizeof(double *) * 17);
     if (!c->Zdev) c->Zdev = (double **)dev_alloc(c, sizeof(double *) * 17);
     if (!c->Vdev || !c->Zdev) return c->fail(IBM_ERR_OOM, "pointer table allocation failed");
     IBM_CUDA(c, cudaMemcpyAsync(c->Vdev, c->V.data(), sizeof(double *) * (m + 1), cudaMemcpyHostToDevice, c->s));
-    IBM_CUDA(c, cudaMemcpyAsync(c->Zdev, c->Z.data(), sizeof(double *) * m, cudaMemcpyHostToDevice, c->s));
+    IBM_CUDA(c, cudaMemcpyAsync(c->Zdev, c->Z.data(), sizeof(double *) * nz, cudaMemcpyHostToDevice, c->s));
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
     c->m_cap = m;
     return IBM_OK;
@@ -157,7 +165,7 @@ static ibm_status build_levels(Ctx *c) {
     while ((int)c->lg.size() < 24) {
         const LevelGeom &L = c->lg.back();
         const int64_t n = (int64_t)L.nx * L.ny * L.nz;
-        if (n <= 64 || (L.nx <= 2 && L.ny <= 2 && L.nz <= 2)) break;
+        if (n <= 512 || (L.nx <= 2 && L.ny <= 2 && L.nz <= 2)) break;
         LevelGeom C;
         C.fx = L.nx > 2 ? 2 : 1;
         C.fy = L.ny > 2 ? 2 : 1;
@@ -176,6 +184,10 @@ static ibm_status build_levels(Ctx *c) {
         C.yf = coarsen(L.yf, L.ny, C.fy, C.ny);
         C.zf = coarsen(L.zf, L.nz, C.fz, C.nz);
         c->lg.push_back(C);
+    }
+    {
+        const LevelGeom &L = c->lg.back();
+        if ((int64_t)L.nx * L.ny * L.nz > 512) return c->fail(IBM_ERR_ARG, "grid too anisotropic to coarsen to 512 cells");
     }
     for (auto &L : c->lg) {
         std::vector<double> cc, w, h;
@@ -222,8 +234,28 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     c->hx = upload(c, c->hhx); c->hy = upload(c, c->hhy); c->hz = upload(c, c->hhz);
     if (!c->xf || !c->yf || !c->zf || !c->xc || !c->yc || !c->zc || !c->dx || !c->dy || !c->dz || !c->hx || !c->hy || !c->hz)
         return c->fail(IBM_ERR_OOM, "grid allocation failed");
+    // per-axis coefficients of the full pressure operator divided by the volume
+    auto coef = [&](const std::vector<double> &h, const std::vector<double> &w, double **m, double **p, double **sm) {
+        const size_t n = w.size();
+        std::vector<double> a(n, 0.0), b(n, 0.0), s(n, 0.0);
+        for (size_t i = 0; i < n; ++i) {
+            if (i > 0) a[i] = 1.0 / (h[i] * w[i]);
+            if (i + 1 < n) b[i] = 1.0 / (h[i + 1] * w[i]);
+            s[i] = a[i] + b[i];
+        }
+        *m = upload(c, a);
+        *p = upload(c, b);
+        *sm = upload(c, s);
+    };
+    double *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
+    coef(c->hhx, c->hdx, &cxm, &cxp, &cxs);
+    coef(c->hhy, c->hdy, &cym, &cyp, &cys);
+    coef(c->hhz, c->hdz, &czm, &czp, &czs);
+    if (!cxm || !cxp || !cxs || !cym || !cyp || !cys || !czm || !czp || !czs)
+        return c->fail(IBM_ERR_OOM, "grid allocation failed");
     c->g = GridDev{c->nx, c->ny, c->nz, c->ndim, c->N, c->xf, c->yf, c->zf, c->xc, c->yc, c->zc,
-                   c->dx, c->dy, c->dz, c->hx, c->hy, c->hz};
+                   c->dx, c->dy, c->dz, c->hx, c->hy, c->hz, cxm, cxp, cxs, cym, cyp, cys, czm, czp, czs,
+                   FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny)};
     const size_t nb = sizeof(double) * c->N;
     c->type = (uint8_t *)dev_alloc(c, c->N);
     c->inside = (uint8_t *)dev_alloc(c, c->N);
@@ -282,7 +314,7 @@ extern "C" ibm_status ibm_create_grid(const ibm_grid_desc *d, ibm_ctx **out) {
     if (d->precision != IBM_FP64 && d->precision != IBM_MIXED) { g_create_error = "bad precision"; return IBM_ERR_ARG; }
     if ((d->alloc == nullptr) != (d->free == nullptr)) { g_create_error = "alloc and free hooks must be given together"; return IBM_ERR_ARG; }
     const double ncell = (double)d->nx * d->ny * (d->ndim == 3 ? d->nz : 1);
-    if (ncell > 9.0e18 / 64) { g_create_error = "grid too large"; return IBM_ERR_ARG; }
+    if (ncell >= 4294967296.0) { g_create_error = "grid too large (at most 2^32 - 1 cells)"; return IBM_ERR_ARG; }
     ibm_ctx *c = new (std::nothrow) ibm_ctx();
     if (!c) { g_create_error = "host allocation failed"; return IBM_ERR_OOM; }
     ibm_status s = create_impl(c, d);

@@ -42,6 +42,26 @@ struct Err {
         if (s_ != IBM_OK) return s_;           \
     } while (0)
 
+// Division by a fixed 32-bit divisor with a multiply-high and a shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): q = (hi(n*m) + n) >> s, with the addition done
+// without overflow as ((n - t) >> 1) + t.
+struct FastDiv {
+    uint32_t d = 1, m = 0, s = 0;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div) {
+        uint32_t l = 0;
+        while ((1ull << l) < div) ++l;          // l = ceil(log2 d)
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+        s = l;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        if (d == 1) return n;
+        const uint32_t t = __umulhi(n, m);
+        return (t + ((n - t) >> 1)) >> (s - 1);
+    }
+};
+
 // device view of a grid level (coordinates and extents)
 struct GridDev {
     int nx, ny, nz, ndim;
@@ -50,7 +70,21 @@ struct GridDev {
     const double *xc, *yc, *zc;   // centres
     const double *dx, *dy, *dz;   // widths
     const double *hx, *hy, *hz;   // centre spacing; h?[i] = c[i]-c[i-1] for i>=1, [0] unused
+    // full pressure operator per axis, divided by the cell volume:
+    // cXm[i] = 1/(h[i] d[i]) (0 at the low wall), cXp[i] = 1/(h[i+1] d[i]) (0 at
+    // the high wall), cXs = cXm + cXp
+    const double *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
+    FastDiv fnx, fny;     // division by nx and ny (cell index < 2^32)
 };
+
+// cell (i, j, k) of a linear index below 2^32
+__device__ __forceinline__ void split3(const GridDev &g, uint32_t c, int &i, int &j, int &k) {
+    const uint32_t t = g.fnx.div(c);
+    i = (int)(c - t * (uint32_t)g.nx);
+    const uint32_t kk = g.fny.div(t);
+    j = (int)(t - kk * (uint32_t)g.ny);
+    k = (int)kk;
+}
 
 // per-ghost tables (device, structure of arrays)
 struct GhostDev {
@@ -62,12 +96,20 @@ struct GhostDev {
 };
 
 // one multigrid level of the staircase operator K = sum_open T (x_c - x_nb)
+// (T the open face area over the centre spacing). A "fine" level holds no
+// coefficient arrays: it derives them from the cell types and 1D metrics.
 template <typename T>
 struct MGLevel {
     int nx, ny, nz;
     int64_t n;
+    FastDiv fnx, fny;
     T *tx, *ty, *tz;   // coefficient of the face on the low side of each cell
-    T *x, *f, *r;      // correction, right-hand side, scratch
+    T *d, *dinv;       // diagonal (sum of the six faces) and its inverse (0 if isolated)
+    T *x, *f;          // correction and right-hand side of coarse levels
+    // fine-level description
+    const uint8_t *type;
+    const T *wx, *wy, *wz;      // cell widths
+    const T *rhx, *rhy, *rhz;   // 1 / centre spacing (index i: face between i-1 and i)
 };
 
 struct Ctx;

@@ -8,8 +8,9 @@ namespace ibm {
 template <typename T>
 struct MGHier {
     std::vector<MGLevel<T>> lv;
-    T *d0 = nullptr;        // diagonal of level 0 (per level diagonals in dg)
-    std::vector<T *> dg;    // diagonal per level
+    bool fine0 = false;     // level 0 derives its coefficients (no arrays)
+    // 1D metrics of level 0 in precision T (fine variant)
+    T *wx = nullptr, *wy = nullptr, *wz = nullptr, *rhx = nullptr, *rhy = nullptr, *rhz = nullptr;
     // PCG vectors on level 0
     T *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
     bool built = false;
@@ -102,6 +103,11 @@ struct Ctx {
     std::vector<double *> V, Z;
     double **Vdev = nullptr, **Zdev = nullptr;   // device arrays of the V / Z pointers
     double *w = nullptr, *rr = nullptr;
+    // near-body band for the preconditioner's local relaxation
+    int64_t nband = 0;
+    int64_t *band = nullptr;      // cell index
+    int64_t *band_g = nullptr;    // position in gidx, -1 for FLUID cells
+    double *btmp = nullptr;
     std::vector<LevelGeom> lg;
     std::vector<double *> lhx, lhy, lhz;   // per level centre spacing (device)
     MGHier<double> mg64;

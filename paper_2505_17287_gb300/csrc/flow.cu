@@ -69,7 +69,7 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3
             continue;
         }
         int i, j, k;
-        ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         const double vol = g.dx[i] * g.dy[j] * g.dz[k];
         const double A[3] = {g.dy[j] * g.dz[k], g.dx[i] * g.dz[k], g.dx[i] * g.dy[j]};
         const int idx[3] = {i, j, k};
@@ -171,7 +171,7 @@ __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const 
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) continue;
         int i, j, k;
-        ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         const double vol = g.dx[i] * g.dy[j] * g.dz[k];
         const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
         const double uc = u[c];
@@ -358,7 +358,7 @@ __global__ void k_divergence(GridDev g, const uint8_t *__restrict__ type, CField
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) { out[c] = 0.0; continue; }
         int i, j, k;
-        ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         const double vol = g.dx[i] * g.dy[j] * g.dz[k];
         double d = g.dy[j] * g.dz[k] * (F.p[0][fx_lo(g, i, j, k) + 1] - F.p[0][fx_lo(g, i, j, k)]);
         d += g.dx[i] * g.dz[k] * (F.p[1][fy_lo(g, i, j, k) + g.nx] - F.p[1][fy_lo(g, i, j, k)]);
@@ -399,7 +399,7 @@ __global__ void k_project_cells(GridDev g, const uint8_t *__restrict__ type, con
             continue;
         }
         int i, j, k;
-        ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         const double pc = phi[c];
         double glo, ghi;
         glo = i > 0 ? (pc - phi[c - 1]) / g.hx[i] : 0.0;

@@ -215,6 +215,68 @@ __global__ void k_write_ghosts(int64_t n, const uint8_t *__restrict__ type, cons
     if (g) gidx[off[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u))] = c;
 }
 
+// counts of set flags per chunk, in column 1 of the 3-column layout
+__global__ void k_count_flags(int64_t n, const uint8_t *__restrict__ f, int64_t *__restrict__ cnt) {
+    __shared__ int sh;
+    if (threadIdx.x == 0) sh = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * CHUNK;
+    int loc = 0;
+    for (int q = threadIdx.x; q < CHUNK; q += blockDim.x) {
+        const int64_t c = base + q;
+        if (c < n && f[c]) ++loc;
+    }
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sh, loc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cnt[3 * (int64_t)blockIdx.x + 0] = 0;
+        cnt[3 * (int64_t)blockIdx.x + 1] = sh;
+        cnt[3 * (int64_t)blockIdx.x + 2] = 0;
+    }
+}
+
+__global__ void k_write_flags(int64_t n, const uint8_t *__restrict__ f, const int64_t *__restrict__ off,
+                              int64_t *__restrict__ out) {
+    __shared__ int wsum[32];
+    const int64_t c = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+    const bool g = c < n && f[c];
+    const unsigned bal = __ballot_sync(0xffffffffu, g);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    if (g) out[off[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u))] = c;
+}
+
+// ascending list of the cells whose flag is set (allocated here)
+ibm_status compact_flags(Ctx *c, const uint8_t *flags, int64_t **out, int64_t *count) {
+    const int64_t nb = (c->N + CHUNK - 1) / CHUNK;
+    int64_t *cnt = (int64_t *)dev_alloc(c, sizeof(int64_t) * 3 * nb);
+    int64_t *off = (int64_t *)dev_alloc(c, sizeof(int64_t) * nb);
+    int64_t *tot = (int64_t *)dev_alloc(c, sizeof(int64_t) * 4);
+    if (!cnt || !off || !tot) return c->fail(IBM_ERR_OOM, "compaction scratch allocation failed");
+    ++c->nlaunch, k_count_flags<<<(unsigned)nb, 256, 0, c->s>>>(c->N, flags, cnt);
+    ++c->nlaunch, k_scan_counts<<<1, 1024, 0, c->s>>>(nb, cnt, off, tot);
+    IBM_LAUNCHED(c);
+    int64_t htot[3] = {0, 0, 0};
+    IBM_CUDA(c, cudaMemcpyAsync(htot, tot, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    *count = htot[1];
+    *out = (int64_t *)dev_alloc(c, sizeof(int64_t) * (htot[1] > 0 ? htot[1] : 1));
+    if (!*out) return c->fail(IBM_ERR_OOM, "compaction output allocation failed");
+    if (htot[1] > 0) {
+        ++c->nlaunch, k_write_flags<<<(unsigned)nb, CHUNK, 0, c->s>>>(c->N, flags, off, *out);
+        IBM_LAUNCHED(c);
+    }
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    dev_free(c, cnt);
+    dev_free(c, off);
+    dev_free(c, tot);
+    return IBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // closest points and weights (must match the oracle operation for operation)
 // ---------------------------------------------------------------------------

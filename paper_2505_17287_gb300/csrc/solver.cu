@@ -1,19 +1,26 @@
 // Pressure Poisson solver (Section 2.1, pressure equation; Section 2.2,
 // Neumann ghost-cell rows) on one GPU.
 //
-//   outer: restarted FGMRES in FP64 on P A phi = P b, where A is the full
-//          ghost-cell operator (FLUID rows: variable-coefficient 7-point
-//          (2D: 5-point) div-grad with ghost neighbours; GHOST rows:
-//          phi_G - sum wp phi_m; DEAD rows: identity) and P removes the
-//          volume-weighted FLUID mean (compatibility);
+//   outer:  FP64 Krylov iteration on P A phi = P b, where A is the full
+//           ghost-cell operator (FLUID rows: variable-coefficient 7-point
+//           (2D: 5-point) div-grad including ghost neighbours; GHOST rows:
+//           phi_G - sum wp phi_m; DEAD rows: identity) and P removes the
+//           volume-weighted FLUID mean (compatibility). BiCGStab (the
+//           paper's Poisson solver, Section 2.1) or restarted FGMRES;
 //   preconditioner: multigrid-preconditioned CG on the staircase operator
-//          K = sum over open faces T_f (x_c - x_nb) (a face is open when
-//          both sides are FLUID), symmetric positive semi-definite, in FP64
-//          or FP32 (storage and arithmetic; dot products accumulate in
-//          FP64), followed by one pass over the ghost rows;
-//   multigrid: V(nu1,nu2) cycle, red-black Gauss-Seidel smoothing, restriction
-//          by summing children, piecewise-constant prolongation, coarse
-//          operators rediscretised from the open child-face areas.
+//           K = sum over open faces T_f (x_c - x_nb) (a face is open when
+//           both sides are FLUID; symmetric positive semi-definite), in FP64
+//           or FP32 (storage and arithmetic; dot products accumulate in
+//           FP64); then the ghost rows; then damped Jacobi sweeps of the full
+//           operator on the cells within two faces of a ghost cell;
+//   multigrid: V(nu1,nu2) cycle, red-black Gauss-Seidel smoothing,
+//           restriction by summing children, piecewise-constant prolongation,
+//           coarse operators rediscretised from the open child-face areas,
+//           coarsest level solved by red-black sweeps in one thread block.
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate, so the FP64 kernels here are
+// written to minimise FP64 instructions: per-axis 1D operator coefficients,
+// reciprocal diagonals, no division in the inner loops.
 #include "ctx.cuh"
 
 #include <math.h>
@@ -21,7 +28,30 @@
 namespace ibm {
 
 // device scalar slots
-enum { S_RZ = 0, S_PQ = 1, S_AL = 2, S_RZN = 3, S_BE = 4, S_MEAN = 5, S_TMP = 8, S_MD = 16 };
+enum {
+    S_RZ = 0, S_PQ = 1, S_AL = 2, S_RZN = 3, S_BE = 4, S_MEAN = 5, S_TMP = 8, S_MD = 16,
+    B_RHO = 34, B_ALPHA = 35, B_OMEGA = 36, B_BETA = 37, B_RHO1 = 38, B_DEN = 39, B_TS = 58, B_TT = 59,
+    B_FLAG = 60
+};
+
+#define KL(kid, kern, grid, block, ...)                      \
+    do {                                                     \
+        kt_begin(c, kid);                                    \
+        ++c->nlaunch;                                        \
+        kern<<<(grid), (block), 0, c->s>>>(__VA_ARGS__);     \
+        kt_end(c, kid);                                      \
+    } while (0)
+
+static inline unsigned nblk(int64_t n, int t = 256) {
+    int64_t b = (n + t - 1) / t;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+}
+
+static inline dim3 rows_grid(int nx, int ny, int nz, int per_thread, int bx) {
+    const int64_t rows = (int64_t)ny * nz;
+    const int xs = (nx + per_thread - 1) / per_thread;
+    return dim3((unsigned)rows, (unsigned)((xs + bx - 1) / bx), 1);
+}
 
 // ---------------------------------------------------------------------------
 // reductions
@@ -40,15 +70,13 @@ __global__ void k_finalize(const double *__restrict__ part, int nparts, int ncol
 }
 
 ibm_status finalize(Ctx *c, const double *part, int nparts, int ncols, double scale, double *out_dev) {
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(part, nparts, ncols, scale, out_dev);
+    KL(-1, k_finalize, 1, RED_THREADS, part, nparts, ncols, scale, out_dev);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
 
 ibm_status reduce_sum(Ctx *c, const double *partials, int nparts, double *out_dev) {
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(partials, nparts, 1, 1.0, out_dev);
-    IBM_LAUNCHED(c);
-    return IBM_OK;
+    return finalize(c, partials, nparts, 1, 1.0, out_dev);
 }
 
 ibm_status sync_scalars(Ctx *c, int n) {
@@ -57,22 +85,18 @@ ibm_status sync_scalars(Ctx *c, int n) {
     return IBM_OK;
 }
 
-__device__ __forceinline__ void cell_ijk(int64_t cidx, int nx, int ny, int &i, int &j, int &k) {
-    int64_t t = cidx / nx;
-    i = (int)(cidx - t * nx);
-    j = (int)(t % ny);
-    k = (int)(t / ny);
-}
+#define GRID_STRIDE(c, n) \
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (n); c += (int64_t)gridDim.x * blockDim.x)
 
 // sum over FLUID cells of vol * x (x null: the FLUID volume)
 __global__ void k_fluid_volsum(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ x,
                                double *__restrict__ part) {
     __shared__ double sh[32];
     double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, g.n) {
         if (type[c] != FLUID) continue;
         int i, j, k;
-        cell_ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         acc += (g.dx[i] * g.dy[j] * g.dz[k]) * (x ? x[c] : 1.0);
     }
     acc = block_sum<RED_THREADS>(acc, sh);
@@ -83,8 +107,8 @@ __global__ void k_fluid_volsum(GridDev g, const uint8_t *__restrict__ type, cons
 __global__ void k_sub_mean(int64_t n, const uint8_t *__restrict__ type, double *__restrict__ x,
                            const double *__restrict__ mean, int ghosts) {
     const double m = *mean;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        uint8_t t = type[c];
+    GRID_STRIDE(c, n) {
+        const uint8_t t = type[c];
         if (t == FLUID || (ghosts && t == GHOST)) x[c] -= m;
         else if (t == DEAD) x[c] = 0.0;
     }
@@ -92,10 +116,9 @@ __global__ void k_sub_mean(int64_t n, const uint8_t *__restrict__ type, double *
 
 ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_host) {
     (void)ghosts_too;
-    ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, c->part);
+    KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, x, c->part);
     IBM_LAUNCHED(c);
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
-    IBM_LAUNCHED(c);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     if (mean_host) {
         IBM_TRY(sync_scalars(c, S_MEAN + 1));
         *mean_host = c->hscal[S_MEAN];
@@ -107,6 +130,24 @@ ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_hos
 // full ghost-cell pressure operator (FP64)
 // ---------------------------------------------------------------------------
 
+// (A x)_c of a FLUID cell with the per-axis coefficients; boundary faces
+// have coefficient 0, so a wall reads the cell itself
+__device__ __forceinline__ double A_row(const GridDev &g, const double *__restrict__ x, int64_t c, int i, int j,
+                                        int k) {
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const double xc = x[c];
+    const double xm = i > 0 ? x[c - 1] : xc, xp = i < g.nx - 1 ? x[c + 1] : xc;
+    const double ym = j > 0 ? x[c - sy] : xc, yp = j < g.ny - 1 ? x[c + sy] : xc;
+    double s = g.cxm[i] * xm + g.cxp[i] * xp + g.cym[j] * ym + g.cyp[j] * yp;
+    double dsum = g.cxs[i] + g.cys[j];
+    if (g.ndim == 3) {
+        const double zm = k > 0 ? x[c - sz] : xc, zp = k < g.nz - 1 ? x[c + sz] : xc;
+        s += g.czm[k] * zm + g.czp[k] * zp;
+        dsum += g.czs[k];
+    }
+    return s - dsum * xc;
+}
+
 // y = sgn * (A x) + b  on FLUID and DEAD rows (b may be null = 0); GHOST rows
 // are written by k_ghost_rows. Partials: sum over FLUID of vol * y.
 __global__ void k_apply_A(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ x,
@@ -114,28 +155,15 @@ __global__ void k_apply_A(GridDev g, const uint8_t *__restrict__ type, const dou
                           double *__restrict__ part) {
     __shared__ double sh[32];
     double acc = 0.0;
-    const int64_t sx = 1, sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, g.n) {
         const uint8_t t = type[c];
         if (t == GHOST) continue;
         if (t == DEAD) { y[c] = 0.0; continue; }
         int i, j, k;
-        cell_ijk(c, g.nx, g.ny, i, j, k);
-        const double xc = x[c];
-        const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
-        double s = 0.0;
-        if (i > 0) s += ax / g.hx[i] * (x[c - sx] - xc);
-        if (i < g.nx - 1) s += ax / g.hx[i + 1] * (x[c + sx] - xc);
-        if (j > 0) s += ay / g.hy[j] * (x[c - sy] - xc);
-        if (j < g.ny - 1) s += ay / g.hy[j + 1] * (x[c + sy] - xc);
-        if (g.ndim == 3) {
-            if (k > 0) s += az / g.hz[k] * (x[c - sz] - xc);
-            if (k < g.nz - 1) s += az / g.hz[k + 1] * (x[c + sz] - xc);
-        }
-        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
-        double v = sgn * (s / vol) + (b ? b[c] : 0.0);
+        split3(g, (uint32_t)c, i, j, k);
+        const double v = sgn * A_row(g, x, c, i, j, k) + (b ? b[c] : 0.0);
         y[c] = v;
-        acc += vol * v;
+        acc += (g.dx[i] * g.dy[j] * g.dz[k]) * v;
     }
     acc = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
@@ -143,7 +171,7 @@ __global__ void k_apply_A(GridDev g, const uint8_t *__restrict__ type, const dou
 
 // GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m)   (b_g = 0)
 __global__ void k_ghost_rows(GhostDev gh, const double *__restrict__ x, double sgn, double *__restrict__ y) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= gh.ng) return;
     const int64_t gi = gh.gidx[q];
     double s = x[gi];
@@ -151,25 +179,27 @@ __global__ void k_ghost_rows(GhostDev gh, const double *__restrict__ x, double s
     y[gi] = sgn * s;
 }
 
+__global__ void k_zero_at(int64_t m, const int64_t *__restrict__ idx, double *__restrict__ x) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < m) x[idx[q]] = 0.0;
+}
+
 // y = P(sgn * A x + b)
 static ibm_status apply_PA(Ctx *c, const double *x, const double *b, double sgn, double *y) {
-    kt_begin(c, K_APPLY_A);
-    ++c->nlaunch, k_apply_A<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, x, b, sgn, y, c->part);
-    kt_end(c, K_APPLY_A);
+    KL(K_APPLY_A, k_apply_A, RED_BLOCKS, RED_THREADS, c->g, c->type, x, b, sgn, y, c->part);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        ++c->nlaunch, k_ghost_rows<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, x, sgn, y);
+        KL(-1, k_ghost_rows, (unsigned)((c->ng + 255) / 256), 256, c->gh, x, sgn, y);
         IBM_LAUNCHED(c);
     }
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
-    IBM_LAUNCHED(c);
-    ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, y, c->scal + S_MEAN, 0);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
 
 // ---------------------------------------------------------------------------
-// FP64 vector kernels for FGMRES
+// FP64 vector kernels: FGMRES
 // ---------------------------------------------------------------------------
 
 struct Coef {
@@ -184,7 +214,7 @@ __global__ void k_mdot(int64_t n, const double *__restrict__ w, const double *co
 #pragma unroll
     for (int q = 0; q < 17; ++q) acc[q] = 0.0;
     double ww = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, n) {
         const double a = w[c];
         ww += a * a;
 #pragma unroll
@@ -192,10 +222,10 @@ __global__ void k_mdot(int64_t n, const double *__restrict__ w, const double *co
             if (q < ncols) acc[q] += a * V[q][c];
     }
     for (int q = 0; q < ncols; ++q) {
-        double t = block_sum<RED_THREADS>(acc[q], sh);
+        const double t = block_sum<RED_THREADS>(acc[q], sh);
         if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
     }
-    double t = block_sum<RED_THREADS>(ww, sh);
+    const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[(size_t)ncols * gridDim.x + blockIdx.x] = t;
 }
 
@@ -204,7 +234,7 @@ __global__ void k_orth(int64_t n, double *__restrict__ w, const double *const *_
                        double *__restrict__ part) {
     __shared__ double sh[32];
     double ww = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, n) {
         double a = w[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
@@ -212,18 +242,17 @@ __global__ void k_orth(int64_t n, double *__restrict__ w, const double *const *_
         w[c] = a;
         ww += a * a;
     }
-    double t = block_sum<RED_THREADS>(ww, sh);
+    const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void k_scale(int64_t n, double *__restrict__ dst, const double *__restrict__ src, double a) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        dst[c] = a * src[c];
+    GRID_STRIDE(c, n) dst[c] = a * src[c];
 }
 
 // x += sum_i y_i Z_i
 __global__ void k_xupd(int64_t n, double *__restrict__ x, const double *const *__restrict__ Z, int ncols, Coef y) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, n) {
         double a = x[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
@@ -233,50 +262,150 @@ __global__ void k_xupd(int64_t n, double *__restrict__ x, const double *const *_
 }
 
 // ---------------------------------------------------------------------------
+// FP64 vector kernels: BiCGStab (scalars live on the device)
+// ---------------------------------------------------------------------------
+
+__global__ void k_dot64(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                        double *__restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    GRID_STRIDE(c, n) acc += a[c] * b[c];
+    acc = block_sum<RED_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// beta = (rho1 / rho) (alpha / omega), rho = rho1; flag 1 on breakdown
+__global__ void k_bicg_beta(double *s) {
+    const double rho1 = s[B_RHO1], rho = s[B_RHO], om = s[B_OMEGA];
+    if (!(rho != 0.0) || !(om != 0.0) || !isfinite(rho1)) { s[B_FLAG] = 1.0; s[B_BETA] = 0.0; }
+    else s[B_BETA] = (rho1 / rho) * (s[B_ALPHA] / om);
+    s[B_RHO] = rho1;
+}
+__global__ void k_bicg_alpha(double *s) {
+    const double den = s[B_DEN];
+    if (!(den != 0.0) || !isfinite(den)) { s[B_FLAG] = 1.0; s[B_ALPHA] = 0.0; }
+    else s[B_ALPHA] = s[B_RHO] / den;
+}
+__global__ void k_bicg_omega(double *s) {
+    const double tt = s[B_TT];
+    s[B_OMEGA] = (tt > 0.0 && isfinite(tt)) ? s[B_TS] / tt : 0.0;
+    if (!(s[B_OMEGA] != 0.0)) s[B_FLAG] = 1.0;
+}
+__global__ void k_bicg_init(double *s) {
+    s[B_RHO] = 1.0;
+    s[B_ALPHA] = 1.0;
+    s[B_OMEGA] = 1.0;
+    s[B_FLAG] = 0.0;
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bicg_p(int64_t n, const double *__restrict__ r, double *__restrict__ p,
+                         const double *__restrict__ v, const double *__restrict__ s) {
+    const double be = s[B_BETA], om = s[B_OMEGA];
+    GRID_STRIDE(c, n) p[c] = r[c] + be * (p[c] - om * v[c]);
+}
+// sv = r - alpha v
+__global__ void k_bicg_s(int64_t n, const double *__restrict__ r, const double *__restrict__ v,
+                         double *__restrict__ sv, const double *__restrict__ s) {
+    const double al = s[B_ALPHA];
+    GRID_STRIDE(c, n) sv[c] = r[c] - al * v[c];
+}
+// partial (t, s) and (t, t)
+__global__ void k_bicg_tdots(int64_t n, const double *__restrict__ t, const double *__restrict__ sv,
+                             double *__restrict__ part) {
+    __shared__ double sh[32];
+    double ts = 0.0, tt = 0.0;
+    GRID_STRIDE(c, n) {
+        const double a = t[c];
+        ts += a * sv[c];
+        tt += a * a;
+    }
+    ts = block_sum<RED_THREADS>(ts, sh);
+    tt = block_sum<RED_THREADS>(tt, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ts;
+        part[gridDim.x + blockIdx.x] = tt;
+    }
+}
+// x += alpha ph + omega sh ; r = sv - omega t ; partial (r, r)
+__global__ void k_bicg_xr(int64_t n, double *__restrict__ x, const double *__restrict__ ph,
+                          const double *__restrict__ sh_, double *__restrict__ r, const double *__restrict__ sv,
+                          const double *__restrict__ t, const double *__restrict__ s, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const double al = s[B_ALPHA], om = s[B_OMEGA];
+    double rr = 0.0;
+    GRID_STRIDE(c, n) {
+        x[c] += al * ph[c] + om * sh_[c];
+        const double v = sv[c] - om * t[c];
+        r[c] = v;
+        rr += v * v;
+    }
+    rr = block_sum<RED_THREADS>(rr, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+// ---------------------------------------------------------------------------
 // multigrid on the staircase operator, precision T
 // ---------------------------------------------------------------------------
 
-// red-black Gauss-Seidel, one colour: x_c = (f_c + sum T x_nb) / D_c for the
-// cells of colour col ((i + j + k) even = 0) with D_c > 0
-template <typename T>
-__global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ D, const T *__restrict__ f, T *__restrict__ x, int col) {
-    const int64_t row = blockIdx.x;             // j + ny * k
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
-    const int par = (j + k + col) & 1;
-    const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + par;
-    if (i >= L.nx) return;
+// sum over the open faces of T_f x_nb, and the diagonal sum T_f, at cell c
+// of a level (FINE: derived from the cell types and 1D metrics)
+template <typename T, bool FINE>
+__device__ __forceinline__ T k_offdiag(const MGLevel<T> &L, const T *__restrict__ x, int64_t c, int i, int j, int k,
+                                       T &d) {
     const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
-    const int64_t c = row * L.nx + i;
-    const T d = D[c];
-    if (d <= T(0)) return;
-    T s = f[c];
-    if (i > 0) s += L.tx[c] * x[c - 1];
-    if (i < L.nx - 1) s += L.tx[c + 1] * x[c + 1];
-    if (j > 0) s += L.ty[c] * x[c - sy];
-    if (j < L.ny - 1) s += L.ty[c + sy] * x[c + sy];
-    if (k > 0) s += L.tz[c] * x[c - sz];
-    if (k < L.nz - 1) s += L.tz[c + sz] * x[c + sz];
-    x[c] = s / d;
-}
-
-template <typename T>
-__device__ __forceinline__ T k_row(const MGLevel<T> &L, const T *__restrict__ D, const T *__restrict__ x, int64_t c,
-                                   int i, int j, int k) {
-    const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
-    T s = D[c] * x[c];
-    if (i > 0) s -= L.tx[c] * x[c - 1];
-    if (i < L.nx - 1) s -= L.tx[c + 1] * x[c + 1];
-    if (j > 0) s -= L.ty[c] * x[c - sy];
-    if (j < L.ny - 1) s -= L.ty[c + sy] * x[c + sy];
-    if (k > 0) s -= L.tz[c] * x[c - sz];
-    if (k < L.nz - 1) s -= L.tz[c + sz] * x[c + sz];
+    T s = T(0);
+    if (FINE) {
+        d = T(0);
+        const T ayz = L.wy[j] * L.wz[k], axz = L.wx[i] * L.wz[k], axy = L.wx[i] * L.wy[j];
+        T t;
+        if (i > 0 && L.type[c - 1] == FLUID) { t = ayz * L.rhx[i]; d += t; s += t * x[c - 1]; }
+        if (i < L.nx - 1 && L.type[c + 1] == FLUID) { t = ayz * L.rhx[i + 1]; d += t; s += t * x[c + 1]; }
+        if (j > 0 && L.type[c - sy] == FLUID) { t = axz * L.rhy[j]; d += t; s += t * x[c - sy]; }
+        if (j < L.ny - 1 && L.type[c + sy] == FLUID) { t = axz * L.rhy[j + 1]; d += t; s += t * x[c + sy]; }
+        if (k > 0 && L.type[c - sz] == FLUID) { t = axy * L.rhz[k]; d += t; s += t * x[c - sz]; }
+        if (k < L.nz - 1 && L.type[c + sz] == FLUID) { t = axy * L.rhz[k + 1]; d += t; s += t * x[c + sz]; }
+    } else {
+        if (i > 0) s += L.tx[c] * x[c - 1];
+        if (i < L.nx - 1) s += L.tx[c + 1] * x[c + 1];
+        if (j > 0) s += L.ty[c] * x[c - sy];
+        if (j < L.ny - 1) s += L.ty[c + sy] * x[c + sy];
+        if (k > 0) s += L.tz[c] * x[c - sz];
+        if (k < L.nz - 1) s += L.tz[c + sz] * x[c + sz];
+        d = L.d[c];
+    }
     return s;
 }
 
+template <typename T, bool FINE>
+__device__ __forceinline__ bool active(const MGLevel<T> &L, int64_t c) {
+    if (FINE) return L.type[c] == FLUID;
+    return L.dinv[c] > T(0);
+}
+
+// red-black Gauss-Seidel, one colour: x_c = (f_c + sum T x_nb) / D_c on the
+// cells of colour col ((i + j + k) even = 0) with D_c > 0
+template <typename T, bool FINE>
+__global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    if (!active<T, FINE>(L, c)) return;
+    T d;
+    const T s = f[c] + k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+    if (FINE) {
+        if (d > T(0)) x[c] = s / d;
+    } else {
+        x[c] = s * L.dinv[c];
+    }
+}
+
 // coarse f_C = sum over children of (f - K x); coarse x_C = 0
-template <typename T>
-__global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ D, const T *__restrict__ f,
-                                 const T *__restrict__ x, MGLevel<T> C, int fx, int fy, int fz) {
+template <typename T, bool FINE>
+__global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, MGLevel<T> C,
+                                 int fx, int fy, int fz) {
     const int64_t row = blockIdx.x;
     const int J = (int)(row % C.ny), K = (int)(row / C.ny);
     const int I = blockIdx.y * blockDim.x + threadIdx.x;
@@ -292,7 +421,10 @@ __global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ D, const T 
                 const int i = fx * I + di;
                 if (i >= L.nx) break;
                 const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-                if (D[c] > T(0)) acc += f[c] - k_row(L, D, x, c, i, j, k);
+                if (!active<T, FINE>(L, c)) continue;
+                T d;
+                const T off = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+                acc += f[c] - (d * x[c] - off);
             }
         }
     }
@@ -301,30 +433,77 @@ __global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ D, const T 
     C.x[cc] = T(0);
 }
 
-// x_c += x_parent(c) on cells with D > 0
-template <typename T>
-__global__ void k_prolong(MGLevel<T> L, const T *__restrict__ D, T *__restrict__ x, MGLevel<T> C, int fx, int fy,
-                          int fz) {
+// x_c += x_parent(c) on active cells
+template <typename T, bool FINE>
+__global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx, int fy, int fz) {
     const int64_t row = blockIdx.x;
     const int j = (int)(row % L.ny), k = (int)(row / L.ny);
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
-    if (D[c] <= T(0)) return;
+    if (!active<T, FINE>(L, c)) return;
     const int64_t p = ((int64_t)(k / fz) * C.ny + (j / fy)) * C.nx + (i / fx);
     x[c] += C.x[p];
 }
 
-// q = K p ; partial (p, q) in FP64
+// coarsest level: red-black sweeps in one block, all data in shared memory
+constexpr int COARSE_MAX = 512;
 template <typename T>
-__global__ void k_spmv_dot(MGLevel<T> L, const T *__restrict__ D, const T *__restrict__ p, T *__restrict__ q,
-                           double *__restrict__ part) {
+__global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const T *__restrict__ f,
+                                                             T *__restrict__ x, int sweeps) {
+    __shared__ T sx[COARSE_MAX], sf[COARSE_MAX], stx[COARSE_MAX], sty[COARSE_MAX], stz[COARSE_MAX],
+        sdi[COARSE_MAX];
+    const int n = (int)L.n;
+    const int c = threadIdx.x;
+    int i = 0, j = 0, k = 0;
+    if (c < n) {
+        i = c % L.nx;
+        j = (c / L.nx) % L.ny;
+        k = c / (L.nx * L.ny);
+        sx[c] = T(0);
+        sf[c] = f[c];
+        stx[c] = L.tx[c];
+        sty[c] = L.ty[c];
+        stz[c] = L.tz[c];
+        sdi[c] = L.dinv[c];
+    }
+    __syncthreads();
+    const int sy = L.nx, sz = L.nx * L.ny;
+    const int par = (i + j + k) & 1;
+    for (int pass = 0; pass < 4 * sweeps; ++pass) {
+        // sweeps x (red, black) then sweeps x (black, red): a palindrome
+        const int colour = pass < 2 * sweeps ? (pass & 1) : 1 - (pass & 1);
+        if (c < n && par == colour && sdi[c] > T(0)) {
+            T s = sf[c];
+            if (i > 0) s += stx[c] * sx[c - 1];
+            if (i < L.nx - 1) s += stx[c + 1] * sx[c + 1];
+            if (j > 0) s += sty[c] * sx[c - sy];
+            if (j < L.ny - 1) s += sty[c + sy] * sx[c + sy];
+            if (k > 0) s += stz[c] * sx[c - sz];
+            if (k < L.nz - 1) s += stz[c + sz] * sx[c + sz];
+            sx[c] = s * sdi[c];
+        }
+        __syncthreads();
+    }
+    if (c < n) x[c] = sx[c];
+}
+
+// q = K p ; partial (p, q) in FP64
+template <typename T, bool FINE>
+__global__ void k_spmv_dot(MGLevel<T> L, const T *__restrict__ p, T *__restrict__ q, double *__restrict__ part) {
     __shared__ double sh[32];
     double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.n; c += (int64_t)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, L.nx, L.ny, i, j, k);
-        T v = D[c] > T(0) ? k_row(L, D, p, c, i, j, k) : T(0);
+    GRID_STRIDE(c, L.n) {
+        T v = T(0);
+        if (active<T, FINE>(L, c)) {
+            const uint32_t t = L.fnx.div((uint32_t)c);
+            const int i = (int)((uint32_t)c - t * (uint32_t)L.nx);
+            const uint32_t kk = L.fny.div(t);
+            const int j = (int)(t - kk * (uint32_t)L.ny), k = (int)kk;
+            T d;
+            const T off = k_offdiag<T, FINE>(L, p, c, i, j, k, d);
+            v = d * p[c] - off;
+        }
         q[c] = v;
         acc += (double)p[c] * (double)v;
     }
@@ -336,8 +515,7 @@ template <typename T>
 __global__ void k_dot(int64_t n, const T *__restrict__ a, const T *__restrict__ b, double *__restrict__ part) {
     __shared__ double sh[32];
     double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)a[c] * (double)b[c];
+    GRID_STRIDE(c, n) acc += (double)a[c] * (double)b[c];
     acc = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
@@ -346,7 +524,7 @@ template <typename T>
 __global__ void k_axpy2(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                         const T *__restrict__ q, const double *__restrict__ scal) {
     const T a = (T)scal[S_AL];
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, n) {
         x[c] += a * p[c];
         r[c] -= a * q[c];
     }
@@ -355,8 +533,7 @@ __global__ void k_axpy2(int64_t n, T *__restrict__ x, T *__restrict__ r, const T
 template <typename T>
 __global__ void k_pupd(int64_t n, T *__restrict__ p, const T *__restrict__ z, const double *__restrict__ scal) {
     const T b = (T)scal[S_BE];
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        p[c] = z[c] + b * p[c];
+    GRID_STRIDE(c, n) p[c] = z[c] + b * p[c];
 }
 
 // scalar updates (one thread)
@@ -370,30 +547,24 @@ __global__ void k_beta(double *scal) {
     scal[S_RZ] = scal[S_RZN];
 }
 
-__global__ void k_zero_at(int64_t m, const int64_t *__restrict__ idx, double *__restrict__ x) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < m) x[idx[q]] = 0.0;
-}
-
 // preconditioner input / output conversion
 template <typename T>
 __global__ void k_pre_in(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ v, T *__restrict__ f) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, g.n) {
         if (type[c] != FLUID) { f[c] = T(0); continue; }
         int i, j, k;
-        cell_ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         f[c] = (T)(-(g.dx[i] * g.dy[j] * g.dz[k]) * v[c]);
     }
 }
 template <typename T>
 __global__ void k_pre_out(int64_t n, const uint8_t *__restrict__ type, const T *__restrict__ x, double *__restrict__ z) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-        z[c] = type[c] == FLUID ? (double)x[c] : 0.0;
+    GRID_STRIDE(c, n) z[c] = type[c] == FLUID ? (double)x[c] : 0.0;
 }
 // ghost rows of the preconditioner: z_g = v_g + sum over FLUID corners wp z_m
 __global__ void k_pre_ghost(GhostDev gh, const uint8_t *__restrict__ type, const double *__restrict__ v,
                             double *__restrict__ z) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= gh.ng) return;
     const int64_t gi = gh.gidx[q];
     double s = v[gi];
@@ -404,15 +575,43 @@ __global__ void k_pre_ghost(GhostDev gh, const uint8_t *__restrict__ type, const
     z[gi] = s;
 }
 
+// one damped Jacobi pass of the full operator on the band: tmp = new z
+__global__ void k_band_jacobi(GridDev g, GhostDev gh, int64_t nb, const int64_t *__restrict__ band,
+                              const int64_t *__restrict__ band_g, const double *__restrict__ v,
+                              const double *__restrict__ z, double omega, double *__restrict__ tmp) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    const int64_t c = band[q];
+    const int64_t gq = band_g[q];
+    double res, diag;
+    if (gq >= 0) {
+        double s = z[c];
+        for (int m = 0; m < 8; ++m) s -= gh.wp[8 * gq + m] * z[gh.sidx[8 * gq + m]];
+        res = v[c] - s;
+        diag = 1.0;
+    } else {
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        res = v[c] - A_row(g, z, c, i, j, k);
+        diag = -(g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0));
+    }
+    tmp[q] = z[c] + omega * res / diag;
+}
+__global__ void k_band_scatter(int64_t nb, const int64_t *__restrict__ band, const double *__restrict__ tmp,
+                               double *__restrict__ z) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < nb) z[band[q]] = tmp[q];
+}
+
 // level coefficient construction ------------------------------------------
 
 // level 0 open face areas: face on the low side of cell c along each axis is
 // open when c and its low neighbour are both FLUID
 __global__ void k_open_area0(GridDev g, const uint8_t *__restrict__ type, double *__restrict__ ox,
                              double *__restrict__ oy, double *__restrict__ oz) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(c, g.n) {
         int i, j, k;
-        cell_ijk(c, g.nx, g.ny, i, j, k);
+        split3(g, (uint32_t)c, i, j, k);
         const bool fl = type[c] == FLUID;
         const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
         ox[c] = (fl && i > 0 && type[c - 1] == FLUID) ? g.dy[j] * g.dz[k] : 0.0;
@@ -428,9 +627,9 @@ __global__ void k_open_area_coarsen(int nx, int ny, int nz, const double *__rest
                                     int cnz, int fx, int fy, int fz, double *__restrict__ cx, double *__restrict__ cy,
                                     double *__restrict__ cz) {
     const int64_t cn = (int64_t)cnx * cny * cnz;
-    for (int64_t cc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cc < cn; cc += (int64_t)gridDim.x * blockDim.x) {
-        int I, J, K;
-        cell_ijk(cc, cnx, cny, I, J, K);
+    GRID_STRIDE(cc, cn) {
+        const int64_t t = cc / cnx;
+        const int I = (int)(cc - t * cnx), J = (int)(t % cny), K = (int)(t / cny);
         double ax = 0.0, ay = 0.0, az = 0.0;
         for (int dk = 0; dk < fz; ++dk) {
             const int k = fz * K + dk;
@@ -454,78 +653,131 @@ __global__ void k_open_area_coarsen(int nx, int ny, int nz, const double *__rest
     }
 }
 
-// T = open area / centre spacing, then D = sum of the six faces
+// T = open area / centre spacing
 template <typename T>
 __global__ void k_level_coef(int nx, int ny, int nz, const double *__restrict__ ox, const double *__restrict__ oy,
                              const double *__restrict__ oz, const double *__restrict__ hx,
                              const double *__restrict__ hy, const double *__restrict__ hz, T *__restrict__ tx,
                              T *__restrict__ ty, T *__restrict__ tz) {
     const int64_t n = (int64_t)nx * ny * nz;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, nx, ny, i, j, k);
+    GRID_STRIDE(c, n) {
+        const int64_t t = c / nx;
+        const int i = (int)(c - t * nx), j = (int)(t % ny), k = (int)(t / ny);
         tx[c] = i > 0 ? (T)(ox[c] / hx[i]) : T(0);
         ty[c] = j > 0 ? (T)(oy[c] / hy[j]) : T(0);
         tz[c] = k > 0 ? (T)(oz[c] / hz[k]) : T(0);
     }
 }
+// D = sum of the six faces; dinv = 1/D (0 when D = 0)
 template <typename T>
-__global__ void k_level_diag(MGLevel<T> L, T *__restrict__ D) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < L.n; c += (int64_t)gridDim.x * blockDim.x) {
-        int i, j, k;
-        cell_ijk(c, L.nx, L.ny, i, j, k);
+__global__ void k_level_diag(MGLevel<T> L) {
+    GRID_STRIDE(c, L.n) {
+        const int64_t t = c / L.nx;
+        const int i = (int)(c - t * L.nx), j = (int)(t % L.ny), k = (int)(t / L.ny);
         const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
         T d = L.tx[c] + L.ty[c] + L.tz[c];
         if (i < L.nx - 1) d += L.tx[c + 1];
         if (j < L.ny - 1) d += L.ty[c + sy];
         if (k < L.nz - 1) d += L.tz[c + sz];
-        D[c] = d;
+        L.d[c] = d;
+        L.dinv[c] = d > T(0) ? T(1) / d : T(0);
     }
+}
+
+// band: FLUID cells within two faces of a ghost cell, plus the ghosts
+__global__ void k_band_seed(int64_t n, const uint8_t *__restrict__ type, uint8_t *__restrict__ f) {
+    GRID_STRIDE(c, n) f[c] = type[c] == GHOST;
+}
+__global__ void k_band_dilate(GridDev g, const uint8_t *__restrict__ type, const uint8_t *__restrict__ in,
+                              uint8_t *__restrict__ out) {
+    GRID_STRIDE(c, g.n) {
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+        bool b = in[c];
+        if (!b && type[c] == FLUID) {
+            b = (i > 0 && in[c - 1]) || (i < g.nx - 1 && in[c + 1]) || (j > 0 && in[c - sy]) ||
+                (j < g.ny - 1 && in[c + sy]) || (k > 0 && in[c - sz]) || (k < g.nz - 1 && in[c + sz]);
+        }
+        out[c] = b;
+    }
+}
+// band_g[q] = position of band[q] in the ascending ghost list, or -1
+__global__ void k_band_gpos(int64_t nb, const int64_t *__restrict__ band, int64_t ng, const int64_t *__restrict__ gidx,
+                            int64_t *__restrict__ band_g) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    const int64_t c = band[q];
+    int64_t lo = 0, hi = ng;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (gidx[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    band_g[q] = (lo < ng && gidx[lo] == c) ? lo : -1;
 }
 
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 
-static inline unsigned nblk(int64_t n, int t = 256) {
-    int64_t b = (n + t - 1) / t;
-    return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
-}
-
-static inline dim3 rows_grid(int nx, int ny, int nz, int per_thread, int bx) {
-    int64_t rows = (int64_t)ny * nz;
-    int xs = (nx + per_thread - 1) / per_thread;
-    return dim3((unsigned)rows, (unsigned)((xs + bx - 1) / bx), 1);
+template <typename T>
+static ibm_status alloc_level_arrays(Ctx *c, MGLevel<T> &M, bool coeffs, bool vecs) {
+    const size_t bytes = sizeof(T) * (size_t)M.n;
+    M.tx = M.ty = M.tz = M.d = M.dinv = M.x = M.f = nullptr;
+    if (coeffs) {
+        M.tx = (T *)dev_alloc(c, bytes);
+        M.ty = (T *)dev_alloc(c, bytes);
+        M.tz = (T *)dev_alloc(c, bytes);
+        M.d = (T *)dev_alloc(c, bytes);
+        M.dinv = (T *)dev_alloc(c, bytes);
+        if (!M.tx || !M.ty || !M.tz || !M.d || !M.dinv) return c->fail(IBM_ERR_OOM, "multigrid level allocation failed");
+    }
+    if (vecs) {
+        M.x = (T *)dev_alloc(c, bytes);
+        M.f = (T *)dev_alloc(c, bytes);
+        if (!M.x || !M.f) return c->fail(IBM_ERR_OOM, "multigrid level allocation failed");
+    }
+    return IBM_OK;
 }
 
 template <typename T>
-static ibm_status build_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &oax,
-                             const std::vector<double *> &oay, const std::vector<double *> &oaz) {
+static T *upload_as(Ctx *c, const std::vector<double> &h, bool reciprocal) {
+    std::vector<T> v(h.size());
+    for (size_t i = 0; i < h.size(); ++i) v[i] = reciprocal ? (h[i] != 0.0 ? (T)(1.0 / h[i]) : T(0)) : (T)h[i];
+    T *d = (T *)dev_alloc(c, sizeof(T) * (v.size() ? v.size() : 1));
+    if (d && v.size()) cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return d;
+}
+
+template <typename T>
+static ibm_status build_hier(Ctx *c, MGHier<T> &H, bool fine0) {
     const int L = (int)c->lg.size();
     H.lv.resize(L);
-    H.dg.resize(L);
+    H.fine0 = fine0;
     for (int l = 0; l < L; ++l) {
         auto &G = c->lg[l];
         MGLevel<T> &M = H.lv[l];
+        M = MGLevel<T>{};
         M.nx = G.nx;
         M.ny = G.ny;
         M.nz = G.nz;
         M.n = (int64_t)G.nx * G.ny * G.nz;
-        const size_t bytes = sizeof(T) * (size_t)M.n;
-        M.tx = (T *)dev_alloc(c, bytes);
-        M.ty = (T *)dev_alloc(c, bytes);
-        M.tz = (T *)dev_alloc(c, bytes);
-        H.dg[l] = (T *)dev_alloc(c, bytes);
-        M.x = l == 0 ? nullptr : (T *)dev_alloc(c, bytes);
-        M.f = l == 0 ? nullptr : (T *)dev_alloc(c, bytes);
-        M.r = nullptr;
-        if (!M.tx || !M.ty || !M.tz || !H.dg[l] || (l > 0 && (!M.x || !M.f)))
-            return c->fail(IBM_ERR_OOM, "multigrid level allocation failed");
-        ++c->nlaunch, k_level_coef<T><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, oax[l], oay[l], oaz[l], c->lhx[l], c->lhy[l],
-                                                     c->lhz[l], M.tx, M.ty, M.tz);
-        IBM_LAUNCHED(c);
-        ++c->nlaunch, k_level_diag<T><<<nblk(M.n), 256, 0, c->s>>>(M, H.dg[l]);
-        IBM_LAUNCHED(c);
+        M.fnx = FastDiv((uint32_t)G.nx);
+        M.fny = FastDiv((uint32_t)G.ny);
+        IBM_TRY(alloc_level_arrays(c, M, !(l == 0 && fine0), l > 0));
+    }
+    if (fine0) {
+        H.wx = upload_as<T>(c, c->hdx, false);
+        H.wy = upload_as<T>(c, c->hdy, false);
+        H.wz = upload_as<T>(c, c->hdz, false);
+        H.rhx = upload_as<T>(c, c->hhx, true);
+        H.rhy = upload_as<T>(c, c->hhy, true);
+        H.rhz = upload_as<T>(c, c->hhz, true);
+        if (!H.wx || !H.wy || !H.wz || !H.rhx || !H.rhy || !H.rhz) return c->fail(IBM_ERR_OOM, "metric allocation failed");
+        MGLevel<T> &M = H.lv[0];
+        M.type = c->type;
+        M.wx = H.wx; M.wy = H.wy; M.wz = H.wz;
+        M.rhx = H.rhx; M.rhy = H.rhy; M.rhz = H.rhz;
     }
     const size_t b0 = sizeof(T) * (size_t)c->N;
     H.px = (T *)dev_alloc(c, b0);
@@ -538,8 +790,28 @@ static ibm_status build_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &
     return IBM_OK;
 }
 
-// Multigrid hierarchy of the staircase operator for the current
-// classification. Level geometry (c->lg, c->lh*) is built at grid creation.
+template <typename T>
+static ibm_status fill_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &ox, const std::vector<double *> &oy,
+                            const std::vector<double *> &oz) {
+    const int L = (int)H.lv.size();
+    for (int l = 0; l < L; ++l) {
+        MGLevel<T> &M = H.lv[l];
+        if (l == 0 && H.fine0) {
+            M.type = c->type;
+            continue;
+        }
+        KL(-1, k_level_coef<T>, nblk(M.n), 256, M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l], c->lhy[l],
+           c->lhz[l], M.tx, M.ty, M.tz);
+        KL(-1, k_level_diag<T>, nblk(M.n), 256, M);
+        IBM_LAUNCHED(c);
+    }
+    return IBM_OK;
+}
+
+ibm_status compact_flags(Ctx *c, const uint8_t *flags, int64_t **out, int64_t *count);
+
+// Multigrid hierarchies of the staircase operator and the near-body band for
+// the current classification.
 ibm_status mg_build(Ctx *c) {
     const int L = (int)c->lg.size();
     std::vector<double *> ox(L), oy(L), oz(L);
@@ -550,39 +822,45 @@ ibm_status mg_build(Ctx *c) {
         oz[l] = (double *)dev_alloc(c, sizeof(double) * n);
         if (!ox[l] || !oy[l] || !oz[l]) return c->fail(IBM_ERR_OOM, "open-area allocation failed");
     }
-    ++c->nlaunch, k_open_area0<<<nblk(c->N), 256, 0, c->s>>>(c->g, c->type, ox[0], oy[0], oz[0]);
+    KL(-1, k_open_area0, nblk(c->N), 256, c->g, c->type, ox[0], oy[0], oz[0]);
     IBM_LAUNCHED(c);
     for (int l = 1; l < L; ++l) {
         auto &F = c->lg[l - 1];
         auto &C = c->lg[l];
         const int64_t n = (int64_t)C.nx * C.ny * C.nz;
-        ++c->nlaunch, k_open_area_coarsen<<<nblk(n), 256, 0, c->s>>>(F.nx, F.ny, F.nz, ox[l - 1], oy[l - 1], oz[l - 1], C.nx, C.ny,
-                                                        C.nz, C.fx, C.fy, C.fz, ox[l], oy[l], oz[l]);
+        KL(-1, k_open_area_coarsen, nblk(n), 256, F.nx, F.ny, F.nz, ox[l - 1], oy[l - 1], oz[l - 1], C.nx, C.ny, C.nz,
+           C.fx, C.fy, C.fz, ox[l], oy[l], oz[l]);
         IBM_LAUNCHED(c);
     }
-    if (!c->mg64.built) IBM_TRY(build_hier<double>(c, c->mg64, ox, oy, oz));
-    else {
-        for (int l = 0; l < L; ++l) {
-            auto &M = c->mg64.lv[l];
-            ++c->nlaunch, k_level_coef<double><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
-                                                              c->lhy[l], c->lhz[l], M.tx, M.ty, M.tz);
-            ++c->nlaunch, k_level_diag<double><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg64.dg[l]);
-        }
-        IBM_LAUNCHED(c);
-    }
+    if (!c->mg64.built) IBM_TRY(build_hier<double>(c, c->mg64, false));
+    IBM_TRY(fill_hier<double>(c, c->mg64, ox, oy, oz));
     if (c->opts.precision == IBM_MIXED) {
-        if (!c->mg32.built) IBM_TRY(build_hier<float>(c, c->mg32, ox, oy, oz));
-        else {
-            for (int l = 0; l < L; ++l) {
-                auto &M = c->mg32.lv[l];
-                ++c->nlaunch, k_level_coef<float><<<nblk(M.n), 256, 0, c->s>>>(M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l],
-                                                                 c->lhy[l], c->lhz[l], M.tx, M.ty, M.tz);
-                ++c->nlaunch, k_level_diag<float><<<nblk(M.n), 256, 0, c->s>>>(M, c->mg32.dg[l]);
-            }
-            IBM_LAUNCHED(c);
-        }
+        if (!c->mg32.built) IBM_TRY(build_hier<float>(c, c->mg32, true));
+        IBM_TRY(fill_hier<float>(c, c->mg32, ox, oy, oz));
+    }
+    // near-body band
+    uint8_t *f0 = (uint8_t *)dev_alloc(c, c->N), *f1 = (uint8_t *)dev_alloc(c, c->N);
+    if (!f0 || !f1) return c->fail(IBM_ERR_OOM, "band flag allocation failed");
+    KL(-1, k_band_seed, nblk(c->N), 256, c->N, c->type, f0);
+    KL(-1, k_band_dilate, nblk(c->N), 256, c->g, c->type, f0, f1);
+    KL(-1, k_band_dilate, nblk(c->N), 256, c->g, c->type, f1, f0);
+    IBM_LAUNCHED(c);
+    dev_free(c, c->band);
+    dev_free(c, c->band_g);
+    dev_free(c, c->btmp);
+    c->band = c->band_g = nullptr;
+    c->btmp = nullptr;
+    IBM_TRY(compact_flags(c, f0, &c->band, &c->nband));
+    c->band_g = (int64_t *)dev_alloc(c, sizeof(int64_t) * (c->nband > 0 ? c->nband : 1));
+    c->btmp = (double *)dev_alloc(c, sizeof(double) * (c->nband > 0 ? c->nband : 1));
+    if (!c->band_g || !c->btmp) return c->fail(IBM_ERR_OOM, "band allocation failed");
+    if (c->nband > 0) {
+        KL(-1, k_band_gpos, (unsigned)((c->nband + 255) / 256), 256, c->nband, c->band, c->ng, c->gidx, c->band_g);
+        IBM_LAUNCHED(c);
     }
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    dev_free(c, f0);
+    dev_free(c, f1);
     for (int l = 0; l < L; ++l) {
         dev_free(c, ox[l]);
         dev_free(c, oy[l]);
@@ -595,9 +873,9 @@ template <typename T>
 static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col) {
     MGLevel<T> &L = H.lv[l];
     const int bx = 128;
-    kt_begin(c, l == 0 ? K_RBGS0 : K_RBGS_C);
-    ++c->nlaunch, k_rbgs<T><<<rows_grid(L.nx, L.ny, L.nz, 2, bx), bx, 0, c->s>>>(L, H.dg[l], f, x, col);
-    kt_end(c, l == 0 ? K_RBGS0 : K_RBGS_C);
+    const dim3 grid = rows_grid(L.nx, L.ny, L.nz, 2, bx);
+    if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true>), grid, bx, L, f, x, col);
+    else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false>), grid, bx, L, f, x, col);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -606,8 +884,13 @@ template <typename T>
 static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     const int L = (int)H.lv.size();
     const int nu1 = c->opts.nu1, nu2 = c->opts.nu2, cs = c->opts.coarse_sweeps;
-    IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
     const int bx = 128;
+    if (L == 1) {
+        KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[0], f0, x0, cs);
+        IBM_LAUNCHED(c);
+        return IBM_OK;
+    }
+    IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
     for (int l = 0; l < L - 1; ++l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
@@ -615,37 +898,24 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             IBM_TRY(rbgs(c, H, l, f, x, 0));
             IBM_TRY(rbgs(c, H, l, f, x, 1));
         }
-        MGLevel<T> Lf = H.lv[l];
+        MGLevel<T> &Lf = H.lv[l];
         MGLevel<T> &Cl = H.lv[l + 1];
         auto &CG = c->lg[l + 1];
-        kt_begin(c, K_RESTRICT);
-        ++c->nlaunch, k_resid_restrict<T><<<rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], f, x, Cl, CG.fx,
-                                                                                     CG.fy, CG.fz);
-        kt_end(c, K_RESTRICT);
+        const dim3 grid = rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx);
+        if (l == 0 && H.fine0) KL(K_RESTRICT, (k_resid_restrict<T, true>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
+        else KL(K_RESTRICT, (k_resid_restrict<T, false>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
         IBM_LAUNCHED(c);
     }
-    {
-        const int l = L - 1;
-        const T *f = l == 0 ? f0 : H.lv[l].f;
-        T *x = l == 0 ? x0 : H.lv[l].x;
-        for (int s = 0; s < cs; ++s) {
-            IBM_TRY(rbgs(c, H, l, f, x, 0));
-            IBM_TRY(rbgs(c, H, l, f, x, 1));
-        }
-        for (int s = 0; s < cs; ++s) {
-            IBM_TRY(rbgs(c, H, l, f, x, 1));
-            IBM_TRY(rbgs(c, H, l, f, x, 0));
-        }
-    }
+    KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
+    IBM_LAUNCHED(c);
     for (int l = L - 2; l >= 0; --l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         MGLevel<T> &Lf = H.lv[l];
         auto &CG = c->lg[l + 1];
-        kt_begin(c, K_PROLONG);
-        ++c->nlaunch, k_prolong<T><<<rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx), bx, 0, c->s>>>(Lf, H.dg[l], x, H.lv[l + 1], CG.fx, CG.fy,
-                                                                              CG.fz);
-        kt_end(c, K_PROLONG);
+        const dim3 grid = rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx);
+        if (l == 0 && H.fine0) KL(K_PROLONG, (k_prolong<T, true>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
+        else KL(K_PROLONG, (k_prolong<T, false>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
         IBM_LAUNCHED(c);
         for (int s = 0; s < nu2; ++s) {
             IBM_TRY(rbgs(c, H, l, f, x, 1));
@@ -664,23 +934,21 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
     IBM_CUDA(c, cudaMemsetAsync(H.px, 0, sizeof(T) * (size_t)n, c->s));
     IBM_TRY(vcycle(c, H, H.pr, H.pz));
     IBM_CUDA(c, cudaMemcpyAsync(H.pp, H.pz, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, c->s));
-    ++c->nlaunch, k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZ);
-    IBM_LAUNCHED(c);
+    KL(-1, k_dot<T>, RED_BLOCKS, RED_THREADS, n, H.pr, H.pz, c->part);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZ));
     for (int it = 0; it < iters; ++it) {
-        kt_begin(c, K_SPMV0);
-        ++c->nlaunch, k_spmv_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(L0, H.dg[0], H.pp, H.pq, c->part);
-        kt_end(c, K_SPMV0);
-        ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_PQ);
-        ++c->nlaunch, k_alpha<<<1, 1, 0, c->s>>>(c->scal);
-        ++c->nlaunch, k_axpy2<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.px, H.pr, H.pp, H.pq, c->scal);
+        if (H.fine0) KL(K_SPMV0, (k_spmv_dot<T, true>), RED_BLOCKS, RED_THREADS, L0, H.pp, H.pq, c->part);
+        else KL(K_SPMV0, (k_spmv_dot<T, false>), RED_BLOCKS, RED_THREADS, L0, H.pp, H.pq, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_PQ));
+        KL(-1, k_alpha, 1, 1, c->scal);
+        KL(-1, k_axpy2<T>, RED_BLOCKS, RED_THREADS, n, H.px, H.pr, H.pp, H.pq, c->scal);
         IBM_LAUNCHED(c);
         if (it + 1 < iters) {
             IBM_TRY(vcycle(c, H, H.pr, H.pz));
-            ++c->nlaunch, k_dot<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pr, H.pz, c->part);
-            ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZN);
-            ++c->nlaunch, k_beta<<<1, 1, 0, c->s>>>(c->scal);
-            ++c->nlaunch, k_pupd<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, H.pp, H.pz, c->scal);
+            KL(-1, k_dot<T>, RED_BLOCKS, RED_THREADS, n, H.pr, H.pz, c->part);
+            IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZN));
+            KL(-1, k_beta, 1, 1, c->scal);
+            KL(-1, k_pupd<T>, RED_BLOCKS, RED_THREADS, n, H.pp, H.pz, c->scal);
             IBM_LAUNCHED(c);
         }
     }
@@ -690,14 +958,23 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 // z = M^{-1} v : FP64 in, FP64 out
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const double *v, double *z) {
-    ++c->nlaunch, k_pre_in<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, v, H.pr);
+    KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     IBM_TRY(pcg(c, H, c->opts.inner_iters));
-    ++c->nlaunch, k_pre_out<T><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, c->type, H.px, z);
+    KL(-1, k_pre_out<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, H.px, z);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        ++c->nlaunch, k_pre_ghost<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->gh, c->type, v, z);
+        KL(-1, k_pre_ghost, (unsigned)((c->ng + 255) / 256), 256, c->gh, c->type, v, z);
         IBM_LAUNCHED(c);
+    }
+    if (c->nband > 0) {
+        const unsigned gb = (unsigned)((c->nband + 255) / 256);
+        for (int s = 0; s < c->opts.band_sweeps; ++s) {
+            KL(-1, k_band_jacobi, gb, 256, c->g, c->gh, c->nband, c->band, c->band_g, v, z, c->opts.band_omega,
+               c->btmp);
+            KL(-1, k_band_scatter, gb, 256, c->nband, c->band, c->btmp, z);
+            IBM_LAUNCHED(c);
+        }
     }
     return IBM_OK;
 }
@@ -709,30 +986,181 @@ static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
 
 // ||x||^2 over all cells
 static ibm_status norm2(Ctx *c, const double *x, double *out) {
-    ++c->nlaunch, k_dot<double><<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->N, x, x, c->part);
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
-    IBM_LAUNCHED(c);
+    KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, c->N, x, x, c->part);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
     IBM_TRY(sync_scalars(c, S_TMP + 1));
     *out = c->hscal[S_TMP];
     return IBM_OK;
+}
+
+// restarted FGMRES; returns outer iterations, relative residual, status
+static ibm_status fgmres(Ctx *c, double *phi, double bnorm, double rtol, int maxit, int *outer_out, int *inner_out,
+                         double *rel_out) {
+    const int64_t n = c->N;
+    const int m = c->opts.restart;
+    int outer = 0, inner = 0;
+    double rel = 0.0;
+    ibm_status status = IBM_OK;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    bool done = false;
+    while (!done) {
+        IBM_TRY(apply_PA(c, phi, c->b, -1.0, c->rr));
+        double rn2;
+        IBM_TRY(norm2(c, c->rr, &rn2));
+        const double beta = sqrt(rn2);
+        rel = beta / bnorm;
+        if (!isfinite(rel)) { status = c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite"); break; }
+        if (rel <= rtol) break;
+        if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
+        KL(-1, k_scale, RED_BLOCKS, RED_THREADS, n, c->V[0], c->rr, 1.0 / beta);
+        IBM_LAUNCHED(c);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int jlast = -1;
+        for (int j = 0; j < m && outer < maxit; ++j) {
+            IBM_TRY(apply_prec(c, c->V[j], c->Z[j]));
+            inner += c->opts.inner_iters;
+            IBM_TRY(apply_PA(c, c->Z[j], nullptr, 1.0, c->w));
+            // classical Gram-Schmidt, with a second pass when the norm drops
+            // by more than a factor 0.7 (Daniel, Gragg, Kaufman, Stewart 1976)
+            double hcol[17] = {0};
+            double wbefore2 = 0.0, wafter2 = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                KL(K_MDOT, k_mdot, RED_BLOCKS, RED_THREADS, n, c->w, (const double *const *)c->Vdev, j + 1, c->part);
+                IBM_TRY(finalize(c, c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD));
+                IBM_TRY(sync_scalars(c, S_MD + j + 2));
+                Coef h{};
+                for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
+                wbefore2 = c->hscal[S_MD + j + 1];
+                KL(K_ORTH, k_orth, RED_BLOCKS, RED_THREADS, n, c->w, (const double *const *)c->Vdev, j + 1, h, c->part);
+                IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
+                IBM_TRY(sync_scalars(c, S_TMP + 1));
+                wafter2 = c->hscal[S_TMP];
+                for (int i = 0; i <= j; ++i) hcol[i] += h.v[i];
+                if (wafter2 > 0.49 * wbefore2) break;
+            }
+            const double hn = sqrt(wafter2);
+            ++outer;
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (!isfinite(hn)) { status = c->fail(IBM_ERR_DIVERGED, "FGMRES breakdown (non-finite)"); done = true; break; }
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            const double rho = hypot(a, bb);
+            cs[j] = rho > 0 ? a / rho : 1.0;
+            sn[j] = rho > 0 ? bb / rho : 0.0;
+            H[(size_t)j * m + j] = rho;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            jlast = j;
+            const double est = fabs(gv[j + 1]) / bnorm;
+            if (hn > 0.0 && j + 1 < m) {
+                KL(-1, k_scale, RED_BLOCKS, RED_THREADS, n, c->V[j + 1], c->w, 1.0 / hn);
+                IBM_LAUNCHED(c);
+            }
+            if (est <= rtol || hn == 0.0) break;
+        }
+        if (done) break;
+        if (jlast < 0) { status = IBM_ERR_NOT_CONVERGED; break; }
+        for (int i = jlast; i >= 0; --i) {
+            double s = gv[i];
+            for (int k = i + 1; k <= jlast; ++k) s -= H[(size_t)i * m + k] * y[k];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        Coef yc{};
+        for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
+        KL(-1, k_xupd, RED_BLOCKS, RED_THREADS, n, phi, (const double *const *)c->Zdev, jlast + 1, yc);
+        IBM_LAUNCHED(c);
+    }
+    *outer_out = outer;
+    *inner_out = inner;
+    *rel_out = rel;
+    return status;
+}
+
+// BiCGStab (van der Vorst 1992) with right preconditioning; scalars stay on
+// the device; one host synchronisation per iteration for the stopping test.
+// A breakdown (rho, (rh, v) or omega zero) restarts from the true residual.
+static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int maxit, int *outer_out,
+                           int *inner_out, double *rel_out) {
+    const int64_t n = c->N;
+    double *r = c->V[0], *rh = c->V[1], *p = c->V[2], *v = c->V[3], *sv = c->V[4], *t = c->V[5];
+    double *ph = c->Z[0], *shv = c->Z[1];
+    int it = 0, inner = 0;
+    double rel = 1.0;
+    ibm_status status = IBM_OK;
+    bool fresh = true;
+    while (true) {
+        if (fresh) {
+            // true residual
+            IBM_TRY(apply_PA(c, phi, c->b, -1.0, r));
+            double rn2;
+            IBM_TRY(norm2(c, r, &rn2));
+            rel = sqrt(rn2) / bnorm;
+            if (!isfinite(rel)) return c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite");
+            if (rel <= rtol) break;
+            if (it >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
+            IBM_CUDA(c, cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+            IBM_CUDA(c, cudaMemsetAsync(p, 0, sizeof(double) * n, c->s));
+            IBM_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * n, c->s));
+            KL(-1, k_bicg_init, 1, 1, c->scal);
+            IBM_LAUNCHED(c);
+            fresh = false;
+        }
+        // rho1 = (rh, r); beta; p = r + beta (p - omega v)
+        KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, n, rh, r, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + B_RHO1));
+        KL(-1, k_bicg_beta, 1, 1, c->scal);
+        KL(-1, k_bicg_p, RED_BLOCKS, RED_THREADS, n, r, p, v, c->scal);
+        IBM_LAUNCHED(c);
+        IBM_TRY(apply_prec(c, p, ph));
+        IBM_TRY(apply_PA(c, ph, nullptr, 1.0, v));
+        KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, n, rh, v, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + B_DEN));
+        KL(-1, k_bicg_alpha, 1, 1, c->scal);
+        KL(-1, k_bicg_s, RED_BLOCKS, RED_THREADS, n, r, v, sv, c->scal);
+        IBM_LAUNCHED(c);
+        IBM_TRY(apply_prec(c, sv, shv));
+        IBM_TRY(apply_PA(c, shv, nullptr, 1.0, t));
+        KL(-1, k_bicg_tdots, RED_BLOCKS, RED_THREADS, n, t, sv, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + B_TS));
+        KL(-1, k_bicg_omega, 1, 1, c->scal);
+        KL(-1, k_bicg_xr, RED_BLOCKS, RED_THREADS, n, phi, ph, shv, r, sv, t, c->scal, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
+        IBM_LAUNCHED(c);
+        inner += 2 * c->opts.inner_iters;
+        ++it;
+        IBM_TRY(sync_scalars(c, B_FLAG + 1));
+        const double rr = sqrt(c->hscal[S_TMP]) / bnorm;
+        if (!isfinite(rr)) return c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite");
+        // converged by the recurrence, breakdown or limit: check the true residual
+        if (rr <= rtol || c->hscal[B_FLAG] != 0.0 || it >= maxit) fresh = true;
+    }
+    *outer_out = it;
+    *inner_out = inner;
+    *rel_out = rel;
+    return status;
 }
 
 // Solve P A phi = P rhs. rhs: FLUID rows read; phi: guess in, solution out.
 ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, int maxit, ibm_solve_stats *st) {
     if (!c->mg64.built || (c->opts.precision == IBM_MIXED && !c->mg32.built)) IBM_TRY(mg_build(c));
     const int64_t n = c->N;
-    const int m = c->opts.restart;
     IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
     // b = P rhs on FLUID rows, 0 elsewhere
-    ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, c->part);
-    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
-    IBM_LAUNCHED(c);
+    KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, rhs, c->part);
+    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, c->b, c->scal + S_MEAN, 0);
+    KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     // GHOST rows of b are 0 (homogeneous Neumann on the body)
     if (c->ng > 0) {
-        ++c->nlaunch, k_zero_at<<<(unsigned)((c->ng + 255) / 256), 256, 0, c->s>>>(c->ng, c->gidx, c->b);
+        KL(-1, k_zero_at, (unsigned)((c->ng + 255) / 256), 256, c->ng, c->gidx, c->b);
         IBM_LAUNCHED(c);
     }
     double bn2;
@@ -743,101 +1171,17 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     ibm_status status = IBM_OK;
     if (!(bnorm > 1e-300)) {
         IBM_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * n, c->s));
-        rel = 0.0;
     } else {
-        std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-        bool done = false;
-        while (!done) {
-            // r = P(b - A phi)
-            IBM_TRY(apply_PA(c, phi, c->b, -1.0, c->rr));
-            double rn2;
-            IBM_TRY(norm2(c, c->rr, &rn2));
-            const double beta = sqrt(rn2);
-            rel = beta / bnorm;
-            if (!isfinite(rel)) { status = c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite"); break; }
-            if (rel <= rtol) break;
-            if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
-            ++c->nlaunch, k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[0], c->rr, 1.0 / beta);
-            IBM_LAUNCHED(c);
-            std::fill(gv.begin(), gv.end(), 0.0);
-            gv[0] = beta;
-            int jlast = -1;
-            for (int j = 0; j < m && outer < maxit; ++j) {
-                IBM_TRY(apply_prec(c, c->V[j], c->Z[j]));
-                inner += c->opts.inner_iters;
-                IBM_TRY(apply_PA(c, c->Z[j], nullptr, 1.0, c->w));
-                // classical Gram-Schmidt, once, with a second pass when the
-                // norm drops by more than 0.7 (Daniel-Gragg-Kaufman-Stewart)
-                double hcol[17] = {0};
-                double wbefore2 = 0.0, wafter2 = 0.0;
-                for (int pass = 0; pass < 2; ++pass) {
-                    kt_begin(c, K_MDOT);
-                    ++c->nlaunch, k_mdot<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1,
-                                                                  c->part);
-                    kt_end(c, K_MDOT);
-                    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD);
-                    IBM_LAUNCHED(c);
-                    IBM_TRY(sync_scalars(c, S_MD + j + 2));
-                    Coef h{};
-                    for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
-                    wbefore2 = c->hscal[S_MD + j + 1];
-                    kt_begin(c, K_ORTH);
-                    ++c->nlaunch, k_orth<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->w, (const double *const *)c->Vdev, j + 1, h,
-                                                                  c->part);
-                    kt_end(c, K_ORTH);
-                    ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP);
-                    IBM_LAUNCHED(c);
-                    IBM_TRY(sync_scalars(c, S_TMP + 1));
-                    wafter2 = c->hscal[S_TMP];
-                    for (int i = 0; i <= j; ++i) hcol[i] += h.v[i];
-                    if (wafter2 > 0.49 * wbefore2) break;
-                }
-                const double hn = sqrt(wafter2);
-                ++outer;
-                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-                H[(size_t)(j + 1) * m + j] = hn;
-                if (!isfinite(hn)) { status = c->fail(IBM_ERR_DIVERGED, "FGMRES breakdown (non-finite)"); done = true; break; }
-                // apply previous rotations to column j
-                for (int i = 0; i < j; ++i) {
-                    const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-                    H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
-                    H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-                }
-                const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
-                const double rho = hypot(a, bb);
-                cs[j] = rho > 0 ? a / rho : 1.0;
-                sn[j] = rho > 0 ? bb / rho : 0.0;
-                H[(size_t)j * m + j] = rho;
-                H[(size_t)(j + 1) * m + j] = 0.0;
-                gv[j + 1] = -sn[j] * gv[j];
-                gv[j] = cs[j] * gv[j];
-                jlast = j;
-                const double est = fabs(gv[j + 1]) / bnorm;
-                if (hn > 0.0 && j + 1 < m) {
-                    ++c->nlaunch, k_scale<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->V[j + 1], c->w, 1.0 / hn);
-                    IBM_LAUNCHED(c);
-                }
-                if (est <= rtol || hn == 0.0) break;
-            }
-            if (done) break;
-            if (jlast < 0) { status = IBM_ERR_NOT_CONVERGED; break; }
-            // back substitution H y = g
-            for (int i = jlast; i >= 0; --i) {
-                double s = gv[i];
-                for (int k = i + 1; k <= jlast; ++k) s -= H[(size_t)i * m + k] * y[k];
-                y[i] = s / H[(size_t)i * m + i];
-            }
-            Coef yc{};
-            for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
-            ++c->nlaunch, k_xupd<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, phi, (const double *const *)c->Zdev, jlast + 1, yc);
-            IBM_LAUNCHED(c);
-        }
+        if (c->opts.outer == IBM_OUTER_FGMRES) status = fgmres(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
+        else status = bicgstab(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
+        if (status != IBM_OK && status != IBM_ERR_NOT_CONVERGED) return status;
         // normalise: zero volume-weighted FLUID mean, shift ghosts too
-        ++c->nlaunch, k_fluid_volsum<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, phi, c->part);
-        ++c->nlaunch, k_finalize<<<1, RED_THREADS, 0, c->s>>>(c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN);
-        ++c->nlaunch, k_sub_mean<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(n, c->type, phi, c->scal + S_MEAN, 1);
+        KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, phi, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+        KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
         IBM_LAUNCHED(c);
     }
+    IBM_TRY(kt_flush(c));
     IBM_CUDA(c, cudaEventRecord(c->ev1, c->s));
     IBM_CUDA(c, cudaEventSynchronize(c->ev1));
     float ms = 0.f;
@@ -849,8 +1193,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
         st->lambda_est = 0.0;
         st->ms = ms;
     }
-    if (status == IBM_ERR_NOT_CONVERGED)
-        c->fail(IBM_ERR_NOT_CONVERGED, "Poisson solve reached its iteration limit");
+    if (status == IBM_ERR_NOT_CONVERGED) c->fail(IBM_ERR_NOT_CONVERGED, "Poisson solve reached its iteration limit");
     return status;
 }
 

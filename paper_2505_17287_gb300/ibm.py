@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_OOM", 3: "IBM_ERR_CUD
 IBM_FLUID, IBM_GHOST, IBM_DEAD = 0, 1, 2
 IBM_BC_INFLOW, IBM_BC_OUTFLOW, IBM_BC_SLIP = 0, 1, 2
 IBM_FP64, IBM_MIXED = 0, 1
+IBM_OUTER_BICGSTAB, IBM_OUTER_FGMRES = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "face_u": 4, "face_v": 5, "face_w": 6, "nold_u": 7, "nold_v": 8,
           "nold_w": 9, "type": 10, "ustar_u": 11, "ustar_v": 12, "ustar_w": 13, "rhs": 14, "step": 15}
 
@@ -43,7 +44,8 @@ class ibm_grid_desc(Structure):
 class ibm_solver_opts(Structure):
     _fields_ = [("rtol", c_double), ("max_outer", c_int), ("restart", c_int), ("inner_iters", c_int),
                 ("nu1", c_int), ("nu2", c_int), ("coarse_sweeps", c_int), ("helm_rtol", c_double),
-                ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int)]
+                ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
+                ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double)]
 
 
 class ibm_table_info(Structure):
