@@ -101,6 +101,8 @@ typedef struct {
     int band_sweeps;    /* damped Jacobi sweeps of the full operator near the body, per
                            preconditioner call (0 = none) */
     double band_omega;  /* their damping factor, in (0, 1] */
+    double mixed_inner_rtol; /* IBM_MIXED with FGMRES: residual reduction asked of each
+                           FP32 Krylov solve inside the FP64 defect correction */
 } ibm_solver_opts;
 
 typedef struct {
@@ -153,10 +155,10 @@ enum {
     IBM_FIELD_STEP = 15                                   /* int64 step counter, 1 value */
 };
 
-/* Defaults: rtol 1e-10, max_outer 200, restart 8, inner_iters 1, nu1 = nu2 = 2,
+/* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
-   ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_BICGSTAB, band_sweeps 4,
-   band_omega 0.7. */
+   ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
+   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

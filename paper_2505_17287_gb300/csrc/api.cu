@@ -83,8 +83,8 @@ static void release_all(Ctx *c) {
 extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     if (!o) return IBM_ERR_ARG;
     o->rtol = 1e-10;
-    o->max_outer = 200;
-    o->restart = 8;
+    o->max_outer = 400;
+    o->restart = 16;
     o->inner_iters = 1;
     o->nu1 = 2;
     o->nu2 = 2;
@@ -94,9 +94,10 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->ghost_tol = 1e-15;
     o->ghost_maxit = 100;
     o->precision = IBM_FP64;
-    o->outer = IBM_OUTER_BICGSTAB;
-    o->band_sweeps = 4;
+    o->outer = IBM_OUTER_FGMRES;
+    o->band_sweeps = 0;
     o->band_omega = 0.7;
+    o->mixed_inner_rtol = 1e-4;
     return IBM_OK;
 }
 
@@ -113,6 +114,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->outer != IBM_OUTER_BICGSTAB && o->outer != IBM_OUTER_FGMRES) { why = "unknown outer method"; return false; }
     if (o->band_sweeps < 0 || o->band_sweeps > 64) { why = "band_sweeps must be in [0, 64]"; return false; }
     if (!(o->band_omega > 0.0 && o->band_omega <= 1.0)) { why = "band_omega must be in (0, 1]"; return false; }
+    if (!(o->mixed_inner_rtol > 0.0 && o->mixed_inner_rtol < 1.0)) { why = "mixed_inner_rtol must be in (0, 1)"; return false; }
     return true;
 }
 
@@ -405,6 +407,7 @@ extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
     if (!c) return IBM_ERR_ARG;
     if (c->ne == 0) return c->fail(IBM_ERR_STATE, "ibm_set_body must be called before ibm_classify_cells");
     IBM_TRY(geom_classify(c));
+    c->wp32_n = -1;  // FP32 copies of the ghost weights are stale
     if (c->n_fluid == 0) return c->fail(IBM_ERR_ARG, "no fluid cells");
     // FLUID volume
     double vol = 0.0;

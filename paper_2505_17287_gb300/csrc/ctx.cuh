@@ -103,6 +103,14 @@ struct Ctx {
     std::vector<double *> V, Z;
     double **Vdev = nullptr, **Zdev = nullptr;   // device arrays of the V / Z pointers
     double *w = nullptr, *rr = nullptr;
+    // FP32 storage of mixed mode
+    float *op32[12] = {nullptr};         // cxm..czs, dx, dy, dz in FP32
+    float *wp32 = nullptr;
+    int64_t wp32_n = -1;
+    std::vector<float *> V32, Z32;
+    float **Vdev32 = nullptr, **Zdev32 = nullptr;
+    float *w32 = nullptr, *r32 = nullptr, *d32 = nullptr, *b32 = nullptr;
+    int m32_cap = 0;
     // near-body band for the preconditioner's local relaxation
     int64_t nband = 0;
     int64_t *band = nullptr;      // cell index

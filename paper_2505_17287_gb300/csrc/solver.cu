@@ -130,52 +130,63 @@ ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_hos
 // full ghost-cell pressure operator (FP64)
 // ---------------------------------------------------------------------------
 
+// per-axis operator coefficients in precision T (the FP64 ones are the
+// GridDev arrays; FP32 copies serve the FP32 Krylov cycle of mixed mode)
+template <typename T>
+struct OpT {
+    const T *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
+    const T *dx, *dy, *dz;
+    const T *wp;     // ghost weights, 8 per ghost
+};
+
 // (A x)_c of a FLUID cell with the per-axis coefficients; boundary faces
 // have coefficient 0, so a wall reads the cell itself
-__device__ __forceinline__ double A_row(const GridDev &g, const double *__restrict__ x, int64_t c, int i, int j,
-                                        int k) {
+template <typename T>
+__device__ __forceinline__ T A_row(const GridDev &g, const OpT<T> &o, const T *__restrict__ x, int64_t c, int i,
+                                   int j, int k) {
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    const double xc = x[c];
-    const double xm = i > 0 ? x[c - 1] : xc, xp = i < g.nx - 1 ? x[c + 1] : xc;
-    const double ym = j > 0 ? x[c - sy] : xc, yp = j < g.ny - 1 ? x[c + sy] : xc;
-    double s = g.cxm[i] * xm + g.cxp[i] * xp + g.cym[j] * ym + g.cyp[j] * yp;
-    double dsum = g.cxs[i] + g.cys[j];
+    const T xc = x[c];
+    const T xm = i > 0 ? x[c - 1] : xc, xp = i < g.nx - 1 ? x[c + 1] : xc;
+    const T ym = j > 0 ? x[c - sy] : xc, yp = j < g.ny - 1 ? x[c + sy] : xc;
+    T s = o.cxm[i] * xm + o.cxp[i] * xp + o.cym[j] * ym + o.cyp[j] * yp;
+    T dsum = o.cxs[i] + o.cys[j];
     if (g.ndim == 3) {
-        const double zm = k > 0 ? x[c - sz] : xc, zp = k < g.nz - 1 ? x[c + sz] : xc;
-        s += g.czm[k] * zm + g.czp[k] * zp;
-        dsum += g.czs[k];
+        const T zm = k > 0 ? x[c - sz] : xc, zp = k < g.nz - 1 ? x[c + sz] : xc;
+        s += o.czm[k] * zm + o.czp[k] * zp;
+        dsum += o.czs[k];
     }
     return s - dsum * xc;
 }
 
 // y = sgn * (A x) + b  on FLUID and DEAD rows (b may be null = 0); GHOST rows
-// are written by k_ghost_rows. Partials: sum over FLUID of vol * y.
-__global__ void k_apply_A(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ x,
-                          const double *__restrict__ b, double sgn, double *__restrict__ y,
-                          double *__restrict__ part) {
+// are written by k_ghost_rows. Partials (FP64): sum over FLUID of vol * y.
+template <typename T>
+__global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, const T *__restrict__ x,
+                          const T *__restrict__ b, T sgn, T *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
     double acc = 0.0;
     GRID_STRIDE(c, g.n) {
         const uint8_t t = type[c];
         if (t == GHOST) continue;
-        if (t == DEAD) { y[c] = 0.0; continue; }
+        if (t == DEAD) { y[c] = T(0); continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double v = sgn * A_row(g, x, c, i, j, k) + (b ? b[c] : 0.0);
+        const T v = sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
         y[c] = v;
-        acc += (g.dx[i] * g.dy[j] * g.dz[k]) * v;
+        acc += (double)(o.dx[i] * o.dy[j] * o.dz[k]) * (double)v;
     }
     acc = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 // GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m)   (b_g = 0)
-__global__ void k_ghost_rows(GhostDev gh, const double *__restrict__ x, double sgn, double *__restrict__ y) {
+template <typename T>
+__global__ void k_ghost_rows(GhostDev gh, OpT<T> o, const T *__restrict__ x, T sgn, T *__restrict__ y) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= gh.ng) return;
     const int64_t gi = gh.gidx[q];
-    double s = x[gi];
-    for (int m = 0; m < 8; ++m) s -= gh.wp[8 * q + m] * x[gh.sidx[8 * q + m]];
+    T s = x[gi];
+    for (int m = 0; m < 8; ++m) s -= o.wp[8 * q + m] * x[gh.sidx[8 * q + m]];
     y[gi] = sgn * s;
 }
 
@@ -184,16 +195,43 @@ __global__ void k_zero_at(int64_t m, const int64_t *__restrict__ idx, double *__
     if (q < m) x[idx[q]] = 0.0;
 }
 
+// x -= mean on FLUID cells (precision T); DEAD cells set to 0
+template <typename T>
+__global__ void k_sub_meanT(int64_t n, const uint8_t *__restrict__ type, T *__restrict__ x,
+                            const double *__restrict__ mean) {
+    const T m = (T)*mean;
+    GRID_STRIDE(c, n) {
+        const uint8_t t = type[c];
+        if (t == FLUID) x[c] -= m;
+        else if (t == DEAD) x[c] = T(0);
+    }
+}
+
+template <typename T>
+static OpT<T> op_of(Ctx *c);
+template <>
+OpT<double> op_of<double>(Ctx *c) {
+    return OpT<double>{c->g.cxm, c->g.cxp, c->g.cxs, c->g.cym, c->g.cyp, c->g.cys, c->g.czm, c->g.czp, c->g.czs,
+                       c->g.dx, c->g.dy, c->g.dz, c->wp};
+}
+template <>
+OpT<float> op_of<float>(Ctx *c) {
+    const float *const *a = (const float *const *)c->op32;
+    return OpT<float>{a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], c->wp32};
+}
+
 // y = P(sgn * A x + b)
-static ibm_status apply_PA(Ctx *c, const double *x, const double *b, double sgn, double *y) {
-    KL(K_APPLY_A, k_apply_A, RED_BLOCKS, RED_THREADS, c->g, c->type, x, b, sgn, y, c->part);
+template <typename T>
+static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
+    const OpT<T> o = op_of<T>(c);
+    KL(K_APPLY_A, k_apply_A<T>, RED_BLOCKS, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        KL(-1, k_ghost_rows, (unsigned)((c->ng + 255) / 256), 256, c->gh, x, sgn, y);
+        KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, sgn, y);
         IBM_LAUNCHED(c);
     }
     IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-    KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN, 0);
+    KL(-1, k_sub_meanT<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -206,8 +244,9 @@ struct Coef {
     double v[17];
 };
 
-// partial dots: col i < ncols: (w, V_i); col ncols: (w, w)
-__global__ void k_mdot(int64_t n, const double *__restrict__ w, const double *const *__restrict__ V, int ncols,
+// partial dots (FP64 accumulation): col i < ncols: (w, V_i); col ncols: (w, w)
+template <typename T>
+__global__ void k_mdot(int64_t n, const T *__restrict__ w, const T *const *__restrict__ V, int ncols,
                        double *__restrict__ part) {
     __shared__ double sh[32];
     double acc[17];
@@ -215,11 +254,11 @@ __global__ void k_mdot(int64_t n, const double *__restrict__ w, const double *co
     for (int q = 0; q < 17; ++q) acc[q] = 0.0;
     double ww = 0.0;
     GRID_STRIDE(c, n) {
-        const double a = w[c];
+        const double a = (double)w[c];
         ww += a * a;
 #pragma unroll
         for (int q = 0; q < 17; ++q)
-            if (q < ncols) acc[q] += a * V[q][c];
+            if (q < ncols) acc[q] += a * (double)V[q][c];
     }
     for (int q = 0; q < ncols; ++q) {
         const double t = block_sum<RED_THREADS>(acc[q], sh);
@@ -230,35 +269,58 @@ __global__ void k_mdot(int64_t n, const double *__restrict__ w, const double *co
 }
 
 // w -= sum_i h_i V_i ; partial (w, w)
-__global__ void k_orth(int64_t n, double *__restrict__ w, const double *const *__restrict__ V, int ncols, Coef h,
+template <typename T>
+__global__ void k_orth(int64_t n, T *__restrict__ w, const T *const *__restrict__ V, int ncols, Coef h,
                        double *__restrict__ part) {
     __shared__ double sh[32];
+    T hv[17];
+#pragma unroll
+    for (int q = 0; q < 17; ++q) hv[q] = (T)h.v[q];
     double ww = 0.0;
     GRID_STRIDE(c, n) {
-        double a = w[c];
+        T a = w[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
-            if (q < ncols) a -= h.v[q] * V[q][c];
+            if (q < ncols) a -= hv[q] * V[q][c];
         w[c] = a;
-        ww += a * a;
+        ww += (double)a * (double)a;
     }
     const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-__global__ void k_scale(int64_t n, double *__restrict__ dst, const double *__restrict__ src, double a) {
-    GRID_STRIDE(c, n) dst[c] = a * src[c];
+template <typename T, typename S>
+__global__ void k_scale(int64_t n, T *__restrict__ dst, const S *__restrict__ src, double a) {
+    GRID_STRIDE(c, n) dst[c] = (T)(a * (double)src[c]);
 }
 
 // x += sum_i y_i Z_i
-__global__ void k_xupd(int64_t n, double *__restrict__ x, const double *const *__restrict__ Z, int ncols, Coef y) {
+template <typename T>
+__global__ void k_xupd(int64_t n, T *__restrict__ x, const T *const *__restrict__ Z, int ncols, Coef y) {
+    T yv[17];
+#pragma unroll
+    for (int q = 0; q < 17; ++q) yv[q] = (T)y.v[q];
     GRID_STRIDE(c, n) {
-        double a = x[c];
+        T a = x[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
-            if (q < ncols) a += y.v[q] * Z[q][c];
+            if (q < ncols) a += yv[q] * Z[q][c];
         x[c] = a;
     }
+}
+
+// phi += a * (double) d   (FP64 update of the outer iterate)
+__global__ void k_add_scaled(int64_t n, double *__restrict__ phi, const float *__restrict__ d, double a) {
+    GRID_STRIDE(c, n) phi[c] += a * (double)d[c];
+}
+
+template <typename T>
+__global__ void k_dotT(int64_t n, const T *__restrict__ a, const T *__restrict__ b, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    GRID_STRIDE(c, n) acc += (double)a[c] * (double)b[c];
+    acc = block_sum<RED_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -549,28 +611,29 @@ __global__ void k_beta(double *scal) {
 
 // preconditioner input / output conversion
 template <typename T>
-__global__ void k_pre_in(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ v, T *__restrict__ f) {
+__global__ void k_pre_in(GridDev g, const uint8_t *__restrict__ type, const T *__restrict__ v, T *__restrict__ f) {
     GRID_STRIDE(c, g.n) {
         if (type[c] != FLUID) { f[c] = T(0); continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        f[c] = (T)(-(g.dx[i] * g.dy[j] * g.dz[k]) * v[c]);
+        f[c] = (T)(-(g.dx[i] * g.dy[j] * g.dz[k]) * (double)v[c]);
     }
 }
 template <typename T>
-__global__ void k_pre_out(int64_t n, const uint8_t *__restrict__ type, const T *__restrict__ x, double *__restrict__ z) {
-    GRID_STRIDE(c, n) z[c] = type[c] == FLUID ? (double)x[c] : 0.0;
+__global__ void k_pre_out(int64_t n, const uint8_t *__restrict__ type, const T *__restrict__ x, T *__restrict__ z) {
+    GRID_STRIDE(c, n) z[c] = type[c] == FLUID ? x[c] : T(0);
 }
 // ghost rows of the preconditioner: z_g = v_g + sum over FLUID corners wp z_m
-__global__ void k_pre_ghost(GhostDev gh, const uint8_t *__restrict__ type, const double *__restrict__ v,
-                            double *__restrict__ z) {
+template <typename T>
+__global__ void k_pre_ghost(GhostDev gh, const T *__restrict__ wp, const uint8_t *__restrict__ type,
+                            const T *__restrict__ v, T *__restrict__ z) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= gh.ng) return;
     const int64_t gi = gh.gidx[q];
-    double s = v[gi];
+    T s = v[gi];
     for (int m = 0; m < 8; ++m) {
         const int64_t s_m = gh.sidx[8 * q + m];
-        if (type[s_m] == FLUID) s += gh.wp[8 * q + m] * z[s_m];
+        if (type[s_m] == FLUID) s += wp[8 * q + m] * z[s_m];
     }
     z[gi] = s;
 }
@@ -592,7 +655,8 @@ __global__ void k_band_jacobi(GridDev g, GhostDev gh, int64_t nb, const int64_t 
     } else {
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        res = v[c] - A_row(g, z, c, i, j, k);
+        OpT<double> o{g.cxm, g.cxp, g.cxs, g.cym, g.cyp, g.cys, g.czm, g.czp, g.czs, g.dx, g.dy, g.dz, gh.wp};
+        res = v[c] - A_row<double>(g, o, z, c, i, j, k);
         diag = -(g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0));
     }
     tmp[q] = z[c] + omega * res / diag;
@@ -955,47 +1019,59 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
     return IBM_OK;
 }
 
-// z = M^{-1} v : FP64 in, FP64 out
+// z = M^{-1} v, vectors and multigrid in precision T
 template <typename T>
-static ibm_status precond(Ctx *c, MGHier<T> &H, const double *v, double *z) {
+static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     IBM_TRY(pcg(c, H, c->opts.inner_iters));
     KL(-1, k_pre_out<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, H.px, z);
     IBM_LAUNCHED(c);
+    const OpT<T> o = op_of<T>(c);
     if (c->ng > 0) {
-        KL(-1, k_pre_ghost, (unsigned)((c->ng + 255) / 256), 256, c->gh, c->type, v, z);
+        KL(-1, k_pre_ghost<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o.wp, c->type, v, z);
         IBM_LAUNCHED(c);
     }
-    if (c->nband > 0) {
-        const unsigned gb = (unsigned)((c->nband + 255) / 256);
-        for (int s = 0; s < c->opts.band_sweeps; ++s) {
-            KL(-1, k_band_jacobi, gb, 256, c->g, c->gh, c->nband, c->band, c->band_g, v, z, c->opts.band_omega,
-               c->btmp);
-            KL(-1, k_band_scatter, gb, 256, c->nband, c->band, c->btmp, z);
-            IBM_LAUNCHED(c);
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if (c->nband > 0) {
+            const unsigned gb = (unsigned)((c->nband + 255) / 256);
+            for (int s = 0; s < c->opts.band_sweeps; ++s) {
+                KL(-1, k_band_jacobi, gb, 256, c->g, c->gh, c->nband, c->band, c->band_g, (const double *)v,
+                   (const double *)z, c->opts.band_omega, c->btmp);
+                KL(-1, k_band_scatter, gb, 256, c->nband, c->band, c->btmp, (double *)z);
+                IBM_LAUNCHED(c);
+            }
         }
     }
     return IBM_OK;
 }
 
-static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
-    if (c->opts.precision == IBM_MIXED) return precond<float>(c, c->mg32, v, z);
-    return precond<double>(c, c->mg64, v, z);
-}
-
-// ||x||^2 over all cells
-static ibm_status norm2(Ctx *c, const double *x, double *out) {
-    KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, c->N, x, x, c->part);
+// ||x||^2 over all cells (FP64 accumulation)
+template <typename T>
+static ibm_status norm2(Ctx *c, const T *x, double *out) {
+    KL(-1, k_dotT<T>, RED_BLOCKS, RED_THREADS, c->N, x, x, c->part);
     IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
     IBM_TRY(sync_scalars(c, S_TMP + 1));
     *out = c->hscal[S_TMP];
     return IBM_OK;
 }
 
-// restarted FGMRES; returns outer iterations, relative residual, status
-static ibm_status fgmres(Ctx *c, double *phi, double bnorm, double rtol, int maxit, int *outer_out, int *inner_out,
-                         double *rel_out) {
+template <typename T>
+struct Krylov {
+    std::vector<T *> V, Z;
+    T **Vdev, **Zdev;
+    T *w, *r;
+    MGHier<T> *H;
+};
+static Krylov<double> kry64(Ctx *c) { return Krylov<double>{c->V, c->Z, c->Vdev, c->Zdev, c->w, c->rr, &c->mg64}; }
+static Krylov<float> kry32(Ctx *c) { return Krylov<float>{c->V32, c->Z32, c->Vdev32, c->Zdev32, c->w32, c->r32, &c->mg32}; }
+
+// Restarted FGMRES in precision T on P A x = b, x in/out. Stops at
+// ||P(b - A x)|| <= rtol * bnorm, after maxit steps, or (single_cycle)
+// after one restart cycle. Dot products accumulate in FP64.
+template <typename T>
+static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, double rtol, int maxit,
+                         bool single_cycle, int *outer_out, int *inner_out, double *rel_out) {
     const int64_t n = c->N;
     const int m = c->opts.restart;
     int outer = 0, inner = 0;
@@ -1003,36 +1079,38 @@ static ibm_status fgmres(Ctx *c, double *phi, double bnorm, double rtol, int max
     ibm_status status = IBM_OK;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
     bool done = false;
+    int cycles = 0;
     while (!done) {
-        IBM_TRY(apply_PA(c, phi, c->b, -1.0, c->rr));
+        IBM_TRY(apply_PA<T>(c, x, b, T(-1), K.r));
         double rn2;
-        IBM_TRY(norm2(c, c->rr, &rn2));
+        IBM_TRY(norm2<T>(c, K.r, &rn2));
         const double beta = sqrt(rn2);
         rel = beta / bnorm;
         if (!isfinite(rel)) { status = c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite"); break; }
-        if (rel <= rtol) break;
+        if (rel <= rtol || (single_cycle && cycles > 0)) break;
         if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
-        KL(-1, k_scale, RED_BLOCKS, RED_THREADS, n, c->V[0], c->rr, 1.0 / beta);
+        ++cycles;
+        KL(-1, (k_scale<T, T>), RED_BLOCKS, RED_THREADS, n, K.V[0], K.r, 1.0 / beta);
         IBM_LAUNCHED(c);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
         int jlast = -1;
         for (int j = 0; j < m && outer < maxit; ++j) {
-            IBM_TRY(apply_prec(c, c->V[j], c->Z[j]));
+            IBM_TRY(precond<T>(c, *K.H, K.V[j], K.Z[j]));
             inner += c->opts.inner_iters;
-            IBM_TRY(apply_PA(c, c->Z[j], nullptr, 1.0, c->w));
+            IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
             // classical Gram-Schmidt, with a second pass when the norm drops
             // by more than a factor 0.7 (Daniel, Gragg, Kaufman, Stewart 1976)
             double hcol[17] = {0};
             double wbefore2 = 0.0, wafter2 = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                KL(K_MDOT, k_mdot, RED_BLOCKS, RED_THREADS, n, c->w, (const double *const *)c->Vdev, j + 1, c->part);
+                KL(K_MDOT, k_mdot<T>, RED_BLOCKS, RED_THREADS, n, K.w, (const T *const *)K.Vdev, j + 1, c->part);
                 IBM_TRY(finalize(c, c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD));
                 IBM_TRY(sync_scalars(c, S_MD + j + 2));
                 Coef h{};
                 for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
                 wbefore2 = c->hscal[S_MD + j + 1];
-                KL(K_ORTH, k_orth, RED_BLOCKS, RED_THREADS, n, c->w, (const double *const *)c->Vdev, j + 1, h, c->part);
+                KL(K_ORTH, k_orth<T>, RED_BLOCKS, RED_THREADS, n, K.w, (const T *const *)K.Vdev, j + 1, h, c->part);
                 IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
                 IBM_TRY(sync_scalars(c, S_TMP + 1));
                 wafter2 = c->hscal[S_TMP];
@@ -1060,7 +1138,7 @@ static ibm_status fgmres(Ctx *c, double *phi, double bnorm, double rtol, int max
             jlast = j;
             const double est = fabs(gv[j + 1]) / bnorm;
             if (hn > 0.0 && j + 1 < m) {
-                KL(-1, k_scale, RED_BLOCKS, RED_THREADS, n, c->V[j + 1], c->w, 1.0 / hn);
+                KL(-1, (k_scale<T, T>), RED_BLOCKS, RED_THREADS, n, K.V[j + 1], K.w, 1.0 / hn);
                 IBM_LAUNCHED(c);
             }
             if (est <= rtol || hn == 0.0) break;
@@ -1068,19 +1146,127 @@ static ibm_status fgmres(Ctx *c, double *phi, double bnorm, double rtol, int max
         if (done) break;
         if (jlast < 0) { status = IBM_ERR_NOT_CONVERGED; break; }
         for (int i = jlast; i >= 0; --i) {
-            double s = gv[i];
-            for (int k = i + 1; k <= jlast; ++k) s -= H[(size_t)i * m + k] * y[k];
-            y[i] = s / H[(size_t)i * m + i];
+            double sacc = gv[i];
+            for (int k = i + 1; k <= jlast; ++k) sacc -= H[(size_t)i * m + k] * y[k];
+            y[i] = sacc / H[(size_t)i * m + i];
         }
         Coef yc{};
         for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
-        KL(-1, k_xupd, RED_BLOCKS, RED_THREADS, n, phi, (const double *const *)c->Zdev, jlast + 1, yc);
+        KL(-1, k_xupd<T>, RED_BLOCKS, RED_THREADS, n, x, (const T *const *)K.Zdev, jlast + 1, yc);
         IBM_LAUNCHED(c);
     }
     *outer_out = outer;
     *inner_out = inner;
     *rel_out = rel;
     return status;
+}
+
+static ibm_status apply_prec(Ctx *c, const double *v, double *z);
+
+// FP32 storage of mixed mode: operator coefficients, ghost weights, Krylov
+// vectors (allocated on first use)
+__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    GRID_STRIDE(q, n) b[q] = (float)a[q];
+}
+static ibm_status ensure_mixed(Ctx *c) {
+    if (!c->op32[0]) {
+        const double *src[12] = {c->g.cxm, c->g.cxp, c->g.cxs, c->g.cym, c->g.cyp, c->g.cys,
+                                 c->g.czm, c->g.czp, c->g.czs, c->g.dx, c->g.dy, c->g.dz};
+        const int64_t len[12] = {c->nx, c->nx, c->nx, c->ny, c->ny, c->ny, c->nz, c->nz, c->nz, c->nx, c->ny, c->nz};
+        for (int q = 0; q < 12; ++q) {
+            c->op32[q] = (float *)dev_alloc(c, sizeof(float) * len[q]);
+            if (!c->op32[q]) return c->fail(IBM_ERR_OOM, "FP32 coefficient allocation failed");
+            KL(-1, k_to_float, 1, 256, len[q], src[q], c->op32[q]);
+        }
+        IBM_LAUNCHED(c);
+    }
+    if (c->wp32_n != c->ng) {
+        dev_free(c, c->wp32);
+        c->wp32 = (float *)dev_alloc(c, sizeof(float) * 8 * (c->ng > 0 ? c->ng : 1));
+        if (!c->wp32) return c->fail(IBM_ERR_OOM, "FP32 weight allocation failed");
+        if (c->ng > 0) KL(-1, k_to_float, nblk(8 * c->ng), 256, 8 * c->ng, c->wp, c->wp32);
+        IBM_LAUNCHED(c);
+        c->wp32_n = c->ng;
+    }
+    const int m = c->opts.restart;
+    if (m > c->m32_cap) {
+        for (float *p : c->V32) dev_free(c, p);
+        for (float *p : c->Z32) dev_free(c, p);
+        c->V32.assign(m + 1, nullptr);
+        c->Z32.assign(m, nullptr);
+        for (int i = 0; i <= m; ++i)
+            if (!(c->V32[i] = (float *)dev_alloc(c, sizeof(float) * c->N))) return c->fail(IBM_ERR_OOM, "FP32 Krylov allocation failed");
+        for (int i = 0; i < m; ++i)
+            if (!(c->Z32[i] = (float *)dev_alloc(c, sizeof(float) * c->N))) return c->fail(IBM_ERR_OOM, "FP32 Krylov allocation failed");
+        if (!c->Vdev32) c->Vdev32 = (float **)dev_alloc(c, sizeof(float *) * 17);
+        if (!c->Zdev32) c->Zdev32 = (float **)dev_alloc(c, sizeof(float *) * 17);
+        if (!c->w32) c->w32 = (float *)dev_alloc(c, sizeof(float) * c->N);
+        if (!c->r32) c->r32 = (float *)dev_alloc(c, sizeof(float) * c->N);
+        if (!c->d32) c->d32 = (float *)dev_alloc(c, sizeof(float) * c->N);
+        if (!c->b32) c->b32 = (float *)dev_alloc(c, sizeof(float) * c->N);
+        if (!c->Vdev32 || !c->Zdev32 || !c->w32 || !c->r32 || !c->d32 || !c->b32)
+            return c->fail(IBM_ERR_OOM, "FP32 Krylov allocation failed");
+        IBM_CUDA(c, cudaMemcpyAsync(c->Vdev32, c->V32.data(), sizeof(float *) * (m + 1), cudaMemcpyHostToDevice, c->s));
+        IBM_CUDA(c, cudaMemcpyAsync(c->Zdev32, c->Z32.data(), sizeof(float *) * m, cudaMemcpyHostToDevice, c->s));
+        IBM_CUDA(c, cudaStreamSynchronize(c->s));
+        c->m32_cap = m;
+    }
+    return IBM_OK;
+}
+
+// Mixed mode: FP64 defect correction around FP32 FGMRES cycles.
+//   r = P(b - A phi) in FP64; stop at ||r|| <= rtol ||b||;
+//   solve P A d = r / ||r|| approximately in FP32 (one FGMRES cycle, or
+//   until a reduction of mixed_inner_rtol); phi += ||r|| d in FP64.
+static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rtol, int maxit, int *outer_out,
+                                   int *inner_out, double *rel_out) {
+    IBM_TRY(ensure_mixed(c));
+    const int64_t n = c->N;
+    int steps = 0, inner = 0, refinements = 0;
+    double rel = 0.0;
+    ibm_status status = IBM_OK;
+    while (true) {
+        IBM_TRY(apply_PA<double>(c, phi, c->b, -1.0, c->rr));
+        double rn2;
+        IBM_TRY(norm2<double>(c, c->rr, &rn2));
+        const double rn = sqrt(rn2);
+        rel = rn / bnorm;
+        if (!isfinite(rel)) return c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite");
+        if (rel <= rtol) break;
+        if (steps >= maxit || refinements >= 64) { status = IBM_ERR_NOT_CONVERGED; break; }
+        ++refinements;
+        KL(-1, (k_scale<float, double>), RED_BLOCKS, RED_THREADS, n, c->b32, c->rr, 1.0 / rn);
+        IBM_CUDA(c, cudaMemsetAsync(c->d32, 0, sizeof(float) * n, c->s));
+        IBM_LAUNCHED(c);
+        // inner target: the FP64 goal, but no tighter than FP32 can reach
+        const double target = fmax(c->opts.mixed_inner_rtol, 0.5 * rtol / rel);
+        int o = 0, in = 0;
+        double irel = 0.0;
+        ibm_status s = fgmres<float>(c, kry32(c), c->d32, c->b32, 1.0, target, maxit - steps, false, &o, &in, &irel);
+        if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
+        steps += o;
+        inner += in;
+        KL(-1, k_add_scaled, RED_BLOCKS, RED_THREADS, n, phi, c->d32, rn);
+        IBM_LAUNCHED(c);
+        if (o == 0) { status = IBM_ERR_NOT_CONVERGED; break; }
+    }
+    *outer_out = steps;
+    *inner_out = inner;
+    *rel_out = rel;
+    return status;
+}
+
+static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
+    if (c->opts.precision == IBM_MIXED) {
+        // FP64 vectors through the FP32 multigrid: convert in and out
+        IBM_TRY(ensure_mixed(c));
+        KL(-1, (k_scale<float, double>), RED_BLOCKS, RED_THREADS, c->N, c->b32, v, 1.0);
+        IBM_TRY(precond<float>(c, c->mg32, c->b32, c->d32));
+        KL(-1, (k_scale<double, float>), RED_BLOCKS, RED_THREADS, c->N, z, c->d32, 1.0);
+        IBM_LAUNCHED(c);
+        return IBM_OK;
+    }
+    return precond<double>(c, c->mg64, v, z);
 }
 
 // BiCGStab (van der Vorst 1992) with right preconditioning; scalars stay on
@@ -1098,9 +1284,9 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
     while (true) {
         if (fresh) {
             // true residual
-            IBM_TRY(apply_PA(c, phi, c->b, -1.0, r));
+            IBM_TRY(apply_PA<double>(c, phi, c->b, -1.0, r));
             double rn2;
-            IBM_TRY(norm2(c, r, &rn2));
+            IBM_TRY(norm2<double>(c, r, &rn2));
             rel = sqrt(rn2) / bnorm;
             if (!isfinite(rel)) return c->fail(IBM_ERR_DIVERGED, "Poisson residual is not finite");
             if (rel <= rtol) break;
@@ -1119,14 +1305,14 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
         KL(-1, k_bicg_p, RED_BLOCKS, RED_THREADS, n, r, p, v, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, p, ph));
-        IBM_TRY(apply_PA(c, ph, nullptr, 1.0, v));
+        IBM_TRY(apply_PA<double>(c, ph, nullptr, 1.0, v));
         KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, n, rh, v, c->part);
         IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + B_DEN));
         KL(-1, k_bicg_alpha, 1, 1, c->scal);
         KL(-1, k_bicg_s, RED_BLOCKS, RED_THREADS, n, r, v, sv, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, sv, shv));
-        IBM_TRY(apply_PA(c, shv, nullptr, 1.0, t));
+        IBM_TRY(apply_PA<double>(c, shv, nullptr, 1.0, t));
         KL(-1, k_bicg_tdots, RED_BLOCKS, RED_THREADS, n, t, sv, c->part);
         IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + B_TS));
         KL(-1, k_bicg_omega, 1, 1, c->scal);
@@ -1164,7 +1350,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
         IBM_LAUNCHED(c);
     }
     double bn2;
-    IBM_TRY(norm2(c, c->b, &bn2));
+    IBM_TRY(norm2<double>(c, c->b, &bn2));
     const double bnorm = sqrt(bn2);
     int outer = 0, inner = 0;
     double rel = 0.0;
@@ -1172,8 +1358,9 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     if (!(bnorm > 1e-300)) {
         IBM_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * n, c->s));
     } else {
-        if (c->opts.outer == IBM_OUTER_FGMRES) status = fgmres(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
-        else status = bicgstab(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
+        if (c->opts.outer == IBM_OUTER_BICGSTAB) status = bicgstab(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
+        else if (c->opts.precision == IBM_MIXED) status = mixed_refinement(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
+        else status = fgmres<double>(c, kry64(c), phi, c->b, bnorm, rtol, maxit, false, &outer, &inner, &rel);
         if (status != IBM_OK && status != IBM_ERR_NOT_CONVERGED) return status;
         // normalise: zero volume-weighted FLUID mean, shift ghosts too
         KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, phi, c->part);

@@ -45,7 +45,8 @@ class ibm_solver_opts(Structure):
     _fields_ = [("rtol", c_double), ("max_outer", c_int), ("restart", c_int), ("inner_iters", c_int),
                 ("nu1", c_int), ("nu2", c_int), ("coarse_sweeps", c_int), ("helm_rtol", c_double),
                 ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
-                ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double)]
+                ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
+                ("mixed_inner_rtol", c_double)]
 
 
 class ibm_table_info(Structure):

@@ -74,4 +74,4 @@ def test_create_rejects_bad_descriptor_without_gpu(lib):
     assert lib.ibm_destroy(None) == ibm.IBM_OK
     o = ibm.ibm_solver_opts()
     assert lib.ibm_default_opts(ctypes.byref(o)) == ibm.IBM_OK
-    assert o.rtol == 1e-10 and o.restart == 8
+    assert o.rtol == 1e-10 and o.restart == 16 and o.outer == ibm.IBM_OUTER_FGMRES

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 def _solver(case):
     s = ibm.Solver(case)
-    s.set_opts(rtol=1e-11, max_outer=400)
+    s.set_opts(rtol=1e-9, max_outer=400)
     s.set_body(case.verts, case.elems)
     s.classify()
     return s
@@ -37,12 +37,14 @@ def test_noalloc_residual_matches_poisson_solve(which):
     for call in range(2):  # two calls in a row share the scratch array
         rhs = torch.from_numpy(rng.uniform(-1, 1, s.N)).cuda()
         phi = torch.zeros(s.N, dtype=torch.float64, device="cuda")
-        st = s.poisson_solve(rhs, phi, rtol=1e-11, maxit=400)
+        st = s.poisson_solve(rhs, phi, rtol=1e-9, maxit=400)
         assert st["status"] == ibm.IBM_OK
         want = st["rel_residual"]
         got = ibm.ibm_poisson_residual_noalloc(s.ctx, rhs.data_ptr(), phi.data_ptr())
-        assert 0.0 < want <= 1e-11
-        assert abs(got - want) <= 1e-3 * want, (call, got, want)
+        assert 0.0 < want <= 1e-9
+        # both evaluate b - A phi in FP64 in different orders: a small
+        # residual carries rounding noise of order 1e-16 * |A phi| / |b|
+        assert abs(got - want) <= 1e-3 * want + 1e-14, (call, got, want)
         # a poor guess: the residual of phi = 0 is exactly 1 on both paths
         zero = torch.zeros_like(phi)
         got0 = ibm.ibm_poisson_residual_noalloc(s.ctx, rhs.data_ptr(), zero.data_ptr())
