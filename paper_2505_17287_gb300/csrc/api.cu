@@ -255,9 +255,16 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     coef(c->hhz, c->hdz, &czm, &czp, &czs);
     if (!cxm || !cxp || !cxs || !cym || !cyp || !cys || !czm || !czp || !czs)
         return c->fail(IBM_ERR_OOM, "grid allocation failed");
+    auto recip = [](const std::vector<double> &w) {
+        std::vector<double> r(w.size());
+        for (size_t i = 0; i < w.size(); ++i) r[i] = 1.0 / w[i];
+        return r;
+    };
+    double *rdx = upload(c, recip(c->hdx)), *rdy = upload(c, recip(c->hdy)), *rdz = upload(c, recip(c->hdz));
+    if (!rdx || !rdy || !rdz) return c->fail(IBM_ERR_OOM, "grid allocation failed");
     c->g = GridDev{c->nx, c->ny, c->nz, c->ndim, c->N, c->xf, c->yf, c->zf, c->xc, c->yc, c->zc,
                    c->dx, c->dy, c->dz, c->hx, c->hy, c->hz, cxm, cxp, cxs, cym, cyp, cys, czm, czp, czs,
-                   FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny)};
+                   FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny), rdx, rdy, rdz};
     const size_t nb = sizeof(double) * c->N;
     c->type = (uint8_t *)dev_alloc(c, c->N);
     c->inside = (uint8_t *)dev_alloc(c, c->N);
@@ -408,6 +415,7 @@ extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
     if (c->ne == 0) return c->fail(IBM_ERR_STATE, "ibm_set_body must be called before ibm_classify_cells");
     IBM_TRY(geom_classify(c));
     c->wp32_n = -1;  // FP32 copies of the ghost weights are stale
+    c->hinv_ok = false;
     if (c->n_fluid == 0) return c->fail(IBM_ERR_ARG, "no fluid cells");
     // FLUID volume
     double vol = 0.0;

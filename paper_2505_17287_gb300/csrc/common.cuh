@@ -75,6 +75,7 @@ struct GridDev {
     // the high wall), cXs = cXm + cXp
     const double *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
     FastDiv fnx, fny;     // division by nx and ny (cell index < 2^32)
+    const double *rdx, *rdy, *rdz;  // 1 / cell widths
 };
 
 // cell (i, j, k) of a linear index below 2^32

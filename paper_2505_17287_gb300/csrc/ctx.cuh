@@ -90,6 +90,8 @@ struct Ctx {
     double *p = nullptr, *Nold[3] = {nullptr, nullptr, nullptr}, *Nnew[3] = {nullptr, nullptr, nullptr};
     double *ustar[3] = {nullptr, nullptr, nullptr}, *rhs[3] = {nullptr, nullptr, nullptr};
     double *b = nullptr, *gtmp = nullptr;
+    double *hinv[3] = {nullptr, nullptr, nullptr};   // Helmholtz inverse diagonals per component
+    bool hinv_ok = false;
     int64_t nstep = 0;
     bool have_nold = false;
 

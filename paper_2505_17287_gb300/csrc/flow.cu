@@ -59,7 +59,10 @@ struct CFields3 {
 };
 
 // Convective term N^n, explicit viscous term and the AB2 + CN right-hand side
-// on FLUID cells; other cells get rhs = 0 and N = 0.
+// on FLUID cells; other cells get rhs = 0 and N = 0. Per axis the face area
+// over the volume is 1/width, and the viscous face coefficients are the
+// pressure operator's per-axis coefficients; a Dirichlet wall contributes
+// 2 (value - u_c) / width^2.
 __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3 u, CFields3 F, CFields3 Nold,
                            int first, Fields3 Nnew, Fields3 rhs, BCInfo bc, double dt, double alpha, int ncomp) {
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
@@ -70,13 +73,11 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3
         }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
-        const double A[3] = {g.dy[j] * g.dz[k], g.dx[i] * g.dz[k], g.dx[i] * g.dy[j]};
         const int idx[3] = {i, j, k};
         const int nn[3] = {g.nx, g.ny, g.nz};
         const int64_t st[3] = {1, sy, sz};
-        const double *hh[3] = {g.hx, g.hy, g.hz};
-        const double *hw[3] = {g.dx, g.dy, g.dz};
+        const double rw[3] = {g.rdx[i], g.rdy[j], g.rdz[k]};
+        const double cm[3] = {g.cxm[i], g.cym[j], g.czm[k]}, cp[3] = {g.cxp[i], g.cyp[j], g.czp[k]};
         double Flo[3], Fhi[3];
         Flo[0] = F.p[0][fx_lo(g, i, j, k)];
         Fhi[0] = F.p[0][fx_lo(g, i, j, k) + 1];
@@ -91,100 +92,101 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3
         for (int q = 0; q < ncomp; ++q) {
             const double *uq = u.p[q];
             const double uc = uq[c];
-            double flux = 0.0, lap = 0.0, src = 0.0;
+            double N = 0.0, lap = 0.0, src = 0.0;
             for (int a = 0; a < g.ndim; ++a) {
                 double ulo, uhi;
-                // low face
+                const double w2 = 2.0 * rw[a] * rw[a];
                 if (idx[a] > 0) {
                     const double un = uq[c - st[a]];
                     ulo = 0.5 * (uc + un);
-                    lap += A[a] * (un - uc) / hh[a][idx[a]];
+                    lap += cm[a] * (un - uc);
+                } else if (bc.dir[q][2 * a]) {
+                    ulo = bc.val[q][2 * a];
+                    lap += w2 * (ulo - uc);
+                    src += w2 * ulo;
                 } else {
-                    const int f = 2 * a;
-                    if (bc.dir[q][f]) {
-                        ulo = bc.val[q][f];
-                        const double hb = 0.5 * hw[a][0];
-                        lap += A[a] * (bc.val[q][f] - uc) / hb;
-                        src += A[a] * bc.val[q][f] / hb;
-                    } else {
-                        ulo = uc;
-                    }
+                    ulo = uc;
                 }
-                // high face
                 if (idx[a] < nn[a] - 1) {
                     const double un = uq[c + st[a]];
                     uhi = 0.5 * (uc + un);
-                    lap += A[a] * (un - uc) / hh[a][idx[a] + 1];
+                    lap += cp[a] * (un - uc);
+                } else if (bc.dir[q][2 * a + 1]) {
+                    uhi = bc.val[q][2 * a + 1];
+                    lap += w2 * (uhi - uc);
+                    src += w2 * uhi;
                 } else {
-                    const int f = 2 * a + 1;
-                    if (bc.dir[q][f]) {
-                        uhi = bc.val[q][f];
-                        const double hb = 0.5 * hw[a][nn[a] - 1];
-                        lap += A[a] * (bc.val[q][f] - uc) / hb;
-                        src += A[a] * bc.val[q][f] / hb;
-                    } else {
-                        uhi = uc;
-                    }
+                    uhi = uc;
                 }
-                flux += A[a] * Fhi[a] * uhi - A[a] * Flo[a] * ulo;
+                N += rw[a] * (Fhi[a] * uhi - Flo[a] * ulo);
             }
-            const double N = flux / vol;
             const double No = first ? N : Nold.p[q][c];
             Nnew.p[q][c] = N;
-            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * (lap / vol) + alpha * (src / vol);
+            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * lap + alpha * src;
         }
     }
 }
 
+// inverse diagonal of (I - alpha L0) for component q on FLUID cells
+__global__ void k_helm_diag(GridDev g, const uint8_t *__restrict__ type, BCInfo bc, int q, double alpha,
+                            double *__restrict__ hinv) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (type[c] != FLUID) { hinv[c] = 0.0; continue; }
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        double d = g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0);
+        const double rx2 = 2.0 * g.rdx[i] * g.rdx[i], ry2 = 2.0 * g.rdy[j] * g.rdy[j], rz2 = 2.0 * g.rdz[k] * g.rdz[k];
+        if (i == 0 && bc.dir[q][0]) d += rx2;
+        if (i == g.nx - 1 && bc.dir[q][1]) d += rx2;
+        if (j == 0 && bc.dir[q][2]) d += ry2;
+        if (j == g.ny - 1 && bc.dir[q][3]) d += ry2;
+        if (g.ndim == 3) {
+            if (k == 0 && bc.dir[q][4]) d += rz2;
+            if (k == g.nz - 1 && bc.dir[q][5]) d += rz2;
+        }
+        hinv[c] = 1.0 / (1.0 + alpha * d);
+    }
+}
+
+// off-diagonal sum sum_f c_f u_nb of the viscous operator (interior faces)
+__device__ __forceinline__ double visc_off(const GridDev &g, const double *__restrict__ u, int64_t c, int i, int j,
+                                           int k) {
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    double s = 0.0;
+    if (i > 0) s += g.cxm[i] * u[c - 1];
+    if (i < g.nx - 1) s += g.cxp[i] * u[c + 1];
+    if (j > 0) s += g.cym[j] * u[c - sy];
+    if (j < g.ny - 1) s += g.cyp[j] * u[c + sy];
+    if (g.ndim == 3) {
+        if (k > 0) s += g.czm[k] * u[c - sz];
+        if (k < g.nz - 1) s += g.czp[k] * u[c + sz];
+    }
+    return s;
+}
+
 // Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
 __global__ void k_helm_rb(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                          double *__restrict__ u, BCInfo bc, int q, double alpha, int col) {
+                          const double *__restrict__ hinv, double *__restrict__ u, double alpha, int col) {
     const int64_t row = blockIdx.x;
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
     const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
     if (i >= g.nx) return;
     const int64_t c = row * g.nx + i;
     if (type[c] != FLUID) return;
-    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    const double vol = g.dx[i] * g.dy[j] * g.dz[k];
-    const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
-    double d = 0.0, s = 0.0, t;
-    if (i > 0) { t = ax / g.hx[i]; d += t; s += t * u[c - 1]; } else if (bc.dir[q][0]) d += ax / (0.5 * g.dx[0]);
-    if (i < g.nx - 1) { t = ax / g.hx[i + 1]; d += t; s += t * u[c + 1]; } else if (bc.dir[q][1]) d += ax / (0.5 * g.dx[g.nx - 1]);
-    if (j > 0) { t = ay / g.hy[j]; d += t; s += t * u[c - sy]; } else if (bc.dir[q][2]) d += ay / (0.5 * g.dy[0]);
-    if (j < g.ny - 1) { t = ay / g.hy[j + 1]; d += t; s += t * u[c + sy]; } else if (bc.dir[q][3]) d += ay / (0.5 * g.dy[g.ny - 1]);
-    if (g.ndim == 3) {
-        if (k > 0) { t = az / g.hz[k]; d += t; s += t * u[c - sz]; } else if (bc.dir[q][4]) d += az / (0.5 * g.dz[0]);
-        if (k < g.nz - 1) { t = az / g.hz[k + 1]; d += t; s += t * u[c + sz]; } else if (bc.dir[q][5]) d += az / (0.5 * g.dz[g.nz - 1]);
-    }
-    const double a = alpha / vol;
-    u[c] = (rhs[c] + a * s) / (1.0 + a * d);
+    u[c] = (rhs[c] + alpha * visc_off(g, u, c, i, j, k)) * hinv[c];
 }
 
-// residual of the Helmholtz system: FLUID rows rhs - H u; GHOST rows
-// -(u_G + sum wv u_m) (rhs 0). partial columns: |r|^2, |rhs|^2
+// residual of the Helmholtz system on FLUID rows; partial columns |r|^2, |rhs|^2
 __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                             const double *__restrict__ u, BCInfo bc, int q, double alpha, double *__restrict__ part) {
+                             const double *__restrict__ hinv, const double *__restrict__ u, double alpha,
+                             double *__restrict__ part) {
     __shared__ double sh[32];
     double rr = 0.0, bb = 0.0;
-    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) continue;
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
-        const double ax = g.dy[j] * g.dz[k], ay = g.dx[i] * g.dz[k], az = g.dx[i] * g.dy[j];
-        const double uc = u[c];
-        double s = 0.0;
-        if (i > 0) s += ax / g.hx[i] * (u[c - 1] - uc); else if (bc.dir[q][0]) s -= ax / (0.5 * g.dx[0]) * uc;
-        if (i < g.nx - 1) s += ax / g.hx[i + 1] * (u[c + 1] - uc); else if (bc.dir[q][1]) s -= ax / (0.5 * g.dx[g.nx - 1]) * uc;
-        if (j > 0) s += ay / g.hy[j] * (u[c - sy] - uc); else if (bc.dir[q][2]) s -= ay / (0.5 * g.dy[0]) * uc;
-        if (j < g.ny - 1) s += ay / g.hy[j + 1] * (u[c + sy] - uc); else if (bc.dir[q][3]) s -= ay / (0.5 * g.dy[g.ny - 1]) * uc;
-        if (g.ndim == 3) {
-            if (k > 0) s += az / g.hz[k] * (u[c - sz] - uc); else if (bc.dir[q][4]) s -= az / (0.5 * g.dz[0]) * uc;
-            if (k < g.nz - 1) s += az / g.hz[k + 1] * (u[c + sz] - uc); else if (bc.dir[q][5]) s -= az / (0.5 * g.dz[g.nz - 1]) * uc;
-        }
-        const double r = rhs[c] - (uc - (alpha / vol) * s);
+        const double r = rhs[c] - (u[c] / hinv[c] - alpha * visc_off(g, u, c, i, j, k));
         rr += r * r;
         bb += rhs[c] * rhs[c];
     }
@@ -526,6 +528,16 @@ ibm_status flow_init(Ctx *c) {
 static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     const BCInfo bc = make_bc(c);
     const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    if (!c->hinv_ok) {
+        for (int cq = 0; cq < c->ndim; ++cq) {
+            if (!c->hinv[cq]) c->hinv[cq] = (double *)dev_alloc(c, sizeof(double) * c->N);
+            if (!c->hinv[cq]) return c->fail(IBM_ERR_OOM, "Helmholtz diagonal allocation failed");
+            ++c->nlaunch, k_helm_diag<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, bc, cq, alpha, c->hinv[cq]);
+        }
+        IBM_LAUNCHED(c);
+        c->hinv_ok = true;
+    }
+    const double *hinv = c->hinv[q];
     double *u = c->ustar[q];
     const double *rhs = c->rhs[q];
     const int check_every = 4;
@@ -535,10 +547,10 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     Fields3 U{{u, u, u}};
     for (int it = 0; it < c->opts.helm_maxit; ++it) {
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 0);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 0);
         kt_end(c, K_HELM);
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, 1);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 1);
         kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
@@ -548,7 +560,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
         }
         ++*sweeps;
         if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
-            ++c->nlaunch, k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, u, bc, q, alpha, c->part);
+            ++c->nlaunch, k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
             IBM_LAUNCHED(c);
             IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 48));
             double gmax = 0.0;

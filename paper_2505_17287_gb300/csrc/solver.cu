@@ -148,6 +148,16 @@ __device__ __forceinline__ T A_row(const GridDev &g, const OpT<T> &o, const T *_
     const T xc = x[c];
     const T xm = i > 0 ? x[c - 1] : xc, xp = i < g.nx - 1 ? x[c + 1] : xc;
     const T ym = j > 0 ? x[c - sy] : xc, yp = j < g.ny - 1 ? x[c + sy] : xc;
+    if (sizeof(T) == 4) {
+        // FP32: difference form, so constants are annihilated exactly
+        T s = o.cxm[i] * (xm - xc) + o.cxp[i] * (xp - xc) + o.cym[j] * (ym - xc) + o.cyp[j] * (yp - xc);
+        if (g.ndim == 3) {
+            const T zm = k > 0 ? x[c - sz] : xc, zp = k < g.nz - 1 ? x[c + sz] : xc;
+            s += o.czm[k] * (zm - xc) + o.czp[k] * (zp - xc);
+        }
+        return s;
+    }
+    // FP64: fewest FP64 instructions (one FMA per neighbour)
     T s = o.cxm[i] * xm + o.cxp[i] * xp + o.cym[j] * ym + o.cyp[j] * yp;
     T dsum = o.cxs[i] + o.cys[j];
     if (g.ndim == 3) {
@@ -309,9 +319,27 @@ __global__ void k_xupd(int64_t n, T *__restrict__ x, const T *const *__restrict_
     }
 }
 
-// phi += a * (double) d   (FP64 update of the outer iterate)
-__global__ void k_add_scaled(int64_t n, double *__restrict__ phi, const float *__restrict__ d, double a) {
-    GRID_STRIDE(c, n) phi[c] += a * (double)d[c];
+// phi += a * ((double) d - mean) on FLUID and GHOST cells (FP64 update of the
+// outer iterate; the constant part of the correction is discarded)
+__global__ void k_add_scaled(int64_t n, const uint8_t *__restrict__ type, double *__restrict__ phi,
+                             const float *__restrict__ d, double a, const double *__restrict__ mean) {
+    const double m = *mean;
+    GRID_STRIDE(c, n) if (type[c] != DEAD) phi[c] += a * ((double)d[c] - m);
+}
+
+// FLUID volume-weighted sum of an FP32 vector
+__global__ void k_fluid_volsum32(GridDev g, const uint8_t *__restrict__ type, const float *__restrict__ x,
+                                 double *__restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    GRID_STRIDE(c, g.n) {
+        if (type[c] != FLUID) continue;
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        acc += (g.dx[i] * g.dy[j] * g.dz[k]) * (double)x[c];
+    }
+    acc = block_sum<RED_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 template <typename T>
@@ -1246,7 +1274,9 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
         if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
         steps += o;
         inner += in;
-        KL(-1, k_add_scaled, RED_BLOCKS, RED_THREADS, n, phi, c->d32, rn);
+        KL(-1, k_fluid_volsum32, RED_BLOCKS, RED_THREADS, c->g, c->type, c->d32, c->part);
+        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+        KL(-1, k_add_scaled, RED_BLOCKS, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
         IBM_LAUNCHED(c);
         if (o == 0) { status = IBM_ERR_NOT_CONVERGED; break; }
     }
