@@ -24,6 +24,8 @@
 #include "ctx.cuh"
 
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 namespace ibm {
 
@@ -189,15 +191,17 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m)   (b_g = 0)
+// GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m) + b_g (b may be null = 0;
+// the pressure equation has b_g = 0, a defect-correction right-hand side not)
 template <typename T>
-__global__ void k_ghost_rows(GhostDev gh, OpT<T> o, const T *__restrict__ x, T sgn, T *__restrict__ y) {
+__global__ void k_ghost_rows(GhostDev gh, OpT<T> o, const T *__restrict__ x, const T *__restrict__ b, T sgn,
+                             T *__restrict__ y) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= gh.ng) return;
     const int64_t gi = gh.gidx[q];
     T s = x[gi];
     for (int m = 0; m < 8; ++m) s -= o.wp[8 * q + m] * x[gh.sidx[8 * q + m]];
-    y[gi] = sgn * s;
+    y[gi] = sgn * s + (b ? b[gi] : T(0));
 }
 
 __global__ void k_zero_at(int64_t m, const int64_t *__restrict__ idx, double *__restrict__ x) {
@@ -237,7 +241,7 @@ static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
     KL(K_APPLY_A, k_apply_A<T>, RED_BLOCKS, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
-        KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, sgn, y);
+        KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, b, sgn, y);
         IBM_LAUNCHED(c);
     }
     IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
@@ -536,16 +540,41 @@ __global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx,
     x[c] += C.x[p];
 }
 
-// coarsest level: red-black sweeps in one block, all data in shared memory
+// coarsest level: red-black sweeps in one block, all data in shared memory.
+// The level operator is singular (constants); the right-hand side is made
+// compatible by removing its mean over the active cells, and the solution is
+// returned with zero mean there, so no constant mode builds up in the
+// preconditioner (which would swamp FP32 corrections).
+template <typename T>
+__device__ __forceinline__ T block_mean_active(T v, bool act, T *red, int *cnt) {
+    // plain shared-memory tree sum over COARSE_MAX slots
+    const int c = threadIdx.x;
+    red[c] = act ? v : T(0);
+    cnt[c] = act ? 1 : 0;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (c < o) {
+            red[c] += red[c + o];
+            cnt[c] += cnt[c + o];
+        }
+        __syncthreads();
+    }
+    const T m = cnt[0] > 0 ? red[0] / T(cnt[0]) : T(0);
+    __syncthreads();
+    return m;
+}
+
 constexpr int COARSE_MAX = 512;
 template <typename T>
 __global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const T *__restrict__ f,
                                                              T *__restrict__ x, int sweeps) {
     __shared__ T sx[COARSE_MAX], sf[COARSE_MAX], stx[COARSE_MAX], sty[COARSE_MAX], stz[COARSE_MAX],
-        sdi[COARSE_MAX];
+        sdi[COARSE_MAX], red[COARSE_MAX];
+    __shared__ int cnt[COARSE_MAX];
     const int n = (int)L.n;
     const int c = threadIdx.x;
     int i = 0, j = 0, k = 0;
+    bool act = false;
     if (c < n) {
         i = c % L.nx;
         j = (c / L.nx) % L.ny;
@@ -556,14 +585,18 @@ __global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const
         sty[c] = L.ty[c];
         stz[c] = L.tz[c];
         sdi[c] = L.dinv[c];
+        act = sdi[c] > T(0);
     }
+    __syncthreads();
+    const T fm = block_mean_active<T>(c < n ? sf[c] : T(0), act, red, cnt);
+    if (act) sf[c] -= fm;
     __syncthreads();
     const int sy = L.nx, sz = L.nx * L.ny;
     const int par = (i + j + k) & 1;
     for (int pass = 0; pass < 4 * sweeps; ++pass) {
         // sweeps x (red, black) then sweeps x (black, red): a palindrome
         const int colour = pass < 2 * sweeps ? (pass & 1) : 1 - (pass & 1);
-        if (c < n && par == colour && sdi[c] > T(0)) {
+        if (c < n && par == colour && act) {
             T s = sf[c];
             if (i > 0) s += stx[c] * sx[c - 1];
             if (i < L.nx - 1) s += stx[c + 1] * sx[c + 1];
@@ -575,7 +608,8 @@ __global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const
         }
         __syncthreads();
     }
-    if (c < n) x[c] = sx[c];
+    const T xm = block_mean_active<T>(c < n ? sx[c] : T(0), act, red, cnt);
+    if (c < n) x[c] = act ? sx[c] - xm : T(0);
 }
 
 // q = K p ; partial (p, q) in FP64
@@ -1272,6 +1306,9 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
         double irel = 0.0;
         ibm_status s = fgmres<float>(c, kry32(c), c->d32, c->b32, 1.0, target, maxit - steps, false, &o, &in, &irel);
         if (s != IBM_OK && s != IBM_ERR_NOT_CONVERGED) return s;
+        if (getenv("IBM_TRACE"))
+            fprintf(stderr, "[ibm] refinement %d: rel %.3e target %.3e fgmres32 steps %d rel32 %.3e status %d\n",
+                    refinements, rel, target, o, irel, (int)s);
         steps += o;
         inner += in;
         KL(-1, k_fluid_volsum32, RED_BLOCKS, RED_THREADS, c->g, c->type, c->d32, c->part);
