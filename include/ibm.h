@@ -235,7 +235,8 @@ ibm_status ibm_launch_count(ibm_ctx *ctx, int64_t *count);
    level; 2 full ghost-cell pressure operator; 3 FGMRES multi-dot; 4 FGMRES
    orthogonalisation; 5 Helmholtz colour pass; 6 convective term and
    AB2/CN right-hand side; 7 red-black pass on coarse levels; 8 residual +
-   restriction; 9 prolongation. Recording adds host overhead per launch. */
+   restriction; 9 prolongation; 10 every other kernel of the Poisson solver.
+   Recording adds host overhead per launch. */
 ibm_status ibm_kernel_timer(ibm_ctx *ctx, int enable);
 ibm_status ibm_kernel_time(ibm_ctx *ctx, int kernel, double *ms_total, int64_t *launches);
 

@@ -41,14 +41,16 @@ void dev_free(Ctx *c, void *p) {
 }
 
 void kt_begin(Ctx *c, int id) {
-    if (!c->kt.on || id < 0) return;
+    if (!c->kt.on) return;
+    if (id < 0) id = K_OTHER;
     if (c->kt.used + 2 > (int)c->kt.pool.size()) kt_flush(c);
     cudaEventRecord(c->kt.pool[c->kt.used], c->s);
     c->kt.ids[c->kt.used / 2] = id;
 }
 
 void kt_end(Ctx *c, int id) {
-    if (!c->kt.on || id < 0) return;
+    (void)id;
+    if (!c->kt.on) return;
     cudaEventRecord(c->kt.pool[c->kt.used + 1], c->s);
     c->kt.used += 2;
 }

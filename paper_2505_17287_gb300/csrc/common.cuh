@@ -19,7 +19,7 @@ constexpr uint8_t FLUID = IBM_FLUID, GHOST = IBM_GHOST, DEAD = IBM_DEAD;
 // RED_BLOCKS blocks of RED_THREADS threads, writes one partial per block,
 // and a single block then adds the partials in a fixed order.
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 4;   // 4 blocks per SM on a 152-SM GB300
+constexpr int RED_BLOCKS = 152 * 8;   // 8 blocks of 256 threads per SM on a 152-SM GB300
 
 // host-side status carrier: message + code
 struct Err {

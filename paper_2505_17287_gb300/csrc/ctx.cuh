@@ -35,7 +35,8 @@ enum KernelId {
     K_RBGS_C = 7,     // red-black colour pass, coarse levels
     K_RESTRICT = 8,   // residual + restriction
     K_PROLONG = 9,    // prolongation + correction
-    K_NKERNELS = 10
+    K_OTHER = 10,     // every other kernel of the Poisson solver
+    K_NKERNELS = 11
 };
 
 // Records a CUDA event pair around every launch of the timed kernels on the

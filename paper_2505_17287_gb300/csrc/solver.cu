@@ -258,27 +258,38 @@ struct Coef {
     double v[17];
 };
 
-// partial dots (FP64 accumulation): col i < ncols: (w, V_i); col ncols: (w, w)
+// Accumulator of the Arnoldi dot products: FP64 for FP64 vectors; for the
+// FP32 cycle each thread sums its own elements in FP32 and the cross-thread
+// reduction is FP64 (per-element FP64 arithmetic would make this streaming
+// kernel FP64-bound on GB300)
+template <typename T> struct Acc { typedef double type; };
+template <> struct Acc<float> { typedef float type; };
+
+// partial dots: col i < ncols: (w, V_i); col ncols: (w, w)
 template <typename T>
 __global__ void k_mdot(int64_t n, const T *__restrict__ w, const T *const *__restrict__ V, int ncols,
                        double *__restrict__ part) {
+    typedef typename Acc<T>::type A;
     __shared__ double sh[32];
-    double acc[17];
+    A acc[17];
 #pragma unroll
-    for (int q = 0; q < 17; ++q) acc[q] = 0.0;
-    double ww = 0.0;
+    for (int q = 0; q < 17; ++q) acc[q] = A(0);
+    A ww = A(0);
     GRID_STRIDE(c, n) {
-        const double a = (double)w[c];
+        const A a = (A)w[c];
         ww += a * a;
 #pragma unroll
         for (int q = 0; q < 17; ++q)
-            if (q < ncols) acc[q] += a * (double)V[q][c];
+            if (q < ncols) acc[q] += a * (A)V[q][c];
     }
-    for (int q = 0; q < ncols; ++q) {
-        const double t = block_sum<RED_THREADS>(acc[q], sh);
-        if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
+#pragma unroll
+    for (int q = 0; q < 17; ++q) {
+        if (q < ncols) {   // ncols is uniform over the block
+            const double t = block_sum<RED_THREADS>((double)acc[q], sh);
+            if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
+        }
     }
-    const double t = block_sum<RED_THREADS>(ww, sh);
+    const double t = block_sum<RED_THREADS>((double)ww, sh);
     if (threadIdx.x == 0) part[(size_t)ncols * gridDim.x + blockIdx.x] = t;
 }
 
@@ -286,20 +297,21 @@ __global__ void k_mdot(int64_t n, const T *__restrict__ w, const T *const *__res
 template <typename T>
 __global__ void k_orth(int64_t n, T *__restrict__ w, const T *const *__restrict__ V, int ncols, Coef h,
                        double *__restrict__ part) {
+    typedef typename Acc<T>::type A;
     __shared__ double sh[32];
     T hv[17];
 #pragma unroll
     for (int q = 0; q < 17; ++q) hv[q] = (T)h.v[q];
-    double ww = 0.0;
+    A ww = A(0);
     GRID_STRIDE(c, n) {
         T a = w[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
             if (q < ncols) a -= hv[q] * V[q][c];
         w[c] = a;
-        ww += (double)a * (double)a;
+        ww += (A)a * (A)a;
     }
-    const double t = block_sum<RED_THREADS>(ww, sh);
+    const double t = block_sum<RED_THREADS>((double)ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 

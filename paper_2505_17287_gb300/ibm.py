@@ -199,7 +199,7 @@ def ibm_launch_count(ctx):
 
 
 KERNEL_IDS = {"rbgs0": 0, "spmv0": 1, "apply_A": 2, "mdot": 3, "orth": 4, "helm": 5, "conv": 6,
-              "rbgs_coarse": 7, "restrict": 8, "prolong": 9}
+              "rbgs_coarse": 7, "restrict": 8, "prolong": 9, "other": 10}
 
 
 def ibm_kernel_timer(ctx, enable: int):
