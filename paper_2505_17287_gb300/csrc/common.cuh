@@ -109,6 +109,7 @@ struct MGLevel {
     T *x, *f;          // correction and right-hand side of coarse levels
     // fine-level description
     const uint8_t *type;
+    const uint8_t *omask;       // bit f: face f (-x,+x,-y,+y,-z,+z) open; bit 7: cell FLUID
     const T *wx, *wy, *wz;      // cell widths
     const T *rhx, *rhy, *rhz;   // 1 / centre spacing (index i: face between i-1 and i)
 };

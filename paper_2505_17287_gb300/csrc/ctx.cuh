@@ -9,6 +9,7 @@ template <typename T>
 struct MGHier {
     std::vector<MGLevel<T>> lv;
     bool fine0 = false;     // level 0 derives its coefficients (no arrays)
+    uint8_t *omask = nullptr;  // open-face mask of level 0 (fine variant)
     // 1D metrics of level 0 in precision T (fine variant)
     T *wx = nullptr, *wy = nullptr, *wz = nullptr, *rhx = nullptr, *rhy = nullptr, *rhz = nullptr;
     // PCG vectors on level 0

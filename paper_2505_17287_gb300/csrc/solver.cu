@@ -265,17 +265,43 @@ struct Coef {
 template <typename T> struct Acc { typedef double type; };
 template <> struct Acc<float> { typedef float type; };
 
-// partial dots: col i < ncols: (w, V_i); col ncols: (w, w)
+// 16-byte vector of T
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; enum { W = 4 }; };
+template <> struct Vec16<double> { typedef double2 type; enum { W = 2 }; };
+template <typename V> __device__ __forceinline__ auto vget(const V &v, int e);
+__device__ __forceinline__ float vget(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2 &v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4 &v, int e, float a) { if (e == 0) v.x = a; else if (e == 1) v.y = a; else if (e == 2) v.z = a; else v.w = a; }
+__device__ __forceinline__ void vset(double2 &v, int e, double a) { if (e == 0) v.x = a; else v.y = a; }
+
+// partial dots: col i < ncols: (w, V_i); col ncols: (w, w). 16-byte loads;
+// the vectors come from cudaMalloc or PyTorch's allocator (256-byte aligned)
 template <typename T>
 __global__ void k_mdot(int64_t n, const T *__restrict__ w, const T *const *__restrict__ V, int ncols,
                        double *__restrict__ part) {
     typedef typename Acc<T>::type A;
+    typedef typename Vec16<T>::type VT;
+    constexpr int W = Vec16<T>::W;
     __shared__ double sh[32];
     A acc[17];
 #pragma unroll
     for (int q = 0; q < 17; ++q) acc[q] = A(0);
     A ww = A(0);
-    GRID_STRIDE(c, n) {
+    const int64_t nv = n / W;
+    GRID_STRIDE(v, nv) {
+        const VT a = reinterpret_cast<const VT *>(w)[v];
+#pragma unroll
+        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+#pragma unroll
+        for (int q = 0; q < 17; ++q)
+            if (q < ncols) {
+                const VT b = reinterpret_cast<const VT *>(V[q])[v];
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b, e);
+            }
+    }
+    for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const A a = (A)w[c];
         ww += a * a;
 #pragma unroll
@@ -298,12 +324,28 @@ template <typename T>
 __global__ void k_orth(int64_t n, T *__restrict__ w, const T *const *__restrict__ V, int ncols, Coef h,
                        double *__restrict__ part) {
     typedef typename Acc<T>::type A;
+    typedef typename Vec16<T>::type VT;
+    constexpr int W = Vec16<T>::W;
     __shared__ double sh[32];
     T hv[17];
 #pragma unroll
     for (int q = 0; q < 17; ++q) hv[q] = (T)h.v[q];
     A ww = A(0);
-    GRID_STRIDE(c, n) {
+    const int64_t nv = n / W;
+    GRID_STRIDE(v, nv) {
+        VT a = reinterpret_cast<const VT *>(w)[v];
+#pragma unroll
+        for (int q = 0; q < 17; ++q)
+            if (q < ncols) {
+                const VT b = reinterpret_cast<const VT *>(V[q])[v];
+#pragma unroll
+                for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - hv[q] * vget(b, e));
+            }
+        reinterpret_cast<VT *>(w)[v] = a;
+#pragma unroll
+        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+    }
+    for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         T a = w[c];
 #pragma unroll
         for (int q = 0; q < 17; ++q)
@@ -463,14 +505,15 @@ __device__ __forceinline__ T k_offdiag(const MGLevel<T> &L, const T *__restrict_
     T s = T(0);
     if (FINE) {
         d = T(0);
+        const unsigned msk = L.omask[c];
         const T ayz = L.wy[j] * L.wz[k], axz = L.wx[i] * L.wz[k], axy = L.wx[i] * L.wy[j];
         T t;
-        if (i > 0 && L.type[c - 1] == FLUID) { t = ayz * L.rhx[i]; d += t; s += t * x[c - 1]; }
-        if (i < L.nx - 1 && L.type[c + 1] == FLUID) { t = ayz * L.rhx[i + 1]; d += t; s += t * x[c + 1]; }
-        if (j > 0 && L.type[c - sy] == FLUID) { t = axz * L.rhy[j]; d += t; s += t * x[c - sy]; }
-        if (j < L.ny - 1 && L.type[c + sy] == FLUID) { t = axz * L.rhy[j + 1]; d += t; s += t * x[c + sy]; }
-        if (k > 0 && L.type[c - sz] == FLUID) { t = axy * L.rhz[k]; d += t; s += t * x[c - sz]; }
-        if (k < L.nz - 1 && L.type[c + sz] == FLUID) { t = axy * L.rhz[k + 1]; d += t; s += t * x[c + sz]; }
+        if (msk & 1u) { t = ayz * L.rhx[i]; d += t; s += t * x[c - 1]; }
+        if (msk & 2u) { t = ayz * L.rhx[i + 1]; d += t; s += t * x[c + 1]; }
+        if (msk & 4u) { t = axz * L.rhy[j]; d += t; s += t * x[c - sy]; }
+        if (msk & 8u) { t = axz * L.rhy[j + 1]; d += t; s += t * x[c + sy]; }
+        if (msk & 16u) { t = axy * L.rhz[k]; d += t; s += t * x[c - sz]; }
+        if (msk & 32u) { t = axy * L.rhz[k + 1]; d += t; s += t * x[c + sz]; }
     } else {
         if (i > 0) s += L.tx[c] * x[c - 1];
         if (i < L.nx - 1) s += L.tx[c + 1] * x[c + 1];
@@ -485,8 +528,28 @@ __device__ __forceinline__ T k_offdiag(const MGLevel<T> &L, const T *__restrict_
 
 template <typename T, bool FINE>
 __device__ __forceinline__ bool active(const MGLevel<T> &L, int64_t c) {
-    if (FINE) return L.type[c] == FLUID;
+    if (FINE) return (L.omask[c] & 0x80u) != 0;
     return L.dinv[c] > T(0);
+}
+
+// open-face mask of the finest level
+__global__ void k_open_mask(GridDev g, const uint8_t *__restrict__ type, uint8_t *__restrict__ m) {
+    GRID_STRIDE(c, g.n) {
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+        unsigned v = 0;
+        if (type[c] == FLUID) {
+            v = 0x80u;
+            if (i > 0 && type[c - 1] == FLUID) v |= 1u;
+            if (i < g.nx - 1 && type[c + 1] == FLUID) v |= 2u;
+            if (j > 0 && type[c - sy] == FLUID) v |= 4u;
+            if (j < g.ny - 1 && type[c + sy] == FLUID) v |= 8u;
+            if (g.ndim == 3 && k > 0 && type[c - sz] == FLUID) v |= 16u;
+            if (g.ndim == 3 && k < g.nz - 1 && type[c + sz] == FLUID) v |= 32u;
+        }
+        m[c] = (uint8_t)v;
+    }
 }
 
 // red-black Gauss-Seidel, one colour: x_c = (f_c + sum T x_nb) / D_c on the
@@ -936,6 +999,11 @@ static ibm_status fill_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &o
         MGLevel<T> &M = H.lv[l];
         if (l == 0 && H.fine0) {
             M.type = c->type;
+            if (!H.omask) H.omask = (uint8_t *)dev_alloc(c, c->N);
+            if (!H.omask) return c->fail(IBM_ERR_OOM, "open-face mask allocation failed");
+            KL(-1, k_open_mask, nblk(c->N), 256, c->g, c->type, H.omask);
+            IBM_LAUNCHED(c);
+            M.omask = H.omask;
             continue;
         }
         KL(-1, k_level_coef<T>, nblk(M.n), 256, M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l], c->lhy[l],
@@ -1098,8 +1166,16 @@ template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, c->type, v, H.pr);
     IBM_LAUNCHED(c);
-    IBM_TRY(pcg(c, H, c->opts.inner_iters));
-    KL(-1, k_pre_out<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, H.px, z);
+    const T *xin = H.px;
+    if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
+        // one CG step is alpha times one V-cycle; FGMRES is invariant to
+        // that scalar, so the V-cycle output is used directly
+        IBM_TRY(vcycle(c, H, H.pr, H.pz));
+        xin = H.pz;
+    } else {
+        IBM_TRY(pcg(c, H, c->opts.inner_iters));
+    }
+    KL(-1, k_pre_out<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, xin, z);
     IBM_LAUNCHED(c);
     const OpT<T> o = op_of<T>(c);
     if (c->ng > 0) {
