@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-kernels", action="store_true", help="also report every timed kernel")
     ap.add_argument("--no-ktimer", action="store_true", help="skip the per-kernel timing pass")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the main timed run (the mixed run beside it is --no-mixed's)")
     return ap.parse_args()
 
 
@@ -186,7 +188,9 @@ def main():
         torch.distributed.barrier()
     case = wing_case(args.size)
     stream = torch.cuda.current_stream()
-    s = ibm.Solver(case, precision=ibm.IBM_FP64)
+    main_prec = ibm.IBM_MIXED if args.precision == "mixed" else ibm.IBM_FP64
+    s = ibm.Solver(case, precision=main_prec)
+    s.set_opts(precision=main_prec)
     t0 = time.perf_counter()
     s.set_body(case.verts, case.elems)
     info = s.classify()
