@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Mcell-steps/s per GB300, mixed vs FP64 at 1e-10 residual; serve p50/p99 latency"
 UNIT = "Mcell-steps/s"
 
+# DRAM traffic of one finest-level FP64 colour pass on the 384x256x256 wing,
+# from an ncu capture of the 256x192x192 case (513.9 MB per launch) scaled by
+# the cell count; valid for the kernel as captured
+RBGS64_TRAFFIC_BYTES = 513.9e6 * 25165824 / 9437184
+
 # algorithmic bytes per cell of one launch of the timed kernels
 # (FP64 s = 8, FP32 s = 4, cell type 1 byte); see the design notes
 def rbgs_pass_bytes(ncells, s, stored_coeffs=True):
@@ -265,7 +270,8 @@ def main():
         "clocks": clocks,
         "roofline": {"bound": "hbm", "kernel": "k_rbgs<double> (finest level, one colour pass)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": RBGS64_TRAFFIC_BYTES if args.size == "384,256,256" and main_prec == ibm.IBM_FP64 else None,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
                      "launches": rb_n, "avg_ms": rb_ms / rb_n if rb_n else None,
                      "algorithmic_bytes_per_launch": rb_bytes},

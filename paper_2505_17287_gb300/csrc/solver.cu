@@ -132,6 +132,12 @@ ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_hos
 // full ghost-cell pressure operator (FP64)
 // ---------------------------------------------------------------------------
 
+// Accumulator type of per-thread partial sums: FP64 for FP64 vectors; FP32
+// for FP32 vectors, whose cross-thread reductions are FP64 (per-element FP64
+// arithmetic would make the FP32 streaming kernels FP64-bound on GB300)
+template <typename T> struct Acc { typedef double type; };
+template <> struct Acc<float> { typedef float type; };
+
 // per-axis operator coefficients in precision T (the FP64 ones are the
 // GridDev arrays; FP32 copies serve the FP32 Krylov cycle of mixed mode)
 template <typename T>
@@ -176,7 +182,7 @@ template <typename T>
 __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, const T *__restrict__ x,
                           const T *__restrict__ b, T sgn, T *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
-    double acc = 0.0;
+    typename Acc<T>::type acc = 0;
     GRID_STRIDE(c, g.n) {
         const uint8_t t = type[c];
         if (t == GHOST) continue;
@@ -185,10 +191,10 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
         split3(g, (uint32_t)c, i, j, k);
         const T v = sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
         y[c] = v;
-        acc += (double)(o.dx[i] * o.dy[j] * o.dz[k]) * (double)v;
+        acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
     }
-    acc = block_sum<RED_THREADS>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double tot = block_sum<RED_THREADS>((double)acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
 // GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m) + b_g (b may be null = 0;
@@ -258,12 +264,6 @@ struct Coef {
     double v[17];
 };
 
-// Accumulator of the Arnoldi dot products: FP64 for FP64 vectors; for the
-// FP32 cycle each thread sums its own elements in FP32 and the cross-thread
-// reduction is FP64 (per-element FP64 arithmetic would make this streaming
-// kernel FP64-bound on GB300)
-template <typename T> struct Acc { typedef double type; };
-template <> struct Acc<float> { typedef float type; };
 
 // 16-byte vector of T
 template <typename T> struct Vec16;
@@ -748,12 +748,13 @@ __global__ void k_beta(double *scal) {
 
 // preconditioner input / output conversion
 template <typename T>
-__global__ void k_pre_in(GridDev g, const uint8_t *__restrict__ type, const T *__restrict__ v, T *__restrict__ f) {
+__global__ void k_pre_in(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, const T *__restrict__ v,
+                         T *__restrict__ f) {
     GRID_STRIDE(c, g.n) {
         if (type[c] != FLUID) { f[c] = T(0); continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        f[c] = (T)(-(g.dx[i] * g.dy[j] * g.dz[k]) * (double)v[c]);
+        f[c] = -(o.dx[i] * o.dy[j] * o.dz[k]) * v[c];
     }
 }
 template <typename T>
@@ -1164,7 +1165,8 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 // z = M^{-1} v, vectors and multigrid in precision T
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
-    KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, c->type, v, H.pr);
+    const OpT<T> oin = op_of<T>(c);
+    KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, oin, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     const T *xin = H.px;
     if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
