@@ -74,6 +74,24 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank scalar over all ranks (replicas: each rank times its
+    own grid; the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job Mcell-steps/s of `world` independent replicas."""
+    return cells * steps * world / (max_ms / 1e3) / 1e6
+
+
 class Clocks:
     """nvidia-smi sampler during the timed region."""
 
@@ -227,10 +245,7 @@ def main():
             for name, kid in ibm.KERNEL_IDS.items():
                 kt[name] = ibm.ibm_kernel_time(s.ctx, kid)
             ibm.ibm_kernel_timer(s.ctx, 0)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ms, stats, launches, kt
 
     for _ in range(args.warmup):
@@ -239,7 +254,7 @@ def main():
     with Clocks(local) as clk:
         ms, stats, launches, _ = timed(args.steps)
     clocks = clk.summary()
-    value = N * args.steps * world / (ms / 1e3) / 1e6
+    value = replica_throughput(N, args.steps, world, ms)
     poisson_ms64 = sum(x["ms_poisson"] for x in stats)
     # roofline of the dominant kernel: a second pass over the same number of
     # steps with the event timer on (the timer adds host work per launch, so
@@ -321,10 +336,7 @@ def main():
                 ibm.ibm_get_field(s.ctx, ibm.FIELDS[k], host_out[k].data_ptr(), 0, host_out[k].numel() * 8)
         sync_all()
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world)
         result["e2e"] = {"value": N * ne2e * world / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h, "steps": ne2e,
                          "path": "ibm_set_field (pinned host) + ibm_step + ibm_get_field (pinned host)"}

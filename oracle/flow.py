@@ -255,6 +255,38 @@ def poisson_matrix(g: Grid, typ, tabs):
                          shape=(g.N, g.N))
 
 
+def poisson_rows(g: Grid, typ, tabs, phi, rows):
+    """(A phi) at the given linear cell indices only, from the definition of
+    the rows (for grids too large to assemble): FLUID rows sum over their
+    interior faces (A/hc)(phi_nb - phi_c) / vol; GHOST rows phi_G - sum wp
+    phi_m; DEAD rows phi."""
+    t = typ.ravel()
+    f = phi.ravel()
+    rows = np.asarray(rows, dtype=np.int64)
+    nx, ny, nz = g.nx, g.ny, g.nz
+    i, j, k = rows % nx, (rows // nx) % ny, rows // (nx * ny)
+    out = np.zeros(rows.size)
+    vol = g.h[0][i] * g.h[1][j] * g.h[2][k]
+    area = [g.h[1][j] * g.h[2][k], g.h[0][i] * g.h[2][k], g.h[0][i] * g.h[1][j]]
+    idx = [i, j, k]
+    n = [nx, ny, nz]
+    stride = [1, nx, nx * ny]
+    fl = t[rows] == FLUID
+    for a in axes(g):
+        lo = fl & (idx[a] > 0)
+        hi = fl & (idx[a] < n[a] - 1)
+        out[lo] += area[a][lo] / g.hc[a][idx[a][lo] - 1] * (f[rows[lo] - stride[a]] - f[rows[lo]]) / vol[lo]
+        out[hi] += area[a][hi] / g.hc[a][idx[a][hi]] * (f[rows[hi] + stride[a]] - f[rows[hi]]) / vol[hi]
+    pos = {int(c): q for q, c in enumerate(tabs["gidx"])}
+    for r, c in enumerate(rows):
+        if t[c] == GHOST:
+            q = pos[int(c)]
+            out[r] = f[c] - np.dot(tabs["wp"][q], f[tabs["sidx"][q]])
+        elif t[c] == DEAD:
+            out[r] = f[c]
+    return out
+
+
 def helmholtz_matrix(g: Grid, typ, tabs, comp, alpha, bc=DEFAULT_BC):
     """Crank-Nicolson velocity operator (I - alpha L0) on FLUID rows (L0 the
     viscous operator without its boundary values), Dirichlet ghost rows

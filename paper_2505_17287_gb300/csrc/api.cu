@@ -120,9 +120,11 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     return true;
 }
 
-// Krylov storage: FGMRES(m) needs m+1 basis and m preconditioned vectors;
-// BiCGStab uses six of the first and two of the second
-static ibm_status alloc_krylov(Ctx *c, int m) {
+namespace ibm {
+// FP64 Krylov storage, allocated on first use by an FP64 outer iteration:
+// FGMRES(m) needs m+1 basis and m preconditioned vectors; BiCGStab uses six
+// of the first and two of the second. Mixed precision never allocates it.
+ibm_status alloc_krylov(Ctx *c, int m) {
     if (m <= c->m_cap) return IBM_OK;
     for (double *p : c->V) dev_free(c, p);
     for (double *p : c->Z) dev_free(c, p);
@@ -142,6 +144,7 @@ static ibm_status alloc_krylov(Ctx *c, int m) {
     c->m_cap = m;
     return IBM_OK;
 }
+}  // namespace ibm
 
 static double *upload(Ctx *c, const std::vector<double> &h) {
     double *d = (double *)dev_alloc(c, sizeof(double) * (h.size() ? h.size() : 1));
@@ -293,7 +296,6 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     if (!c->p || !c->b || !c->w || !c->rr || !c->part || !c->scal) return c->fail(IBM_ERR_OOM, "solver vector allocation failed");
     IBM_CUDA(c, cudaMemsetAsync(c->p, 0, nb, c->s));
     IBM_CUDA(c, cudaMemsetAsync(c->scal, 0, sizeof(double) * 64, c->s));
-    IBM_TRY(alloc_krylov(c, c->opts.restart));
     IBM_TRY(build_levels(c));
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
     return IBM_OK;
@@ -343,10 +345,8 @@ extern "C" ibm_status ibm_set_opts(ibm_ctx *c, const ibm_solver_opts *o) {
     if (!c || !o) return IBM_ERR_ARG;
     std::string why;
     if (!opts_ok(o, why)) return c->fail(IBM_ERR_ARG, why);
-    const bool to_mixed = o->precision == IBM_MIXED && !c->mg32.built;
     c->opts = *o;
-    IBM_TRY(alloc_krylov(c, o->restart));
-    if (to_mixed && c->classified) IBM_TRY(mg_build(c));
+
     return IBM_OK;
 }
 

@@ -135,6 +135,9 @@ struct Ctx {
     }
 };
 
+// FP64 Krylov storage on first use (api.cu)
+ibm_status alloc_krylov(Ctx *c, int m);
+
 // event timer (api.cu)
 void kt_begin(Ctx *c, int id);
 void kt_end(Ctx *c, int id);

@@ -1039,9 +1039,15 @@ ibm_status mg_build(Ctx *c) {
            C.fx, C.fy, C.fz, ox[l], oy[l], oz[l]);
         IBM_LAUNCHED(c);
     }
-    if (!c->mg64.built) IBM_TRY(build_hier<double>(c, c->mg64, false));
-    IBM_TRY(fill_hier<double>(c, c->mg64, ox, oy, oz));
-    if (c->opts.precision == IBM_MIXED) {
+    // each hierarchy is built when its precision is first used and refreshed
+    // on every later classification
+    const bool need64 = c->opts.precision == IBM_FP64 || c->mg64.built;
+    const bool need32 = c->opts.precision == IBM_MIXED || c->mg32.built;
+    if (need64) {
+        if (!c->mg64.built) IBM_TRY(build_hier<double>(c, c->mg64, false));
+        IBM_TRY(fill_hier<double>(c, c->mg64, ox, oy, oz));
+    }
+    if (need32) {
         if (!c->mg32.built) IBM_TRY(build_hier<float>(c, c->mg32, true));
         IBM_TRY(fill_hier<float>(c, c->mg32, ox, oy, oz));
     }
@@ -1492,7 +1498,8 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
 
 // Solve P A phi = P rhs. rhs: FLUID rows read; phi: guess in, solution out.
 ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, int maxit, ibm_solve_stats *st) {
-    if (!c->mg64.built || (c->opts.precision == IBM_MIXED && !c->mg32.built)) IBM_TRY(mg_build(c));
+    if ((c->opts.precision == IBM_FP64 && !c->mg64.built) || (c->opts.precision == IBM_MIXED && !c->mg32.built))
+        IBM_TRY(mg_build(c));
     const int64_t n = c->N;
     IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
     // b = P rhs on FLUID rows, 0 elsewhere
@@ -1515,6 +1522,8 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     if (!(bnorm > 1e-300)) {
         IBM_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * n, c->s));
     } else {
+        if (c->opts.outer == IBM_OUTER_BICGSTAB || c->opts.precision != IBM_MIXED)
+            IBM_TRY(alloc_krylov(c, c->opts.restart));
         if (c->opts.outer == IBM_OUTER_BICGSTAB) status = bicgstab(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
         else if (c->opts.precision == IBM_MIXED) status = mixed_refinement(c, phi, bnorm, rtol, maxit, &outer, &inner, &rel);
         else status = fgmres<double>(c, kry64(c), phi, c->b, bnorm, rtol, maxit, false, &outer, &inner, &rel);
