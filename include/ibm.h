@@ -103,6 +103,8 @@ typedef struct {
     double band_omega;  /* their damping factor, in (0, 1] */
     double mixed_inner_rtol; /* IBM_MIXED with FGMRES: residual reduction asked of each
                            FP32 Krylov solve inside the FP64 defect correction */
+    int mg_interp;      /* multigrid transfer: 1 trilinear prolongation with its transpose
+                           as restriction, 0 piecewise constant with summation */
 } ibm_solver_opts;
 
 typedef struct {
@@ -158,7 +160,7 @@ enum {
 /* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
-   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4. */
+   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -100,6 +100,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->band_sweeps = 0;
     o->band_omega = 0.7;
     o->mixed_inner_rtol = 1e-4;
+    o->mg_interp = 1;
     return IBM_OK;
 }
 
@@ -117,6 +118,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->band_sweeps < 0 || o->band_sweeps > 64) { why = "band_sweeps must be in [0, 64]"; return false; }
     if (!(o->band_omega > 0.0 && o->band_omega <= 1.0)) { why = "band_omega must be in (0, 1]"; return false; }
     if (!(o->mixed_inner_rtol > 0.0 && o->mixed_inner_rtol < 1.0)) { why = "mixed_inner_rtol must be in (0, 1)"; return false; }
+    if (o->mg_interp != 0 && o->mg_interp != 1) { why = "mg_interp must be 0 or 1"; return false; }
     return true;
 }
 
@@ -205,6 +207,54 @@ static ibm_status build_levels(Ctx *c) {
         axis_arrays(L.zf, cc, w, h);
         c->lhz.push_back(upload(c, h));
         if (!c->lhx.back() || !c->lhy.back() || !c->lhz.back()) return c->fail(IBM_ERR_OOM, "level geometry allocation failed");
+    }
+    // trilinear transfer tables: linear interpolation between the two coarse
+    // centres around each fine centre (the nearer-side neighbour of its
+    // parent), the parent alone at the ends and along uncoarsened axes
+    for (int a = 0; a < 3; ++a) {
+        c->tI[a].assign(c->lg.size(), nullptr);
+        c->tJ[a].assign(c->lg.size(), nullptr);
+        c->tw64[a].assign(c->lg.size(), nullptr);
+        c->tw32[a].assign(c->lg.size(), nullptr);
+    }
+    for (size_t l = 1; l < c->lg.size(); ++l) {
+        const LevelGeom &F = c->lg[l - 1], &C = c->lg[l];
+        const std::vector<double> *ff[3] = {&F.xf, &F.yf, &F.zf}, *cf[3] = {&C.xf, &C.yf, &C.zf};
+        const int fac[3] = {C.fx, C.fy, C.fz};
+        for (int a = 0; a < 3; ++a) {
+            const std::vector<double> &fa = *ff[a], &ca = *cf[a];
+            const int nf = (int)fa.size() - 1, nc = (int)ca.size() - 1;
+            std::vector<int> I(nf), J(nf);
+            std::vector<double> w(nf), w32d(nf);
+            std::vector<float> w32(nf);
+            for (int i = 0; i < nf; ++i) {
+                const double xi = 0.5 * (fa[i] + fa[i + 1]);
+                if (fac[a] == 1) { I[i] = i; J[i] = -1; w[i] = 1.0; }
+                else {
+                    int pI = i / 2 < nc - 1 ? i / 2 : nc - 1;
+                    const double XI = 0.5 * (ca[pI] + ca[pI + 1]);
+                    int pJ = xi < XI ? pI - 1 : pI + 1;
+                    if (xi == XI || pJ < 0 || pJ >= nc) { I[i] = pI; J[i] = -1; w[i] = 1.0; }
+                    else {
+                        const double XJ = 0.5 * (ca[pJ] + ca[pJ + 1]);
+                        I[i] = pI; J[i] = pJ; w[i] = (xi - XJ) / (XI - XJ);
+                    }
+                }
+                w32[i] = (float)w[i];
+            }
+            int *dI = (int *)dev_alloc(c, sizeof(int) * nf), *dJ = (int *)dev_alloc(c, sizeof(int) * nf);
+            double *dw = (double *)dev_alloc(c, sizeof(double) * nf);
+            float *dw32 = (float *)dev_alloc(c, sizeof(float) * nf);
+            if (!dI || !dJ || !dw || !dw32) return c->fail(IBM_ERR_OOM, "transfer table allocation failed");
+            IBM_CUDA(c, cudaMemcpy(dI, I.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
+            IBM_CUDA(c, cudaMemcpy(dJ, J.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
+            IBM_CUDA(c, cudaMemcpy(dw, w.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+            IBM_CUDA(c, cudaMemcpy(dw32, w32.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
+            c->tI[a][l] = dI;
+            c->tJ[a][l] = dJ;
+            c->tw64[a][l] = dw;
+            c->tw32[a][l] = dw32;
+        }
     }
     return IBM_OK;
 }

@@ -14,6 +14,9 @@ struct MGHier {
     T *wx = nullptr, *wy = nullptr, *wz = nullptr, *rhx = nullptr, *rhy = nullptr, *rhz = nullptr;
     // PCG vectors on level 0
     T *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
+    // per fine level: residual scratch (level >= 1) and 1 / sum of the active
+    // coarse interpolation weights of each cell (trilinear transfer)
+    std::vector<T *> res, pn;
     bool built = false;
 };
 
@@ -122,6 +125,12 @@ struct Ctx {
     double *btmp = nullptr;
     std::vector<LevelGeom> lg;
     std::vector<double *> lhx, lhy, lhz;   // per level centre spacing (device)
+    // trilinear transfer from level l-1 to level l, per axis (entry 0 unused):
+    // fine index i interpolates coarse tI[i] with weight tw[i] and coarse
+    // tJ[i] (-1: none) with 1 - tw[i]
+    std::vector<int *> tI[3], tJ[3];
+    std::vector<double *> tw64[3];
+    std::vector<float *> tw32[3];
     MGHier<double> mg64;
     MGHier<float> mg32;
 

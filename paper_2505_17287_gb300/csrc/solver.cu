@@ -615,6 +615,135 @@ __global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx,
     x[c] += C.x[p];
 }
 
+// trilinear transfer ----------------------------------------------------------
+
+template <typename T>
+struct Xfer {
+    const int *Ix, *Jx, *Iy, *Jy, *Iz, *Jz;
+    const T *wx, *wy, *wz;
+};
+
+// the up-to-two coarse indices and weights of fine index i along one axis
+template <typename T>
+__device__ __forceinline__ int xfer_axis(const int *I, const int *J, const T *w, int i, int *idx, T *wt) {
+    idx[0] = I[i];
+    wt[0] = w[i];
+    if (J[i] >= 0) {
+        idx[1] = J[i];
+        wt[1] = T(1) - w[i];
+        return 2;
+    }
+    return 1;
+}
+
+// fine residual r = f - K x on active cells, 0 elsewhere
+template <typename T, bool FINE>
+__global__ void k_resid(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, T *__restrict__ r) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    if (!active<T, FINE>(L, c)) { r[c] = T(0); return; }
+    T d;
+    const T off = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+    r[c] = f[c] - (d * x[c] - off);
+}
+
+// pn_c = 1 / (sum of the weights of the active coarse cells of c), 0 if c inactive
+template <typename T, bool FINE>
+__global__ void k_pnorm(MGLevel<T> L, MGLevel<T> C, Xfer<T> X, T *__restrict__ pn) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    if (!active<T, FINE>(L, c)) { pn[c] = T(0); return; }
+    int ia[2], ib[2], ic[2];
+    T wa[2], wb[2], wc[2];
+    const int na = xfer_axis(X.Ix, X.Jx, X.wx, i, ia, wa);
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
+    T sum = T(0);
+    for (int q3 = 0; q3 < nc; ++q3)
+        for (int q2 = 0; q2 < nb; ++q2)
+            for (int q1 = 0; q1 < na; ++q1) {
+                const int64_t cc = ((int64_t)ic[q3] * C.ny + ib[q2]) * C.nx + ia[q1];
+                if (C.dinv[cc] > T(0)) sum += (wa[q1] * wb[q2]) * wc[q3];
+            }
+    pn[c] = sum > T(0) ? T(1) / sum : T(0);
+}
+
+// x_c += pn_c * sum over the active coarse cells C of w_cC x_C
+template <typename T, bool FINE>
+__global__ void k_prolong_tl(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, Xfer<T> X, const T *__restrict__ pn) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    const T p = pn[c];
+    if (!(p > T(0))) return;
+    int ia[2], ib[2], ic[2];
+    T wa[2], wb[2], wc[2];
+    const int na = xfer_axis(X.Ix, X.Jx, X.wx, i, ia, wa);
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
+    T acc = T(0);
+    for (int q3 = 0; q3 < nc; ++q3)
+        for (int q2 = 0; q2 < nb; ++q2)
+            for (int q1 = 0; q1 < na; ++q1) {
+                const int64_t cc = ((int64_t)ic[q3] * C.ny + ib[q2]) * C.nx + ia[q1];
+                if (C.dinv[cc] > T(0)) acc += ((wa[q1] * wb[q2]) * wc[q3]) * C.x[cc];
+            }
+    x[c] += acc * p;
+}
+
+// the fine cells whose interpolation reaches coarse index I along one axis
+template <typename T>
+__device__ __forceinline__ int xfer_gather(const int *I, const int *J, const T *w, int nf, int fac, int Ic, int *idx,
+                                           T *wt) {
+    if (fac == 1) {
+        idx[0] = Ic;
+        wt[0] = T(1);
+        return 1;
+    }
+    int n = 0;
+    for (int i = 2 * Ic - 1; i <= 2 * Ic + 2; ++i) {
+        if (i < 0 || i >= nf) continue;
+        if (I[i] == Ic) { idx[n] = i; wt[n] = w[i]; ++n; }
+        else if (J[i] == Ic) { idx[n] = i; wt[n] = T(1) - w[i]; ++n; }
+    }
+    return n;
+}
+
+// restriction by the transpose of the prolongation: f_C = sum_c w_cC pn_c r_c
+template <typename T>
+__global__ void k_restrict_tl(MGLevel<T> L, const T *__restrict__ r, const T *__restrict__ pn, MGLevel<T> C,
+                              Xfer<T> X, int fx, int fy, int fz) {
+    const int64_t row = blockIdx.x;
+    const int Jc = (int)(row % C.ny), Kc = (int)(row / C.ny);
+    const int Ic = blockIdx.y * blockDim.x + threadIdx.x;
+    if (Ic >= C.nx) return;
+    const int64_t cc = row * C.nx + Ic;
+    C.x[cc] = T(0);
+    if (!(C.dinv[cc] > T(0))) { C.f[cc] = T(0); return; }
+    int ia[4], ib[4], ic[4];
+    T wa[4], wb[4], wc[4];
+    const int na = xfer_gather(X.Ix, X.Jx, X.wx, L.nx, fx, Ic, ia, wa);
+    const int nb = xfer_gather(X.Iy, X.Jy, X.wy, L.ny, fy, Jc, ib, wb);
+    const int nc = xfer_gather(X.Iz, X.Jz, X.wz, L.nz, fz, Kc, ic, wc);
+    T acc = T(0);
+    for (int q3 = 0; q3 < nc; ++q3)
+        for (int q2 = 0; q2 < nb; ++q2)
+            for (int q1 = 0; q1 < na; ++q1) {
+                const int64_t f = ((int64_t)ic[q3] * L.ny + ib[q2]) * L.nx + ia[q1];
+                const T p = pn[f];
+                if (p > T(0)) acc += ((wa[q1] * wb[q2]) * wc[q3]) * (p * r[f]);
+            }
+    C.f[cc] = acc;
+}
+
 // coarsest level: red-black sweeps in one block, all data in shared memory.
 // The level operator is singular (constants); the right-hand side is made
 // compatible by removing its mean over the active cells, and the solution is
@@ -923,6 +1052,19 @@ __global__ void k_band_gpos(int64_t nb, const int64_t *__restrict__ band, int64_
 // ---------------------------------------------------------------------------
 
 template <typename T>
+static Xfer<T> xfer_of(Ctx *c, int l);
+template <>
+Xfer<double> xfer_of<double>(Ctx *c, int l) {
+    return Xfer<double>{c->tI[0][l], c->tJ[0][l], c->tI[1][l], c->tJ[1][l], c->tI[2][l], c->tJ[2][l],
+                        c->tw64[0][l], c->tw64[1][l], c->tw64[2][l]};
+}
+template <>
+Xfer<float> xfer_of<float>(Ctx *c, int l) {
+    return Xfer<float>{c->tI[0][l], c->tJ[0][l], c->tI[1][l], c->tJ[1][l], c->tI[2][l], c->tJ[2][l],
+                       c->tw32[0][l], c->tw32[1][l], c->tw32[2][l]};
+}
+
+template <typename T>
 static ibm_status alloc_level_arrays(Ctx *c, MGLevel<T> &M, bool coeffs, bool vecs) {
     const size_t bytes = sizeof(T) * (size_t)M.n;
     M.tx = M.ty = M.tz = M.d = M.dinv = M.x = M.f = nullptr;
@@ -981,6 +1123,14 @@ static ibm_status build_hier(Ctx *c, MGHier<T> &H, bool fine0) {
         M.wx = H.wx; M.wy = H.wy; M.wz = H.wz;
         M.rhx = H.rhx; M.rhy = H.rhy; M.rhz = H.rhz;
     }
+    H.res.assign(L, nullptr);
+    H.pn.assign(L, nullptr);
+    for (int l = 0; l + 1 < L; ++l) {
+        const size_t bytes = sizeof(T) * (size_t)H.lv[l].n;
+        H.pn[l] = (T *)dev_alloc(c, bytes);
+        if (l > 0) H.res[l] = (T *)dev_alloc(c, bytes);
+        if (!H.pn[l] || (l > 0 && !H.res[l])) return c->fail(IBM_ERR_OOM, "transfer buffer allocation failed");
+    }
     const size_t b0 = sizeof(T) * (size_t)c->N;
     H.px = (T *)dev_alloc(c, b0);
     H.pr = (T *)dev_alloc(c, b0);
@@ -1010,6 +1160,14 @@ static ibm_status fill_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &o
         KL(-1, k_level_coef<T>, nblk(M.n), 256, M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l], c->lhy[l],
            c->lhz[l], M.tx, M.ty, M.tz);
         KL(-1, k_level_diag<T>, nblk(M.n), 256, M);
+        IBM_LAUNCHED(c);
+    }
+    // trilinear transfer normalisation of every fine level
+    for (int l = 0; l + 1 < L; ++l) {
+        MGLevel<T> &M = H.lv[l];
+        const dim3 grid = rows_grid(M.nx, M.ny, M.nz, 1, 128);
+        if (l == 0 && H.fine0) KL(-1, (k_pnorm<T, true>), grid, 128, M, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
+        else KL(-1, (k_pnorm<T, false>), grid, 128, M, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
         IBM_LAUNCHED(c);
     }
     return IBM_OK;
@@ -1115,8 +1273,18 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         MGLevel<T> &Cl = H.lv[l + 1];
         auto &CG = c->lg[l + 1];
         const dim3 grid = rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx);
-        if (l == 0 && H.fine0) KL(K_RESTRICT, (k_resid_restrict<T, true>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
-        else KL(K_RESTRICT, (k_resid_restrict<T, false>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
+        if (c->opts.mg_interp == 1) {
+            // fine residual, then restriction by the transpose of the trilinear prolongation
+            T *r = l == 0 ? H.pq : H.res[l];
+            const dim3 fgrid = rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx);
+            if (l == 0 && H.fine0) KL(K_RESTRICT, (k_resid<T, true>), fgrid, bx, Lf, f, x, r);
+            else KL(K_RESTRICT, (k_resid<T, false>), fgrid, bx, Lf, f, x, r);
+            KL(K_RESTRICT, k_restrict_tl<T>, grid, bx, Lf, r, H.pn[l], Cl, xfer_of<T>(c, l + 1), CG.fx, CG.fy, CG.fz);
+        } else if (l == 0 && H.fine0) {
+            KL(K_RESTRICT, (k_resid_restrict<T, true>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
+        } else {
+            KL(K_RESTRICT, (k_resid_restrict<T, false>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
+        }
         IBM_LAUNCHED(c);
     }
     KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
@@ -1127,8 +1295,16 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         MGLevel<T> &Lf = H.lv[l];
         auto &CG = c->lg[l + 1];
         const dim3 grid = rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx);
-        if (l == 0 && H.fine0) KL(K_PROLONG, (k_prolong<T, true>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
-        else KL(K_PROLONG, (k_prolong<T, false>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
+        if (c->opts.mg_interp == 1) {
+            if (l == 0 && H.fine0)
+                KL(K_PROLONG, (k_prolong_tl<T, true>), grid, bx, Lf, x, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
+            else
+                KL(K_PROLONG, (k_prolong_tl<T, false>), grid, bx, Lf, x, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
+        } else if (l == 0 && H.fine0) {
+            KL(K_PROLONG, (k_prolong<T, true>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
+        } else {
+            KL(K_PROLONG, (k_prolong<T, false>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
+        }
         IBM_LAUNCHED(c);
         for (int s = 0; s < nu2; ++s) {
             IBM_TRY(rbgs(c, H, l, f, x, 1));

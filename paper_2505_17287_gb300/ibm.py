@@ -46,7 +46,7 @@ class ibm_solver_opts(Structure):
                 ("nu1", c_int), ("nu2", c_int), ("coarse_sweeps", c_int), ("helm_rtol", c_double),
                 ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
                 ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
-                ("mixed_inner_rtol", c_double)]
+                ("mixed_inner_rtol", c_double), ("mg_interp", c_int)]
 
 
 class ibm_table_info(Structure):
