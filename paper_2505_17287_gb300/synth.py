@@ -294,19 +294,27 @@ def cylinder_case(nx: int = 256, ny: int = 128, nseg: int = 512, Re: float = 100
 
 
 def wing_case(nx: int = 384, ny: int = 256, nz: int = 256, Re: float = 1000.0,
-              dt: float = 0.002, nsteps: int = 10, ratio: float = 1.01,
+              dt: float = 0.002, nsteps: int = 10, ratio: float = None,
               n_chord: int = 100, n_span: int = 50) -> Case:
     """3D NACA0012 finite wing, chord 1, span 2 (aspect ratio 2), 15 degrees
     incidence, in a box 10 chords wide with the leading edge 3 chords from
     the inflow (Section 3.2.2 shaped). Grid stretched away from a uniform
-    core that covers the wing's bounding box plus a quarter chord."""
+    core that covers the wing's bounding box plus a quarter chord.
+
+    The stretching profile is that of the 384x256x256 grid with a growth of
+    1.01 per cell; other cell counts sample the same profile, so a grid with
+    twice the cells per axis refines the reference grid (growth
+    1.01**(384/nx) per cell along x, likewise y and z). `ratio` overrides
+    the growth on every axis."""
     v, t = naca_wing(n_chord, n_span, 2.0, 15.0)
     lo, hi = v.min(0) - 0.25, v.max(0) + 0.25
-    xf = stretched_faces(-3.0, 7.0, nx, lo[0], hi[0], ratio)
-    yf = stretched_faces(-5.0, 5.0, ny, lo[1], hi[1], ratio)
-    zf = stretched_faces(-5.0, 5.0, nz, lo[2], hi[2], ratio)
+    ref = (384, 256, 256)
+    r = [ratio if ratio is not None else 1.01 ** (ref[a] / n) for a, n in enumerate((nx, ny, nz))]
+    xf = stretched_faces(-3.0, 7.0, nx, lo[0], hi[0], r[0])
+    yf = stretched_faces(-5.0, 5.0, ny, lo[1], hi[1], r[1])
+    zf = stretched_faces(-5.0, 5.0, nz, lo[2], hi[2], r[2])
     return Case("wing3d", 3, xf, yf, zf, v, t, Re, dt, nsteps,
-                meta={"nx": nx, "ny": ny, "nz": nz, "ntri": int(t.shape[0]), "ratio": ratio})
+                meta={"nx": nx, "ny": ny, "nz": nz, "ntri": int(t.shape[0]), "ratio": r})
 
 
 def sphere_case(n: int = 32, radius: float = 0.3, Re: float = 200.0, dt: float = None,
