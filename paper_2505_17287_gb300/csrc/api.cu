@@ -216,6 +216,9 @@ static ibm_status build_levels(Ctx *c) {
         c->tJ[a].assign(c->lg.size(), nullptr);
         c->tw64[a].assign(c->lg.size(), nullptr);
         c->tw32[a].assign(c->lg.size(), nullptr);
+        c->gI[a].assign(c->lg.size(), nullptr);
+        c->gw64[a].assign(c->lg.size(), nullptr);
+        c->gw32[a].assign(c->lg.size(), nullptr);
     }
     for (size_t l = 1; l < c->lg.size(); ++l) {
         const LevelGeom &F = c->lg[l - 1], &C = c->lg[l];
@@ -254,6 +257,34 @@ static ibm_status build_levels(Ctx *c) {
             c->tJ[a][l] = dJ;
             c->tw64[a][l] = dw;
             c->tw32[a][l] = dw32;
+            // transpose: the weight of fine i in coarse I[i] is w, in J[i] it
+            // is 1 - w, rounded in each precision as the prolongation rounds it
+            std::vector<int> gi((size_t)4 * nc, -1);
+            std::vector<double> gw((size_t)4 * nc, 0.0);
+            std::vector<float> gw32((size_t)4 * nc, 0.0f);
+            std::vector<int> fill(nc, 0);
+            for (int i = 0; i < nf; ++i) {
+                const int targets[2] = {I[i], J[i]};
+                for (int t = 0; t < 2; ++t) {
+                    const int C2 = targets[t];
+                    if (C2 < 0) continue;
+                    if (fill[C2] >= 4) return c->fail(IBM_ERR_ARG, "transfer table: more than four fine cells per coarse cell");
+                    const size_t q = (size_t)4 * C2 + fill[C2]++;
+                    gi[q] = i;
+                    gw[q] = t == 0 ? w[i] : 1.0 - w[i];
+                    gw32[q] = t == 0 ? w32[i] : 1.0f - w32[i];
+                }
+            }
+            int *dgi = (int *)dev_alloc(c, sizeof(int) * 4 * nc);
+            double *dgw = (double *)dev_alloc(c, sizeof(double) * 4 * nc);
+            float *dgw32 = (float *)dev_alloc(c, sizeof(float) * 4 * nc);
+            if (!dgi || !dgw || !dgw32) return c->fail(IBM_ERR_OOM, "transfer table allocation failed");
+            IBM_CUDA(c, cudaMemcpy(dgi, gi.data(), sizeof(int) * 4 * nc, cudaMemcpyHostToDevice));
+            IBM_CUDA(c, cudaMemcpy(dgw, gw.data(), sizeof(double) * 4 * nc, cudaMemcpyHostToDevice));
+            IBM_CUDA(c, cudaMemcpy(dgw32, gw32.data(), sizeof(float) * 4 * nc, cudaMemcpyHostToDevice));
+            c->gI[a][l] = dgi;
+            c->gw64[a][l] = dgw;
+            c->gw32[a][l] = dgw32;
         }
     }
     return IBM_OK;

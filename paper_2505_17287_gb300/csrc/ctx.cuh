@@ -131,6 +131,11 @@ struct Ctx {
     std::vector<int *> tI[3], tJ[3];
     std::vector<double *> tw64[3];
     std::vector<float *> tw32[3];
+    // the transpose, for restriction: coarse index I gathers from up to four
+    // fine indices gI[4I+s] (-1: none) with weights gw[4I+s]
+    std::vector<int *> gI[3];
+    std::vector<double *> gw64[3];
+    std::vector<float *> gw32[3];
     MGHier<double> mg64;
     MGHier<float> mg32;
 

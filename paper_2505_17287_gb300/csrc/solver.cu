@@ -23,6 +23,8 @@
 // reciprocal diagonals, no division in the inner loops.
 #include "ctx.cuh"
 
+#include <utility>
+
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -275,72 +277,72 @@ __device__ __forceinline__ double vget(const double2 &v, int e) { return e == 0 
 __device__ __forceinline__ void vset(float4 &v, int e, float a) { if (e == 0) v.x = a; else if (e == 1) v.y = a; else if (e == 2) v.z = a; else v.w = a; }
 __device__ __forceinline__ void vset(double2 &v, int e, double a) { if (e == 0) v.x = a; else v.y = a; }
 
-// partial dots: col i < ncols: (w, V_i); col ncols: (w, w). 16-byte loads;
-// the vectors come from cudaMalloc or PyTorch's allocator (256-byte aligned)
+// Krylov basis vectors handed to a kernel by value (kernel parameter space),
+// so the loop loads no pointers from global memory
 template <typename T>
-__global__ void k_mdot(int64_t n, const T *__restrict__ w, const T *const *__restrict__ V, int ncols,
-                       double *__restrict__ part) {
+struct VPtrs {
+    const T *p[17];
+};
+
+// partial dots: col q < NC: (w, V_q); col NC: (w, w). The column count is a
+// template parameter so every loop is unrolled without predicates; 16-byte
+// loads (the vectors come from cudaMalloc or PyTorch's allocator, 256-byte
+// aligned)
+template <typename T, int NC>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__restrict__ w, VPtrs<T> V,
+                                                      double *__restrict__ part) {
     typedef typename Acc<T>::type A;
     typedef typename Vec16<T>::type VT;
     constexpr int W = Vec16<T>::W;
     __shared__ double sh[32];
-    A acc[17];
+    A acc[NC + 1];
 #pragma unroll
-    for (int q = 0; q < 17; ++q) acc[q] = A(0);
-    A ww = A(0);
+    for (int q = 0; q <= NC; ++q) acc[q] = A(0);
     const int64_t nv = n / W;
     GRID_STRIDE(v, nv) {
         const VT a = reinterpret_cast<const VT *>(w)[v];
+        VT b[NC];
 #pragma unroll
-        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+        for (int q = 0; q < NC; ++q) b[q] = reinterpret_cast<const VT *>(V.p[q])[v];
 #pragma unroll
-        for (int q = 0; q < 17; ++q)
-            if (q < ncols) {
-                const VT b = reinterpret_cast<const VT *>(V[q])[v];
+        for (int e = 0; e < W; ++e) acc[NC] += (A)vget(a, e) * (A)vget(a, e);
 #pragma unroll
-                for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b, e);
-            }
+        for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b[q], e);
     }
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const A a = (A)w[c];
-        ww += a * a;
+        acc[NC] += a * a;
 #pragma unroll
-        for (int q = 0; q < 17; ++q)
-            if (q < ncols) acc[q] += a * (A)V[q][c];
+        for (int q = 0; q < NC; ++q) acc[q] += a * (A)V.p[q][c];
     }
 #pragma unroll
-    for (int q = 0; q < 17; ++q) {
-        if (q < ncols) {   // ncols is uniform over the block
-            const double t = block_sum<RED_THREADS>((double)acc[q], sh);
-            if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
-        }
+    for (int q = 0; q <= NC; ++q) {
+        const double t = block_sum<RED_THREADS>((double)acc[q], sh);
+        if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
     }
-    const double t = block_sum<RED_THREADS>((double)ww, sh);
-    if (threadIdx.x == 0) part[(size_t)ncols * gridDim.x + blockIdx.x] = t;
 }
 
-// w -= sum_i h_i V_i ; partial (w, w)
-template <typename T>
-__global__ void k_orth(int64_t n, T *__restrict__ w, const T *const *__restrict__ V, int ncols, Coef h,
-                       double *__restrict__ part) {
+// w -= sum_q h_q V_q ; partial (w, w)
+template <typename T, int NC>
+__global__ void __launch_bounds__(RED_THREADS) k_orth(int64_t n, T *__restrict__ w, VPtrs<T> V, Coef h,
+                                                      double *__restrict__ part) {
     typedef typename Acc<T>::type A;
     typedef typename Vec16<T>::type VT;
     constexpr int W = Vec16<T>::W;
     __shared__ double sh[32];
-    T hv[17];
-#pragma unroll
-    for (int q = 0; q < 17; ++q) hv[q] = (T)h.v[q];
     A ww = A(0);
     const int64_t nv = n / W;
     GRID_STRIDE(v, nv) {
         VT a = reinterpret_cast<const VT *>(w)[v];
+        VT b[NC];
 #pragma unroll
-        for (int q = 0; q < 17; ++q)
-            if (q < ncols) {
-                const VT b = reinterpret_cast<const VT *>(V[q])[v];
+        for (int q = 0; q < NC; ++q) b[q] = reinterpret_cast<const VT *>(V.p[q])[v];
 #pragma unroll
-                for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - hv[q] * vget(b, e));
-            }
+        for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - (T)h.v[q] * vget(b[q], e));
         reinterpret_cast<VT *>(w)[v] = a;
 #pragma unroll
         for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
@@ -348,13 +350,28 @@ __global__ void k_orth(int64_t n, T *__restrict__ w, const T *const *__restrict_
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         T a = w[c];
 #pragma unroll
-        for (int q = 0; q < 17; ++q)
-            if (q < ncols) a -= hv[q] * V[q][c];
+        for (int q = 0; q < NC; ++q) a -= (T)h.v[q] * V.p[q][c];
         w[c] = a;
         ww += (A)a * (A)a;
     }
     const double t = block_sum<RED_THREADS>((double)ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// kernel tables indexed by the column count - 1
+template <typename T>
+using MdotFn = void (*)(int64_t, const T *, VPtrs<T>, double *);
+template <typename T>
+using OrthFn = void (*)(int64_t, T *, VPtrs<T>, Coef, double *);
+template <typename T, int... I>
+static const MdotFn<T> *mdot_table(std::integer_sequence<int, I...>) {
+    static const MdotFn<T> t[] = {&k_mdot<T, I + 1>...};
+    return t;
+}
+template <typename T, int... I>
+static const OrthFn<T> *orth_table(std::integer_sequence<int, I...>) {
+    static const OrthFn<T> t[] = {&k_orth<T, I + 1>...};
+    return t;
 }
 
 template <typename T, typename S>
@@ -616,11 +633,19 @@ __global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx,
 }
 
 // trilinear transfer ----------------------------------------------------------
+//
+// Prolongation P interpolates each fine cell from the (up to) 2x2x2 coarse
+// cells around it with separable linear weights, renormalised over the
+// active coarse cells (pn); restriction is its transpose. Both are applied
+// one axis at a time, which needs a few multiply-adds per fine cell instead
+// of one per (fine cell, coarse cell) pair.
 
 template <typename T>
 struct Xfer {
-    const int *Ix, *Jx, *Iy, *Jy, *Iz, *Jz;
+    const int *Ix, *Jx, *Iy, *Jy, *Iz, *Jz;   // scatter: fine index -> coarse
     const T *wx, *wy, *wz;
+    const int *Gx, *Gy, *Gz;                  // gather: coarse index -> 4 fine
+    const T *gwx, *gwy, *gwz;
 };
 
 // the up-to-two coarse indices and weights of fine index i along one axis
@@ -634,20 +659,6 @@ __device__ __forceinline__ int xfer_axis(const int *I, const int *J, const T *w,
         return 2;
     }
     return 1;
-}
-
-// fine residual r = f - K x on active cells, 0 elsewhere
-template <typename T, bool FINE>
-__global__ void k_resid(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, T *__restrict__ r) {
-    const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= L.nx) return;
-    const int64_t c = row * L.nx + i;
-    if (!active<T, FINE>(L, c)) { r[c] = T(0); return; }
-    T d;
-    const T off = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
-    r[c] = f[c] - (d * x[c] - off);
 }
 
 // pn_c = 1 / (sum of the weights of the active coarse cells of c), 0 if c inactive
@@ -674,53 +685,58 @@ __global__ void k_pnorm(MGLevel<T> L, MGLevel<T> C, Xfer<T> X, T *__restrict__ p
     pn[c] = sum > T(0) ? T(1) / sum : T(0);
 }
 
-// x_c += pn_c * sum over the active coarse cells C of w_cC x_C
+// Restriction, first axis, fused with the fine residual: for one fine row
+// (j, k) and RX_THREADS coarse x-indices I,
+//   tA[I + cnx (j + ny k)] = sum_s gwx[4I+s] * (pn r)(gIx[4I+s], j, k),
+// r = f - K x. The block computes pn r for the fine cells its coarse cells
+// gather from (two more than twice their number when x is coarsened) into
+// shared memory, then each thread sums its four. zcol >= 0 names the colour
+// the smoother relaxed last: the residual of every cell it updated is zero
+// (up to rounding) and is taken as zero without evaluating the stencil.
+constexpr int RX_THREADS = 128;
 template <typename T, bool FINE>
-__global__ void k_prolong_tl(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, Xfer<T> X, const T *__restrict__ pn) {
+__global__ void __launch_bounds__(RX_THREADS)
+    k_resid_rx(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, const T *__restrict__ pn, Xfer<T> X,
+               int cnx, int fx, int zcol, T *__restrict__ tA) {
+    __shared__ T sg[2 * RX_THREADS + 2];
     const int64_t row = blockIdx.x;
     const int j = (int)(row % L.ny), k = (int)(row / L.ny);
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= L.nx) return;
-    const int64_t c = row * L.nx + i;
-    const T p = pn[c];
-    if (!(p > T(0))) return;
-    int ia[2], ib[2], ic[2];
-    T wa[2], wb[2], wc[2];
-    const int na = xfer_axis(X.Ix, X.Jx, X.wx, i, ia, wa);
-    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
-    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
-    T acc = T(0);
-    for (int q3 = 0; q3 < nc; ++q3)
-        for (int q2 = 0; q2 < nb; ++q2)
-            for (int q1 = 0; q1 < na; ++q1) {
-                const int64_t cc = ((int64_t)ic[q3] * C.ny + ib[q2]) * C.nx + ia[q1];
-                if (C.dinv[cc] > T(0)) acc += ((wa[q1] * wb[q2]) * wc[q3]) * C.x[cc];
+    const int I0 = blockIdx.y * RX_THREADS;
+    const int lo = fx == 2 ? 2 * I0 - 1 : I0;
+    const int cnt = fx == 2 ? 2 * RX_THREADS + 2 : RX_THREADS;
+    for (int t = threadIdx.x; t < cnt; t += RX_THREADS) {
+        const int i = lo + t;
+        T g = T(0);
+        if (i >= 0 && i < L.nx) {
+            const int64_t c = row * L.nx + i;
+            const bool relaxed = ((i + j + k) & 1) == zcol && (FINE ? (L.omask[c] & 0x3fu) != 0 : true);
+            const T p = relaxed ? T(0) : pn[c];
+            if (p > T(0)) {
+                T d;
+                const T off = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+                g = p * (f[c] - (d * x[c] - off));
             }
-    x[c] += acc * p;
+        }
+        sg[t] = g;
+    }
+    __syncthreads();
+    const int I = I0 + threadIdx.x;
+    if (I < cnx) {
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = X.Gx[4 * I + s];
+            if (i >= 0 && (unsigned)(i - lo) < (unsigned)cnt) acc += X.gwx[4 * I + s] * sg[i - lo];
+        }
+        tA[row * cnx + I] = acc;
+    }
 }
 
-// the fine cells whose interpolation reaches coarse index I along one axis
+// Restriction, second and third axes: f_C = sum_z gwz sum_y gwy tA (tA has
+// the coarse x extent and the fine y, z extents); x_C = 0, and f_C = 0 on
+// inactive coarse cells.
 template <typename T>
-__device__ __forceinline__ int xfer_gather(const int *I, const int *J, const T *w, int nf, int fac, int Ic, int *idx,
-                                           T *wt) {
-    if (fac == 1) {
-        idx[0] = Ic;
-        wt[0] = T(1);
-        return 1;
-    }
-    int n = 0;
-    for (int i = 2 * Ic - 1; i <= 2 * Ic + 2; ++i) {
-        if (i < 0 || i >= nf) continue;
-        if (I[i] == Ic) { idx[n] = i; wt[n] = w[i]; ++n; }
-        else if (J[i] == Ic) { idx[n] = i; wt[n] = T(1) - w[i]; ++n; }
-    }
-    return n;
-}
-
-// restriction by the transpose of the prolongation: f_C = sum_c w_cC pn_c r_c
-template <typename T>
-__global__ void k_restrict_tl(MGLevel<T> L, const T *__restrict__ r, const T *__restrict__ pn, MGLevel<T> C,
-                              Xfer<T> X, int fx, int fy, int fz) {
+__global__ void k_restrict_yz(MGLevel<T> C, const T *__restrict__ tA, int fny, Xfer<T> X) {
     const int64_t row = blockIdx.x;
     const int Jc = (int)(row % C.ny), Kc = (int)(row / C.ny);
     const int Ic = blockIdx.y * blockDim.x + threadIdx.x;
@@ -728,20 +744,62 @@ __global__ void k_restrict_tl(MGLevel<T> L, const T *__restrict__ r, const T *__
     const int64_t cc = row * C.nx + Ic;
     C.x[cc] = T(0);
     if (!(C.dinv[cc] > T(0))) { C.f[cc] = T(0); return; }
-    int ia[4], ib[4], ic[4];
-    T wa[4], wb[4], wc[4];
-    const int na = xfer_gather(X.Ix, X.Jx, X.wx, L.nx, fx, Ic, ia, wa);
-    const int nb = xfer_gather(X.Iy, X.Jy, X.wy, L.ny, fy, Jc, ib, wb);
-    const int nc = xfer_gather(X.Iz, X.Jz, X.wz, L.nz, fz, Kc, ic, wc);
     T acc = T(0);
-    for (int q3 = 0; q3 < nc; ++q3)
-        for (int q2 = 0; q2 < nb; ++q2)
-            for (int q1 = 0; q1 < na; ++q1) {
-                const int64_t f = ((int64_t)ic[q3] * L.ny + ib[q2]) * L.nx + ia[q1];
-                const T p = pn[f];
-                if (p > T(0)) acc += ((wa[q1] * wb[q2]) * wc[q3]) * (p * r[f]);
-            }
+#pragma unroll
+    for (int s3 = 0; s3 < 4; ++s3) {
+        const int k = X.Gz[4 * Kc + s3];
+        if (k < 0) continue;
+        T a2 = T(0);
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+            const int j = X.Gy[4 * Jc + s2];
+            if (j >= 0) a2 += X.gwy[4 * Jc + s2] * tA[((int64_t)k * fny + j) * C.nx + Ic];
+        }
+        acc += X.gwz[4 * Kc + s3] * a2;
+    }
     C.f[cc] = acc;
+}
+
+// Prolongation, first axis: tB[i + fnx (J + cny K)] = the x-interpolation of
+// coarse row (J, K) at fine index i. Coarse x is zero on inactive coarse
+// cells (restriction clears it, smoothing and the coarse solve write only
+// active cells), so no mask is needed here.
+template <typename T>
+__global__ void k_prolong_x(int fnx, MGLevel<T> C, Xfer<T> X, T *__restrict__ tB) {
+    const int64_t row = blockIdx.x;
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= fnx) return;
+    const T *xr = C.x + row * C.nx;
+    const int J2 = X.Jx[i];
+    const T w = X.wx[i];
+    T v = w * xr[X.Ix[i]];
+    if (J2 >= 0) v += (T(1) - w) * xr[J2];
+    tB[row * fnx + i] = v;
+}
+
+// Prolongation, second and third axes, and the correction:
+// x_c += pn_c * sum_z wz sum_y wy tB on fine cells with pn_c > 0
+template <typename T>
+__global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restrict__ tB, int cny, Xfer<T> X,
+                             const T *__restrict__ pn) {
+    const int64_t row = blockIdx.x;
+    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    const T p = pn[c];
+    if (!(p > T(0))) return;
+    int ib[2], ic[2];
+    T wb[2], wc[2];
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
+    T acc = T(0);
+    for (int q3 = 0; q3 < nc; ++q3) {
+        T a2 = T(0);
+        for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * tB[((int64_t)ic[q3] * cny + ib[q2]) * L.nx + i];
+        acc += wc[q3] * a2;
+    }
+    x[c] += acc * p;
 }
 
 // coarsest level: red-black sweeps in one block, all data in shared memory.
@@ -1055,13 +1113,15 @@ template <typename T>
 static Xfer<T> xfer_of(Ctx *c, int l);
 template <>
 Xfer<double> xfer_of<double>(Ctx *c, int l) {
-    return Xfer<double>{c->tI[0][l], c->tJ[0][l], c->tI[1][l], c->tJ[1][l], c->tI[2][l], c->tJ[2][l],
-                        c->tw64[0][l], c->tw64[1][l], c->tw64[2][l]};
+    return Xfer<double>{c->tI[0][l],   c->tJ[0][l],   c->tI[1][l],   c->tJ[1][l],   c->tI[2][l],
+                        c->tJ[2][l],   c->tw64[0][l], c->tw64[1][l], c->tw64[2][l], c->gI[0][l],
+                        c->gI[1][l],   c->gI[2][l],   c->gw64[0][l], c->gw64[1][l], c->gw64[2][l]};
 }
 template <>
 Xfer<float> xfer_of<float>(Ctx *c, int l) {
-    return Xfer<float>{c->tI[0][l], c->tJ[0][l], c->tI[1][l], c->tJ[1][l], c->tI[2][l], c->tJ[2][l],
-                       c->tw32[0][l], c->tw32[1][l], c->tw32[2][l]};
+    return Xfer<float>{c->tI[0][l],   c->tJ[0][l],   c->tI[1][l],   c->tJ[1][l],   c->tI[2][l],
+                       c->tJ[2][l],   c->tw32[0][l], c->tw32[1][l], c->tw32[2][l], c->gI[0][l],
+                       c->gI[1][l],   c->gI[2][l],   c->gw32[0][l], c->gw32[1][l], c->gw32[2][l]};
 }
 
 template <typename T>
@@ -1274,12 +1334,18 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         auto &CG = c->lg[l + 1];
         const dim3 grid = rows_grid(Cl.nx, Cl.ny, Cl.nz, 1, bx);
         if (c->opts.mg_interp == 1) {
-            // fine residual, then restriction by the transpose of the trilinear prolongation
-            T *r = l == 0 ? H.pq : H.res[l];
-            const dim3 fgrid = rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx);
-            if (l == 0 && H.fine0) KL(K_RESTRICT, (k_resid<T, true>), fgrid, bx, Lf, f, x, r);
-            else KL(K_RESTRICT, (k_resid<T, false>), fgrid, bx, Lf, f, x, r);
-            KL(K_RESTRICT, k_restrict_tl<T>, grid, bx, Lf, r, H.pn[l], Cl, xfer_of<T>(c, l + 1), CG.fx, CG.fy, CG.fz);
+            // fine residual and restriction along x, then along y and z
+            // (transpose of the trilinear prolongation)
+            T *tA = l == 0 ? H.pq : H.res[l];
+            const Xfer<T> X = xfer_of<T>(c, l + 1);
+            const dim3 rgrid((unsigned)((int64_t)Lf.ny * Lf.nz), (unsigned)((Cl.nx + RX_THREADS - 1) / RX_THREADS));
+            const int zcol = nu1 > 0 ? 1 : -1;   // each pre-smoothing sweep ends with colour 1
+            if (l == 0 && H.fine0)
+                KL(K_RESTRICT, (k_resid_rx<T, true>), rgrid, RX_THREADS, Lf, f, x, H.pn[l], X, Cl.nx, CG.fx, zcol, tA);
+            else
+                KL(K_RESTRICT, (k_resid_rx<T, false>), rgrid, RX_THREADS, Lf, f, x, H.pn[l], X, Cl.nx, CG.fx, zcol,
+                   tA);
+            KL(K_RESTRICT, k_restrict_yz<T>, grid, bx, Cl, tA, Lf.ny, X);
         } else if (l == 0 && H.fine0) {
             KL(K_RESTRICT, (k_resid_restrict<T, true>), grid, bx, Lf, f, x, Cl, CG.fx, CG.fy, CG.fz);
         } else {
@@ -1296,10 +1362,11 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         auto &CG = c->lg[l + 1];
         const dim3 grid = rows_grid(Lf.nx, Lf.ny, Lf.nz, 1, bx);
         if (c->opts.mg_interp == 1) {
-            if (l == 0 && H.fine0)
-                KL(K_PROLONG, (k_prolong_tl<T, true>), grid, bx, Lf, x, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
-            else
-                KL(K_PROLONG, (k_prolong_tl<T, false>), grid, bx, Lf, x, H.lv[l + 1], xfer_of<T>(c, l + 1), H.pn[l]);
+            MGLevel<T> &Cl = H.lv[l + 1];
+            T *tB = l == 0 ? H.pq : H.res[l];
+            const Xfer<T> X = xfer_of<T>(c, l + 1);
+            KL(K_PROLONG, k_prolong_x<T>, rows_grid(Lf.nx, Cl.ny, Cl.nz, 1, bx), bx, Lf.nx, Cl, X, tB);
+            KL(K_PROLONG, k_prolong_yz<T>, grid, bx, Lf, x, tB, Cl.ny, X, H.pn[l]);
         } else if (l == 0 && H.fine0) {
             KL(K_PROLONG, (k_prolong<T, true>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
         } else {
@@ -1435,16 +1502,20 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
             // classical Gram-Schmidt, with a second pass when the norm drops
             // by more than a factor 0.7 (Daniel, Gragg, Kaufman, Stewart 1976)
+            VPtrs<T> vp{};
+            for (int i = 0; i <= j; ++i) vp.p[i] = K.V[i];
             double hcol[17] = {0};
             double wbefore2 = 0.0, wafter2 = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                KL(K_MDOT, k_mdot<T>, RED_BLOCKS, RED_THREADS, n, K.w, (const T *const *)K.Vdev, j + 1, c->part);
+                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], RED_BLOCKS, RED_THREADS, n,
+                   K.w, vp, c->part);
                 IBM_TRY(finalize(c, c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD));
                 IBM_TRY(sync_scalars(c, S_MD + j + 2));
                 Coef h{};
                 for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
                 wbefore2 = c->hscal[S_MD + j + 1];
-                KL(K_ORTH, k_orth<T>, RED_BLOCKS, RED_THREADS, n, K.w, (const T *const *)K.Vdev, j + 1, h, c->part);
+                KL(K_ORTH, orth_table<T>(std::make_integer_sequence<int, 17>())[j], RED_BLOCKS, RED_THREADS, n,
+                   K.w, vp, h, c->part);
                 IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
                 IBM_TRY(sync_scalars(c, S_TMP + 1));
                 wafter2 = c->hscal[S_TMP];
