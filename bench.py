@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-kernels", action="store_true", help="also report every timed kernel")
     ap.add_argument("--no-ktimer", action="store_true", help="skip the per-kernel timing pass")
+    ap.add_argument("--serve", type=int, default=40,
+                    help="requests of the 3D multi-sphere serving stream to replay (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="cases resident at once in the serving leg")
+    ap.add_argument("--serve-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the main timed run (the mixed run beside it is --no-mixed's)")
     return ap.parse_args()
@@ -191,6 +195,45 @@ def cpu_baseline_sample():
     return {"value": g.N * 2 / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "plain FP64 oracle (sparse direct solves), wing case on a 32x24x24 grid (18,432 cells), "
                       "one run of 2 fractional steps including the matrix factorisations"}
+
+
+def serve_leg(nreq, slots, precision):
+    """Replay the first nreq requests of the seeded 3D multi-sphere stream
+    (Poisson arrivals at 50/s, 1-8 icospheres of 5120 triangles, n^3 grids
+    with n in [64, 256], 10 steps each) against the request loop in real
+    time; latency = completion - arrival."""
+    import numpy as np
+    from paper_2505_17287_gb300 import ibm, synth
+    times, cases = synth.serve_stream(nreq)
+    srv = ibm.Server(max_slots=slots)
+    t0 = time.perf_counter()
+    ids = []
+    for t, c in zip(times, cases):
+        d = t - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        ids.append(srv.submit(c, precision=precision))
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    ok = [r for r in res if r["status"] == ibm.IBM_OK]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1e3
+    svc = np.array([r["t_done"] - r["t_admit"] for r in ok]) * 1e3
+    first = min(r["t_submit"] for r in res)
+    last = max(r["t_done"] for r in res)
+    work = sum(r["cells"] * r["steps"] for r in ok)
+    return {"requests": nreq, "completed_ok": len(ok), "arrival_rate_per_s": 50.0, "slots": slots,
+            "precision": "mixed" if precision == ibm.IBM_MIXED else "fp64",
+            "p50_ms": float(np.percentile(lat, 50)) if len(ok) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(ok) else None,
+            "service_p50_ms": float(np.percentile(svc, 50)) if len(ok) else None,
+            "value": work / (last - first) / 1e6, "unit": UNIT,
+            "completed_per_s": len(ok) / (last - first), "makespan_s": last - first,
+            "cells_total": int(sum(r["cells"] for r in ok)), "peak_running": st["peak_running"],
+            "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9,
+            "workload": "seeded stream: Poisson arrivals 50/s; 1-8 icospheres (5120 triangles each, radii "
+                        "0.2-0.6) in [-4,8]x[-3,3]^2; n^3 grids, log n uniform in [log 64, log 256], n a "
+                        "multiple of 16; Re 100-500; CFL 0.2; 10 steps per request; Poisson rtol 1e-10"}
 
 
 def main():
@@ -346,6 +389,11 @@ def main():
         except Exception as e:  # the oracle is optional on a box without it
             result["cpu_baseline"] = {"value": None, "error": str(e)}
     s.close()
+    if rank == 0 and args.serve > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        result["serve"] = serve_leg(args.serve, args.serve_slots,
+                                    ibm.IBM_MIXED if args.serve_precision == "mixed" else ibm.IBM_FP64)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -27,6 +27,7 @@ SOURCES = {
     "solver.cu": [],
     "flow.cu": [],
     "noalloc.cu": [],
+    "serve.cu": [],
 }
 COMMON = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
@@ -43,6 +44,7 @@ def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(ROOT, "include", "ibm.h"))
+    headers.append(os.path.join(ROOT, "include", "ibm_serve.h"))
 
     def one(name):
         src = os.path.join(CSRC, name)

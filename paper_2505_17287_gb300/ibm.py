@@ -69,7 +69,36 @@ class ibm_tables_host(Structure):
                                         "sidx", "wv", "wp", "bv", "bp")]
 
 
-EXPORTS = ["ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
+IBM_REQ_STEP, IBM_REQ_POISSON = 0, 1
+
+
+class ibm_server_opts(Structure):
+    _fields_ = [("max_slots", c_int), ("device", c_int), ("hbm_reserve", c_size_t), ("hbm_budget", c_size_t)]
+
+
+class ibm_request(Structure):
+    _fields_ = [("kind", c_int), ("grid", ibm_grid_desc), ("opts", c_void_p), ("nbodies", c_int),
+                ("verts", c_void_p), ("nverts", c_void_p), ("elems", c_void_p), ("nelems", c_void_p),
+                ("nsteps", c_int), ("rhs", c_void_p), ("rtol", c_double), ("maxit", c_int),
+                ("out_u", c_void_p), ("out_v", c_void_p), ("out_w", c_void_p), ("out_p", c_void_p)]
+
+
+class ibm_result(Structure):
+    _fields_ = [("status", c_int), ("cells", c_int64), ("steps", c_int), ("t_submit", c_double),
+                ("t_admit", c_double), ("t_done", c_double), ("bytes_estimate", c_size_t),
+                ("bytes_peak", c_size_t), ("step", ibm_step_stats), ("solve", ibm_solve_stats), ("slot", c_int),
+                ("error", ctypes.c_char * 160)]
+
+
+class ibm_server_stats(Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("queued", c_int64),
+                ("running", c_int64), ("peak_running", c_int), ("budget", c_size_t), ("admitted_bytes", c_size_t),
+                ("peak_admitted_bytes", c_size_t)]
+
+
+EXPORTS = ["ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
+           "ibm_server_destroy",
+           "ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
            "ibm_kernel_timer", "ibm_kernel_time", "ibm_launch_count", "ibm_poisson_residual_noalloc",
            "ibm_destroy", "ibm_last_error"]
@@ -105,9 +134,16 @@ def load_library(path: str = LIB_PATH):
     L.ibm_destroy.argtypes = [P]
     L.ibm_last_error.argtypes = [P]
     L.ibm_last_error.restype = c_char_p
+    L.ibm_case_bytes.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int64]
+    L.ibm_server_create.argtypes = [POINTER(ibm_server_opts), POINTER(c_void_p)]
+    L.ibm_server_submit.argtypes = [P, POINTER(ibm_request), POINTER(c_int64)]
+    L.ibm_server_wait.argtypes = [P, c_int64, c_double, POINTER(ibm_result)]
+    L.ibm_server_get_stats.argtypes = [P, POINTER(ibm_server_stats)]
+    L.ibm_server_destroy.argtypes = [P]
     for name in EXPORTS:
         if name != "ibm_last_error":
             getattr(L, name).restype = c_int
+    L.ibm_case_bytes.restype = c_size_t
     _lib = L
     return L
 
@@ -372,3 +408,115 @@ class Solver:
     def set_state(self, st):
         for k in self.state_names():
             self.set(k, st[k])
+
+
+# --------------------------------------------------------------------------
+# request loop over many cases (include/ibm_serve.h)
+# --------------------------------------------------------------------------
+
+def ibm_case_bytes(ndim, nx, ny, nz, precision, nelems_total):
+    return int(load_library().ibm_case_bytes(ndim, nx, ny, nz, precision, nelems_total))
+
+
+def _status_check(status, what):
+    if status != IBM_OK:
+        raise IBMError(status, what)
+    return status
+
+
+class Server:
+    """ibm_server: `max_slots` cases resident and advancing at once on their
+    own streams, admitted first-in first-out by free device memory."""
+
+    def __init__(self, max_slots=4, device=0, hbm_reserve=2 << 30, hbm_budget=0):
+        load_library()
+        o = ibm_server_opts(max_slots, device, hbm_reserve, hbm_budget)
+        h = c_void_p()
+        _status_check(load_library().ibm_server_create(byref(o), byref(h)), "ibm_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, case, kind=IBM_REQ_STEP, nsteps=None, precision=IBM_FP64, opts=None, outputs=False,
+               rhs=None, rtol=0.0, maxit=0, bc=(0, 1, 2, 2, 2, 2)):
+        """Queue one case (a synth.Case; every body of synth.case_bodies(case)).
+        outputs=True returns u, v, w, p (STEP) or phi (POISSON) from wait()."""
+        from . import synth
+        nx, ny = len(case.xf) - 1, len(case.yf) - 1
+        nz = len(case.zf) - 1 if case.ndim == 3 else 1
+        N = nx * ny * nz
+        keep = {}
+        xf = keep["xf"] = np.ascontiguousarray(case.xf, dtype=np.float64)
+        yf = keep["yf"] = np.ascontiguousarray(case.yf, dtype=np.float64)
+        zf = keep["zf"] = np.ascontiguousarray(case.zf if case.ndim == 3 else [0.0, 1.0], dtype=np.float64)
+        r = ibm_request()
+        r.kind = kind
+        g = r.grid
+        g.ndim, g.nx, g.ny, g.nz = case.ndim, nx, ny, nz
+        g.xf, g.yf, g.zf = _p(xf), _p(yf), _p(zf)
+        g.Re, g.dt = float(case.Re), float(case.dt)
+        g.u_inf = (c_double * 3)(*[float(x) for x in case.u_inf])
+        g.bc = (c_int * 6)(*bc)
+        g.precision = precision
+        if opts is not None:
+            keep["opts"] = opts
+            r.opts = ctypes.cast(ctypes.pointer(opts), c_void_p)
+        bodies = synth.case_bodies(case)
+        vs = [np.ascontiguousarray(np.c_[v, np.zeros(len(v))] if v.shape[1] == 2 else v, dtype=np.float64)
+              for v, _ in bodies]
+        es = [np.ascontiguousarray(e, dtype=np.int32) for _, e in bodies]
+        vp = (c_void_p * len(vs))(*[v.ctypes.data for v in vs])
+        ep = (c_void_p * len(es))(*[e.ctypes.data for e in es])
+        nv = np.array([len(v) for v in vs], np.int64)
+        ne = np.array([len(e) for e in es], np.int64)
+        keep.update(vs=vs, es=es, vp=vp, ep=ep, nv=nv, ne=ne)
+        r.nbodies = len(vs)
+        r.verts, r.elems = ctypes.cast(vp, c_void_p), ctypes.cast(ep, c_void_p)
+        r.nverts, r.nelems = _p(nv), _p(ne)
+        r.nsteps = int(nsteps if nsteps is not None else case.nsteps)
+        if kind == IBM_REQ_POISSON:
+            b = keep["rhs"] = np.ascontiguousarray(rhs, dtype=np.float64).reshape(-1)
+            assert b.size == N
+            r.rhs = _p(b)
+            r.rtol, r.maxit = float(rtol), int(maxit)
+        outs = {}
+        if outputs:
+            names = (("u", "v", "w", "p") if case.ndim == 3 else ("u", "v", "p")) if kind == IBM_REQ_STEP else ("p",)
+            for n in names:
+                outs[n] = np.zeros((nz, ny, nx), np.float64)
+                setattr(r, "out_" + n, _p(outs[n]))
+        rid = c_int64()
+        _status_check(load_library().ibm_server_submit(self.h, byref(r), byref(rid)), "ibm_server_submit")
+        self._keep[rid.value] = (keep, outs)
+        return rid.value
+
+    def wait(self, rid, timeout=-1.0):
+        """Result dict of request rid, or None if it is not done within timeout."""
+        res = ibm_result()
+        st = load_library().ibm_server_wait(self.h, rid, float(timeout), byref(res))
+        if st == IBM_ERR_TIMEOUT:
+            return None
+        _status_check(st, "ibm_server_wait")
+        _, outs = self._keep.pop(rid)
+        out = {k: getattr(res, k) for k, _ in ibm_result._fields_ if k not in ("step", "solve", "error")}
+        out["error"] = res.error.decode(errors="replace")
+        out["step"] = {k: getattr(res.step, k) for k, _ in ibm_step_stats._fields_}
+        out["solve"] = {k: getattr(res.solve, k) for k, _ in ibm_solve_stats._fields_}
+        out["latency_s"] = res.t_done - res.t_submit
+        out["outputs"] = outs
+        return out
+
+    def stats(self):
+        s = ibm_server_stats()
+        _status_check(load_library().ibm_server_get_stats(self.h, byref(s)), "ibm_server_get_stats")
+        return {k: getattr(s, k) for k, _ in ibm_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().ibm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

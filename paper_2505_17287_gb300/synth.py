@@ -349,6 +349,66 @@ def ensemble_2d(ncases: int = 64, seed: int = 250517287):
     return out
 
 
+_UNIT_SPHERES = {}
+
+
+def _unit_icosphere(level: int):
+    if level not in _UNIT_SPHERES:
+        _UNIT_SPHERES[level] = icosphere(level, 1.0)
+    return _UNIT_SPHERES[level]
+
+
+def multi_sphere_case(n: int, spheres, Re: float, nsteps: int = 10, level: int = 4,
+                      lo=(-4.0, -3.0, -3.0), hi=(8.0, 3.0, 3.0)) -> Case:
+    """Uniform n^3 grid on the box [lo, hi] with one icosphere body
+    (20*4**level triangles) per (radius, centre) in `spheres`; dt from a CFL
+    number of 0.2 at unit inflow velocity."""
+    V1, T1 = _unit_icosphere(level)
+    bodies = [(V1 * r + np.asarray(c, dtype=np.float64), T1.copy()) for r, c in spheres]
+    xf, yf, zf = (uniform_faces(lo[a], hi[a], n) for a in range(3))
+    h = min(np.diff(xf).min(), np.diff(yf).min(), np.diff(zf).min())
+    return Case(f"spheres{len(bodies)}_n{n}", 3, xf, yf, zf, bodies[0][0], bodies[0][1], Re, 0.2 * h, nsteps,
+                meta={"bodies": bodies, "n": n, "spheres": [(float(r), tuple(map(float, c))) for r, c in spheres]})
+
+
+def case_bodies(case: Case):
+    """The (verts, elems) of every body of a case."""
+    return case.meta.get("bodies") or [(case.verts, case.elems)]
+
+
+def serve_stream(nreq: int = 500, seed: int = 250517288, rate: float = 50.0, nmin: int = 64, nmax: int = 256,
+                 nsteps: int = 10, level: int = 4):
+    """Seeded request stream of 3D multi-body cases: arrivals form a Poisson
+    process of `rate` requests per second; each request has 1 to 8
+    icospheres (5120 triangles each at level 4) with radii in [0.2, 0.6] and
+    centres uniform in the inner half [-1, 5] x [-1.5, 1.5]^2 of the domain
+    [-4, 8] x [-3, 3]^2, kept at least two cell widths apart by rejection; an
+    n^3 grid with log n uniform in [log nmin, log nmax], n rounded down to a
+    multiple of 16; Re uniform in [100, 500]; `nsteps` steps per request.
+    Returns (arrival times in seconds, cases)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    times, cases = [], []
+    for _ in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax)))) // 16 * 16
+        n = max(n, nmin)
+        h = 12.0 / n
+        k = int(rng.integers(1, 9))
+        spheres = []
+        tries = 0
+        while len(spheres) < k and tries < 10000:
+            tries += 1
+            r = rng.uniform(0.2, 0.6)
+            c = rng.uniform((-1.0, -1.5, -1.5), (5.0, 1.5, 1.5))
+            if all(np.linalg.norm(c - np.asarray(c2)) >= r + r2 + 2.0 * h for r2, c2 in spheres):
+                spheres.append((r, c))
+        Re = rng.uniform(100.0, 500.0)
+        times.append(t)
+        cases.append(multi_sphere_case(n, spheres, Re, nsteps, level))
+    return np.asarray(times), cases
+
+
 def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=shape)

@@ -11,10 +11,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ibm.h")
+SERVE_HEADER = os.path.join(ROOT, "include", "ibm_serve.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def _declared():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(ibm_[a-z_]+)\s*\(", src)))
 
@@ -44,8 +47,10 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_2505_17287_gb300 import ibm
     structs = {"ibm_grid_desc": ibm.ibm_grid_desc, "ibm_solver_opts": ibm.ibm_solver_opts,
                "ibm_table_info": ibm.ibm_table_info, "ibm_solve_stats": ibm.ibm_solve_stats,
-               "ibm_step_stats": ibm.ibm_step_stats, "ibm_tables_host": ibm.ibm_tables_host}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+               "ibm_step_stats": ibm.ibm_step_stats, "ibm_tables_host": ibm.ibm_tables_host,
+               "ibm_server_opts": ibm.ibm_server_opts, "ibm_request": ibm.ibm_request,
+               "ibm_result": ibm.ibm_result, "ibm_server_stats": ibm.ibm_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{SERVE_HEADER}"', "int main(void){"]
     for s, cls in structs.items():
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
         for f, _ in cls._fields_:
@@ -75,3 +80,18 @@ def test_create_rejects_bad_descriptor_without_gpu(lib):
     o = ibm.ibm_solver_opts()
     assert lib.ibm_default_opts(ctypes.byref(o)) == ibm.IBM_OK
     assert o.rtol == 1e-10 and o.restart == 16 and o.outer == ibm.IBM_OUTER_FGMRES
+
+
+def test_server_argument_checks_without_gpu(lib):
+    from paper_2505_17287_gb300 import ibm
+    o = ibm.ibm_server_opts(0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.ibm_server_create(ctypes.byref(o), ctypes.byref(h)) == ibm.IBM_ERR_ARG
+    assert h.value is None
+    assert lib.ibm_server_destroy(None) == ibm.IBM_OK
+    # footprint estimate: grows with the grid, mixed below FP64, body storage counted
+    b64 = ibm.ibm_case_bytes(3, 128, 128, 128, ibm.IBM_FP64, 5120)
+    b32 = ibm.ibm_case_bytes(3, 128, 128, 128, ibm.IBM_MIXED, 5120)
+    assert b32 < b64 < ibm.ibm_case_bytes(3, 256, 128, 128, ibm.IBM_FP64, 5120)
+    assert ibm.ibm_case_bytes(3, 128, 128, 128, ibm.IBM_FP64, 50000) > b64
+    assert 300 * 128 ** 3 < b64 < 2000 * 128 ** 3
