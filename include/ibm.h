@@ -105,6 +105,14 @@ typedef struct {
                            FP32 Krylov solve inside the FP64 defect correction */
     int mg_interp;      /* multigrid transfer: 1 trilinear prolongation with its transpose
                            as restriction, 0 piecewise constant with summation */
+    int tile_x;         /* threads per block along x of the multigrid smoother and
+                           transfer kernels (one block per grid row segment):
+                           32, 64, 128, 256 or 512 */
+    int graph;          /* 1: the multigrid V-cycle is captured once into a CUDA graph
+                           and replayed at every preconditioner call (one launch
+                           instead of ~10 per level; not on the legacy default
+                           stream, which cannot be captured, nor while the kernel
+                           timer runs); 0: launched kernel by kernel */
 } ibm_solver_opts;
 
 typedef struct {
@@ -160,7 +168,8 @@ enum {
 /* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
-   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1. */
+   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
+   tile_x 128, graph 1. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

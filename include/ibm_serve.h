@@ -120,6 +120,20 @@ ibm_status ibm_server_get_stats(ibm_server *srv, ibm_server_stats *out);
    join the workers and release every device resource. */
 ibm_status ibm_server_destroy(ibm_server *srv);
 
+/* Autotuner (no counterpart in the paper): builds the case (desc, bodies,
+   on desc's stream and allocator), then for each of the ncand option sets
+   restores the same impulsive-start state, takes one untimed step (which
+   also captures any CUDA graph the options ask for), restores the state
+   again and times `steps` fractional steps with CUDA events on the stream.
+   ms_per_step[i] (host, ncand values) receives candidate i's device time
+   per step, or a negative value if it failed (IBM_ERR_ARG options,
+   non-convergence); *best the index of the fastest. IBM_ERR_ARG for bad
+   arguments, IBM_ERR_NOT_CONVERGED if no candidate succeeded; errors in
+   building the case are returned as they come. */
+ibm_status ibm_tune(const ibm_grid_desc *desc, int nbodies, const double *const *verts, const int64_t *nverts,
+                    const int32_t *const *elems, const int64_t *nelems, const ibm_solver_opts *cand, int ncand,
+                    int steps, int *best, double *ms_per_step);
+
 #ifdef __cplusplus
 }
 #endif

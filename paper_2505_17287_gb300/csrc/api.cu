@@ -73,6 +73,8 @@ ibm_status kt_flush(Ctx *c) {
 
 static void release_all(Ctx *c) {
     if (c->s) cudaStreamSynchronize(c->s);
+    if (c->mg64.vgraph) cudaGraphExecDestroy(c->mg64.vgraph);
+    if (c->mg32.vgraph) cudaGraphExecDestroy(c->mg32.vgraph);
     std::vector<void *> a = c->allocs;
     for (void *p : a) dev_free(c, p);
     if (c->hscal) cudaFreeHost(c->hscal);
@@ -101,6 +103,8 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->band_omega = 0.7;
     o->mixed_inner_rtol = 1e-4;
     o->mg_interp = 1;
+    o->tile_x = 128;
+    o->graph = 1;
     return IBM_OK;
 }
 
@@ -119,6 +123,11 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (!(o->band_omega > 0.0 && o->band_omega <= 1.0)) { why = "band_omega must be in (0, 1]"; return false; }
     if (!(o->mixed_inner_rtol > 0.0 && o->mixed_inner_rtol < 1.0)) { why = "mixed_inner_rtol must be in (0, 1)"; return false; }
     if (o->mg_interp != 0 && o->mg_interp != 1) { why = "mg_interp must be 0 or 1"; return false; }
+    if (o->tile_x != 32 && o->tile_x != 64 && o->tile_x != 128 && o->tile_x != 256 && o->tile_x != 512) {
+        why = "tile_x must be 32, 64, 128, 256 or 512";
+        return false;
+    }
+    if (o->graph != 0 && o->graph != 1) { why = "graph must be 0 or 1"; return false; }
     return true;
 }
 

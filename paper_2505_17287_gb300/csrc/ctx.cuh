@@ -18,6 +18,11 @@ struct MGHier {
     // coarse interpolation weights of each cell (trilinear transfer)
     std::vector<T *> res, pn;
     bool built = false;
+    // the V-cycle z = M^{-1} r on (pr -> pz) captured as a CUDA graph, with
+    // the settings it was captured for and its kernel count
+    cudaGraphExec_t vgraph = nullptr;
+    uint64_t vgraph_key = 0;
+    int64_t vgraph_kernels = 0;
 };
 
 // 1D coordinates of one multigrid level (host) and the axis coarsening flags
@@ -141,6 +146,7 @@ struct Ctx {
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
     int64_t nlaunch = 0;   // kernels launched by this context so far
+    uint64_t mg_gen = 0;   // multigrid rebuild counter (invalidates captured V-cycles)
 
     ibm_status fail(ibm_status code, const std::string &m) {
         err.code = code;

@@ -456,3 +456,79 @@ extern "C" ibm_status ibm_server_destroy(ibm_server *s) {
     delete s;
     return IBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+
+extern "C" ibm_status ibm_tune(const ibm_grid_desc *desc, int nbodies, const double *const *verts,
+                               const int64_t *nverts, const int32_t *const *elems, const int64_t *nelems,
+                               const ibm_solver_opts *cand, int ncand, int steps, int *best, double *ms_per_step) {
+    if (!desc || nbodies < 1 || !verts || !nverts || !elems || !nelems || !cand || ncand < 1 || steps < 1 || !best ||
+        !ms_per_step)
+        return IBM_ERR_ARG;
+    ibm_ctx *ctx = nullptr;
+    ibm_status st = ibm_create_grid(desc, &ctx);
+    if (st != IBM_OK) return st;
+    const int nz = desc->ndim == 3 ? desc->nz : 1;
+    const int64_t N = (int64_t)desc->nx * desc->ny * nz;
+    // state fields and their sizes (doubles; the step counter is one int64)
+    std::vector<std::pair<int, size_t>> fields = {{IBM_FIELD_U, N}, {IBM_FIELD_V, N}, {IBM_FIELD_P, N},
+                                                  {IBM_FIELD_FACE_U, (size_t)(desc->nx + 1) * desc->ny * nz},
+                                                  {IBM_FIELD_FACE_V, (size_t)desc->nx * (desc->ny + 1) * nz},
+                                                  {IBM_FIELD_NOLD_U, N}, {IBM_FIELD_NOLD_V, N}};
+    if (desc->ndim == 3) {
+        fields.push_back({IBM_FIELD_W, N});
+        fields.push_back({IBM_FIELD_FACE_W, (size_t)desc->nx * desc->ny * (nz + 1)});
+        fields.push_back({IBM_FIELD_NOLD_W, N});
+    }
+    std::vector<std::vector<double>> saved(fields.size());
+    cudaStream_t s = (cudaStream_t)desc->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    do {
+        for (int b = 0; b < nbodies && st == IBM_OK; ++b) st = ibm_set_body(ctx, verts[b], nverts[b], elems[b], nelems[b]);
+        if (st != IBM_OK || (st = ibm_classify_cells(ctx, nullptr)) != IBM_OK) break;
+        for (size_t f = 0; f < fields.size() && st == IBM_OK; ++f) {
+            saved[f].resize(fields[f].second);
+            st = ibm_get_field(ctx, fields[f].first, saved[f].data(), 0, sizeof(double) * fields[f].second);
+        }
+        if (st != IBM_OK) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            st = IBM_ERR_CUDA;
+            break;
+        }
+        auto restore = [&]() {
+            ibm_status r = IBM_OK;
+            for (size_t f = 0; f < fields.size() && r == IBM_OK; ++f)
+                r = ibm_set_field(ctx, fields[f].first, saved[f].data(), 0, sizeof(double) * fields[f].second);
+            const int64_t zero = 0;
+            if (r == IBM_OK) r = ibm_set_field(ctx, IBM_FIELD_STEP, &zero, 0, sizeof(int64_t));
+            return r;
+        };
+        int bi = -1;
+        for (int i = 0; i < ncand; ++i) {
+            ms_per_step[i] = -1.0;
+            if (ibm_set_opts(ctx, &cand[i]) != IBM_OK) continue;
+            if (restore() != IBM_OK || ibm_step(ctx, 1, nullptr) != IBM_OK) continue;
+            if (restore() != IBM_OK) continue;
+            if (cudaEventRecord(e0, s) != cudaSuccess) break;
+            const ibm_status r = ibm_step(ctx, steps, nullptr);
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            if (r != IBM_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+            ms_per_step[i] = ms / steps;
+            if (bi < 0 || ms_per_step[i] < ms_per_step[bi]) bi = i;
+        }
+        cudaGetLastError();
+        if (bi < 0) {
+            st = IBM_ERR_NOT_CONVERGED;
+            break;
+        }
+        *best = bi;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ibm_destroy(ctx);
+    return st;
+}

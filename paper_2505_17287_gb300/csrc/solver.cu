@@ -1239,6 +1239,7 @@ ibm_status compact_flags(Ctx *c, const uint8_t *flags, int64_t **out, int64_t *c
 // the current classification.
 ibm_status mg_build(Ctx *c) {
     const int L = (int)c->lg.size();
+    ++c->mg_gen;
     std::vector<double *> ox(L), oy(L), oz(L);
     for (int l = 0; l < L; ++l) {
         const int64_t n = (int64_t)c->lg[l].nx * c->lg[l].ny * c->lg[l].nz;
@@ -1303,7 +1304,7 @@ ibm_status mg_build(Ctx *c) {
 template <typename T>
 static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col) {
     MGLevel<T> &L = H.lv[l];
-    const int bx = 128;
+    const int bx = c->opts.tile_x;
     const dim3 grid = rows_grid(L.nx, L.ny, L.nz, 2, bx);
     if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true>), grid, bx, L, f, x, col);
     else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false>), grid, bx, L, f, x, col);
@@ -1315,7 +1316,7 @@ template <typename T>
 static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     const int L = (int)H.lv.size();
     const int nu1 = c->opts.nu1, nu2 = c->opts.nu2, cs = c->opts.coarse_sweeps;
-    const int bx = 128;
+    const int bx = c->opts.tile_x;
     if (L == 1) {
         KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[0], f0, x0, cs);
         IBM_LAUNCHED(c);
@@ -1381,6 +1382,43 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     return IBM_OK;
 }
 
+// The V-cycle pr -> pz as one CUDA graph: captured from the stream the
+// first time (and again after a multigrid rebuild or a change of its
+// settings), then replayed with a single launch. Its buffers are fixed, so
+// the graph stays valid for the life of the hierarchy.
+template <typename T>
+static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H) {
+    const ibm_solver_opts &o = c->opts;
+    const uint64_t key = ((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
+                           (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 2 + (uint64_t)o.mg_interp + 1;
+    if (!H.vgraph || H.vgraph_key != key) {
+        if (H.vgraph) {
+            IBM_CUDA(c, cudaStreamSynchronize(c->s));
+            cudaGraphExecDestroy(H.vgraph);
+            H.vgraph = nullptr;
+        }
+        const int64_t n0 = c->nlaunch;
+        IBM_CUDA(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+        const ibm_status st = vcycle(c, H, H.pr, H.pz);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->s, &g);
+        IBM_TRY(st);
+        if (e != cudaSuccess) return c->fail(IBM_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&H.vgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+            H.vgraph = nullptr;
+            return c->fail(IBM_ERR_CUDA, std::string("V-cycle graph instantiation: ") + cudaGetErrorString(e2));
+        }
+        H.vgraph_key = key;
+        H.vgraph_kernels = c->nlaunch - n0;
+        c->nlaunch = n0;   // counted when the graph runs
+    }
+    IBM_CUDA(c, cudaGraphLaunch(H.vgraph, c->s));
+    c->nlaunch += H.vgraph_kernels;
+    return IBM_OK;
+}
+
 // MG-PCG with a fixed number of iterations: K x = f, with f in H.pr on
 // entry (it becomes the residual); the solution is left in H.px
 template <typename T>
@@ -1421,7 +1459,9 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
         // one CG step is alpha times one V-cycle; FGMRES is invariant to
         // that scalar, so the V-cycle output is used directly
-        IBM_TRY(vcycle(c, H, H.pr, H.pz));
+        // (the legacy default stream cannot be captured: launched directly there)
+        if (c->opts.graph && !c->kt.on && c->s != nullptr && c->s != cudaStreamLegacy) IBM_TRY(vcycle_graph(c, H));
+        else IBM_TRY(vcycle(c, H, H.pr, H.pz));
         xin = H.pz;
     } else {
         IBM_TRY(pcg(c, H, c->opts.inner_iters));

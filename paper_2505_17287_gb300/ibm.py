@@ -46,7 +46,7 @@ class ibm_solver_opts(Structure):
                 ("nu1", c_int), ("nu2", c_int), ("coarse_sweeps", c_int), ("helm_rtol", c_double),
                 ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
                 ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
-                ("mixed_inner_rtol", c_double), ("mg_interp", c_int)]
+                ("mixed_inner_rtol", c_double), ("mg_interp", c_int), ("tile_x", c_int), ("graph", c_int)]
 
 
 class ibm_table_info(Structure):
@@ -96,7 +96,7 @@ class ibm_server_stats(Structure):
                 ("peak_admitted_bytes", c_size_t)]
 
 
-EXPORTS = ["ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
+EXPORTS = ["ibm_tune", "ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
            "ibm_server_destroy",
            "ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
@@ -140,6 +140,8 @@ def load_library(path: str = LIB_PATH):
     L.ibm_server_wait.argtypes = [P, c_int64, c_double, POINTER(ibm_result)]
     L.ibm_server_get_stats.argtypes = [P, POINTER(ibm_server_stats)]
     L.ibm_server_destroy.argtypes = [P]
+    L.ibm_tune.argtypes = [POINTER(ibm_grid_desc), c_int, P, P, P, P, POINTER(ibm_solver_opts), c_int, c_int,
+                           POINTER(c_int), P]
     for name in EXPORTS:
         if name != "ibm_last_error":
             getattr(L, name).restype = c_int
@@ -520,3 +522,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def ibm_tune(case, candidates, steps=3, stream=None, bc=(0, 1, 2, 2, 2, 2), precision=IBM_FP64):
+    """Time `steps` fractional steps of `case` under each option set in
+    `candidates` (ibm_solver_opts) on `stream` (a torch.cuda.Stream; default
+    a new one, so V-cycle graphs can be captured). Returns (best index, ms per
+    step of each candidate, negative = failed)."""
+    import torch
+    from . import synth
+    st = stream if stream is not None else torch.cuda.Stream()
+    nx, ny = len(case.xf) - 1, len(case.yf) - 1
+    nz = len(case.zf) - 1 if case.ndim == 3 else 1
+    xf = np.ascontiguousarray(case.xf, dtype=np.float64)
+    yf = np.ascontiguousarray(case.yf, dtype=np.float64)
+    zf = np.ascontiguousarray(case.zf if case.ndim == 3 else [0.0, 1.0], dtype=np.float64)
+    d = ibm_grid_desc()
+    d.ndim, d.nx, d.ny, d.nz = case.ndim, nx, ny, nz
+    d.xf, d.yf, d.zf = _p(xf), _p(yf), _p(zf)
+    d.Re, d.dt = float(case.Re), float(case.dt)
+    d.u_inf = (c_double * 3)(*[float(x) for x in case.u_inf])
+    d.bc = (c_int * 6)(*bc)
+    d.precision = precision
+    d.stream = c_void_p(st.cuda_stream)
+    bodies = synth.case_bodies(case)
+    vs = [np.ascontiguousarray(np.c_[v, np.zeros(len(v))] if v.shape[1] == 2 else v, dtype=np.float64)
+          for v, _ in bodies]
+    es = [np.ascontiguousarray(e, dtype=np.int32) for _, e in bodies]
+    vp = (c_void_p * len(vs))(*[v.ctypes.data for v in vs])
+    ep = (c_void_p * len(es))(*[e.ctypes.data for e in es])
+    nv = np.array([len(v) for v in vs], np.int64)
+    ne = np.array([len(e) for e in es], np.int64)
+    cand = (ibm_solver_opts * len(candidates))(*candidates)
+    ms = np.zeros(len(candidates))
+    best = c_int(-1)
+    torch.cuda.synchronize()
+    _status_check(load_library().ibm_tune(byref(d), len(vs), ctypes.cast(vp, c_void_p), _p(nv),
+                                          ctypes.cast(ep, c_void_p), _p(ne), cand, len(candidates), steps,
+                                          byref(best), _p(ms)), "ibm_tune")
+    return best.value, ms
