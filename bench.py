@@ -32,6 +32,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# more hardware work queues, so the independent cases of the ensemble and
+# serving legs (one stream each) run concurrently; read at CUDA context creation
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "Mcell-steps/s per GB300, mixed vs FP64 at 1e-10 residual; serve p50/p99 latency"
 UNIT = "Mcell-steps/s"
@@ -69,6 +72,8 @@ def parse():
                     help="requests of the 3D multi-sphere serving stream to replay (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=4, help="cases resident at once in the serving leg")
     ap.add_argument("--serve-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--ensemble", type=int, default=64,
+                    help="cases of the seeded 2D ensemble to run, 50 steps each (0: skip)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the main timed run (the mixed run beside it is --no-mixed's)")
     return ap.parse_args()
@@ -236,6 +241,29 @@ def serve_leg(nreq, slots, precision):
                         "multiple of 16; Re 100-500; CFL 0.2; 10 steps per request; Poisson rtol 1e-10"}
 
 
+def ensemble_leg(ncases):
+    """The seeded 2D ensemble (ellipses and circles, grids 128x64 to
+    1024x512, Re 50-200, CFL 0.2, 50 steps each) in mixed precision: options
+    autotuned per size class, every case resident on its own stream with its
+    step captured as device-controlled CUDA graphs, all steps enqueued at
+    once; throughput = cell-steps / wall time of the steps."""
+    from paper_2505_17287_gb300 import ensemble, ibm, synth
+    cases = synth.ensemble_2d(ncases)
+    t0 = time.perf_counter()
+    tuned = ensemble.tune(cases, steps=2)
+    tune_s = time.perf_counter() - t0
+    out = ensemble.run_graphs(cases, tuned=tuned)
+    return {"cases": ncases, "steps_each": 50, "ok": out["ok"], "value": out["mcell_steps_per_s"], "unit": UNIT,
+            "wall_s": out["wall_s"], "cell_steps": out["cell_steps"], "setup_s": out["setup_s"], "tune_s": tune_s,
+            "precision": "mixed", "path": "ibm_step_async of device-controlled step graphs (opts graph=2), one "
+                                        "stream per case, all enqueued from one thread",
+            "tuned": {str(k): ensemble.describe(v[0]) for k, v in sorted(tuned.items())},
+            "max_rel_residual": max(r["rel_residual"] for r in out["results"]),
+            "workload": "seeded 2D ensemble: 64 ellipse/circle bodies (semi-axes 0.3-1.0, angle 0-pi), "
+                        "grids nx in [128, 1024] (multiple of 32) x nx/2 on [-8,24]x[-8,8], Re 50-200, "
+                        "dt = 0.2 h, 50 steps, Poisson rtol 1e-10"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -389,6 +417,10 @@ def main():
         except Exception as e:  # the oracle is optional on a box without it
             result["cpu_baseline"] = {"value": None, "error": str(e)}
     s.close()
+    if rank == 0 and args.ensemble > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        result["ensemble"] = ensemble_leg(args.ensemble)
     if rank == 0 and args.serve > 0:
         torch.cuda.synchronize()
         torch.cuda.empty_cache()

@@ -112,7 +112,9 @@ typedef struct {
                            and replayed at every preconditioner call (one launch
                            instead of ~10 per level; not on the legacy default
                            stream, which cannot be captured, nor while the kernel
-                           timer runs); 0: launched kernel by kernel */
+                           timer runs); 2: the whole fractional step is one captured
+                           graph with device-side loop control (ibm_step_async);
+                           0: launched kernel by kernel */
 } ibm_solver_opts;
 
 typedef struct {
@@ -210,6 +212,27 @@ ibm_status ibm_classify_cells(ibm_ctx *ctx, ibm_table_info *out);
    when a solve hit its iteration limit (the step is still completed),
    IBM_ERR_DIVERGED on NaN/Inf (state then undefined). */
 ibm_status ibm_step(ibm_ctx *ctx, int nsteps, ibm_step_stats *out);
+
+/* Device-controlled steps (no counterpart in the paper). With opts.graph ==
+   2 every step after the first of a classification runs as one captured
+   CUDA graph whose Helmholtz, ghost-refresh, FGMRES and refinement loops are
+   conditional nodes decided on the device (same kernels and stopping tests
+   as ibm_step; Givens rotations evaluated on the device), so a step needs
+   no host round trip; not available on the legacy default stream or with
+   BiCGStab or inner_iters > 1 (those steps run host-driven). The graphs are
+   captured on first use and again after a re-classification or an option
+   change. ibm_step_async enqueues nsteps such steps on the context stream
+   and returns without waiting (steps that cannot be captured still run to
+   completion inside the call); ibm_step_wait waits for them and returns
+   their statistics and status as ibm_step would (per-phase times are not
+   split: ms_total only). ibm_step is ibm_step_async + ibm_step_wait. */
+ibm_status ibm_step_async(ibm_ctx *ctx, int nsteps);
+/* Capture now the graphs the next steps will use (the next step and both
+   alternations of the step buffers after it), so that later ibm_step /
+   ibm_step_async calls launch without capturing; a no-op when the steps
+   would not be captured. */
+ibm_status ibm_step_prepare(ibm_ctx *ctx);
+ibm_status ibm_step_wait(ibm_ctx *ctx, ibm_step_stats *out);
 
 /* Solve the ghost-cell pressure Poisson system A phi = P b (Section 2.1
    pressure equation; Section 2.2 Neumann ghost rows) on the classified

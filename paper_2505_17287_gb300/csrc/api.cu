@@ -75,10 +75,14 @@ static void release_all(Ctx *c) {
     if (c->s) cudaStreamSynchronize(c->s);
     if (c->mg64.vgraph) cudaGraphExecDestroy(c->mg64.vgraph);
     if (c->mg32.vgraph) cudaGraphExecDestroy(c->mg32.vgraph);
+    for (int i = 0; i < Ctx::NSGRAPH; ++i)
+        if (c->sgraph[i]) cudaGraphExecDestroy(c->sgraph[i]);
+    for (int i = 0; i < 8; ++i)
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
     std::vector<void *> a = c->allocs;
     for (void *p : a) dev_free(c, p);
     if (c->hscal) cudaFreeHost(c->hscal);
-    cudaEvent_t ev[4] = {c->ev0, c->ev1, c->ev2, c->ev3};
+    cudaEvent_t ev[6] = {c->ev0, c->ev1, c->ev2, c->ev3, c->ev4, c->ev5};
     for (auto e : ev)
         if (e) cudaEventDestroy(e);
     for (auto e : c->kt.pool) cudaEventDestroy(e);
@@ -127,7 +131,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
         why = "tile_x must be 32, 64, 128, 256 or 512";
         return false;
     }
-    if (o->graph != 0 && o->graph != 1) { why = "graph must be 0 or 1"; return false; }
+    if (o->graph < 0 || o->graph > 2) { why = "graph must be 0, 1 or 2"; return false; }
     return true;
 }
 
@@ -313,6 +317,12 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     c->NFx = (int64_t)(c->nx + 1) * c->ny * c->nz;
     c->NFy = (int64_t)c->nx * (c->ny + 1) * c->nz;
     c->NFz = (int64_t)c->nx * c->ny * (c->nz + 1);
+    {
+        const int64_t r = (c->N + 8 * RED_THREADS - 1) / (8 * RED_THREADS);
+        c->nred = (int)(r < 1 ? 1 : (r > RED_BLOCKS ? RED_BLOCKS : r));
+        const int64_t e = (c->N + 255) / 256;
+        c->nelem = (unsigned)(e < 1 ? 1 : (e > 152 * 16 ? 152 * 16 : e));
+    }
     c->hxf.assign(d->xf, d->xf + c->nx + 1);
     c->hyf.assign(d->yf, d->yf + c->ny + 1);
     if (c->ndim == 3) c->hzf.assign(d->zf, d->zf + c->nz + 1);
@@ -324,6 +334,8 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     IBM_CUDA(c, cudaEventCreate(&c->ev1));
     IBM_CUDA(c, cudaEventCreate(&c->ev2));
     IBM_CUDA(c, cudaEventCreate(&c->ev3));
+    IBM_CUDA(c, cudaEventCreate(&c->ev4));
+    IBM_CUDA(c, cudaEventCreate(&c->ev5));
     IBM_CUDA(c, cudaMallocHost((void **)&c->hscal, sizeof(double) * 64));
     c->xf = upload(c, c->hxf); c->yf = upload(c, c->hyf); c->zf = upload(c, c->hzf);
     c->xc = upload(c, c->hxc); c->yc = upload(c, c->hyc); c->zc = upload(c, c->hzc);
@@ -531,23 +543,69 @@ extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
     return IBM_OK;
 }
 
+// enqueue nsteps steps; host-driven steps complete here, captured ones are
+// only launched (their statistics are collected by step_collect)
+static ibm_status step_enqueue(ibm_ctx *c, int nsteps) {
+    for (int q = 0; q < nsteps; ++q) {
+        if (step_graph_eligible(c) == IBM_OK) {
+            if (c->pend_graph == 0) IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
+            IBM_TRY(flow_step_graph(c));
+            ++c->pend_graph;
+            continue;
+        }
+        ibm_status s = flow_step(c, &c->pend);
+        if (s == IBM_ERR_NOT_CONVERGED) c->pend_status = s;
+        else if (s != IBM_OK) return s;
+    }
+    return IBM_OK;
+}
+
+static ibm_status step_collect(ibm_ctx *c, ibm_step_stats *out) {
+    ibm_status status = c->pend_status;
+    ibm_status hard = IBM_OK;
+    if (c->pend_graph > 0) {
+        IBM_CUDA(c, cudaEventRecord(c->ev3, c->s));
+        const ibm_status s = step_stats_read(c, &c->pend);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev2, c->ev3);
+        c->pend.ms_total += ms;
+        c->pend_graph = 0;
+        if (s == IBM_ERR_NOT_CONVERGED) status = s;
+        else if (s != IBM_OK) hard = s;
+    }
+    if (hard == IBM_OK && c->pend.steps > 0) hard = div_stat(c, &c->pend.max_div);
+    if (out) *out = c->pend;
+    c->pend = ibm_step_stats{};
+    c->pend_status = IBM_OK;
+    return hard != IBM_OK ? hard : status;
+}
+
 extern "C" ibm_status ibm_step(ibm_ctx *c, int nsteps, ibm_step_stats *out) {
     if (!c) return IBM_ERR_ARG;
     if (nsteps < 0) return c->fail(IBM_ERR_ARG, "nsteps must be >= 0");
     if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_step");
-    ibm_step_stats st{};
-    ibm_status status = IBM_OK;
-    for (int q = 0; q < nsteps; ++q) {
-        ibm_status s = flow_step(c, &st);
-        if (s == IBM_ERR_NOT_CONVERGED) status = s;
-        else if (s != IBM_OK) {
-            if (out) *out = st;
-            return s;
-        }
-    }
-    if (nsteps > 0) IBM_TRY(div_stat(c, &st.max_div));
-    if (out) *out = st;
-    return status;
+    const ibm_status s = step_enqueue(c, nsteps);
+    const ibm_status r = step_collect(c, out);
+    return s != IBM_OK ? s : r;
+}
+
+extern "C" ibm_status ibm_step_async(ibm_ctx *c, int nsteps) {
+    if (!c) return IBM_ERR_ARG;
+    if (nsteps < 0) return c->fail(IBM_ERR_ARG, "nsteps must be >= 0");
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_step_async");
+    return step_enqueue(c, nsteps);
+}
+
+extern "C" ibm_status ibm_step_prepare(ibm_ctx *c) {
+    if (!c) return IBM_ERR_ARG;
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_step_prepare");
+    if (step_graph_eligible(c) != IBM_OK) return IBM_OK;
+    return flow_graph_prepare(c);
+}
+
+extern "C" ibm_status ibm_step_wait(ibm_ctx *c, ibm_step_stats *out) {
+    if (!c) return IBM_ERR_ARG;
+    return step_collect(c, out);
 }
 
 extern "C" ibm_status ibm_poisson_solve(ibm_ctx *c, const double *rhs, double *phi, double rtol, int maxit,

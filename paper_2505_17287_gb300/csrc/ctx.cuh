@@ -145,7 +145,33 @@ struct Ctx {
     MGHier<float> mg32;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    cudaEvent_t ev4 = nullptr, ev5 = nullptr;   // Poisson solve timing
+
+    // device-controlled step (opts.graph == 2): the whole fractional step is
+    // captured once per buffer parity into a CUDA graph whose loops are
+    // conditional nodes; dctl holds the solver control blocks, dstats the
+    // statistics accumulated by the graphs
+    bool capturing = false;
+    cudaStream_t side[8] = {nullptr};
+    int side_depth = 0;
+    void *dctl = nullptr;
+    void *dstats = nullptr;
+    void *hctl = nullptr;   // Helmholtz / ghost refresh control of the captured step
+    // steps enqueued by ibm_step_async and not yet collected by ibm_step_wait
+    ibm_step_stats pend{};
+    int pend_graph = 0;
+    ibm_status pend_status = IBM_OK;
+    static constexpr int NSGRAPH = 4;   // first step + two buffer parities, one spare
+    cudaGraphExec_t sgraph[NSGRAPH] = {nullptr};
+    uint64_t sgraph_key[NSGRAPH] = {0};
+    const double *sgraph_nold[NSGRAPH] = {nullptr};
     int64_t nlaunch = 0;   // kernels launched by this context so far
+    // launch sizes that follow the grid: reduction kernels run nred blocks of
+    // RED_THREADS (at most RED_BLOCKS, about 8 cells per thread below that;
+    // a function of N only, so reductions stay deterministic), elementwise
+    // grid-stride kernels nelem blocks of 256
+    int nred = RED_BLOCKS;
+    unsigned nelem = 152 * 16;
     uint64_t mg_gen = 0;   // multigrid rebuild counter (invalidates captured V-cycles)
 
     ibm_status fail(ibm_status code, const std::string &m) {
@@ -177,6 +203,22 @@ ibm_status geom_classify(Ctx *c);
 // flow.cu
 ibm_status flow_init(Ctx *c);
 ibm_status flow_step(Ctx *c, ibm_step_stats *st);
+ibm_status step_graph_eligible(Ctx *c);
+ibm_status flow_step_graph(Ctx *c);
+ibm_status flow_graph_prepare(Ctx *c);
+ibm_status step_graph_begin(Ctx *c);
+ibm_status step_graph_end(Ctx *c, ibm_step_stats *st, int steps);
+ibm_status poisson_solve_dev(Ctx *c, const double *rhs, double *phi, double rtol, int maxit);
+ibm_status poisson_dev_prepare(Ctx *c);
+ibm_status step_stats_dev(Ctx *c, const int *hsw);
+ibm_status step_stats_read(Ctx *c, ibm_step_stats *st);
+// conditional graph nodes during stream capture
+struct CondScope {
+    cudaStream_t outer = nullptr;
+};
+ibm_status cond_handle(Ctx *c, cudaGraphConditionalHandle *h);
+ibm_status cond_open(Ctx *c, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle h, CondScope *sc);
+ibm_status cond_close(Ctx *c, CondScope *sc);
 ibm_status ghost_refresh_velocity(Ctx *c, int comp, int *iters);
 ibm_status div_stat(Ctx *c, double *out);
 

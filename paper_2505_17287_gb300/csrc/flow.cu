@@ -465,11 +465,11 @@ static ibm_status faces_from(Ctx *c, double *const *ucell) {
         IBM_LAUNCHED(c);
     }
     CFields3 F{{c->F[0], c->F[1], c->F[2]}};
-    ++c->nlaunch, k_bnd_flux<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, F, bc, c->part);
+    ++c->nlaunch, k_bnd_flux<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, F, bc, c->part);
     IBM_LAUNCHED(c);
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 56));
+    IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 56));
     Fields3 Fw{{c->F[0], c->F[1], c->F[2]}};
-    ++c->nlaunch, k_outflow_corr<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, Fw, bc, c->scal + 56);
+    ++c->nlaunch, k_outflow_corr<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, Fw, bc, c->scal + 56);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -525,18 +525,24 @@ ibm_status flow_init(Ctx *c) {
 }
 
 // Helmholtz solve for component q, u = ustar (initial guess u^n)
-static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
+static ibm_status helm_prepare(Ctx *c) {
     const BCInfo bc = make_bc(c);
     const double alpha = c->desc.dt / (2.0 * c->desc.Re);
     if (!c->hinv_ok) {
         for (int cq = 0; cq < c->ndim; ++cq) {
             if (!c->hinv[cq]) c->hinv[cq] = (double *)dev_alloc(c, sizeof(double) * c->N);
             if (!c->hinv[cq]) return c->fail(IBM_ERR_OOM, "Helmholtz diagonal allocation failed");
-            ++c->nlaunch, k_helm_diag<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, bc, cq, alpha, c->hinv[cq]);
+            ++c->nlaunch, k_helm_diag<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, bc, cq, alpha, c->hinv[cq]);
         }
         IBM_LAUNCHED(c);
         c->hinv_ok = true;
     }
+    return IBM_OK;
+}
+
+static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
+    const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    IBM_TRY(helm_prepare(c));
     const double *hinv = c->hinv[q];
     double *u = c->ustar[q];
     const double *rhs = c->rhs[q];
@@ -560,9 +566,9 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
         }
         ++*sweeps;
         if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
-            ++c->nlaunch, k_helm_resid<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+            ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
             IBM_LAUNCHED(c);
-            IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + 48));
+            IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
             double gmax = 0.0;
             if (c->ng > 0) {
                 // ghost-row residual: largest change a further Jacobi pass would make
@@ -594,7 +600,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
     kt_begin(c, K_CONV);
-    ++c->nlaunch, k_conv_rhs<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
                                            alpha, nc);
     kt_end(c, K_CONV);
     IBM_LAUNCHED(c);
@@ -611,7 +617,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     IBM_TRY(faces_from(c, c->ustar));
     CFields3 Fs{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
     double *braw = c->rhs[0];
-    ++c->nlaunch, k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
+    ++c->nlaunch, k_divergence<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
     IBM_LAUNCHED(c);
     IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
     ibm_solve_stats ps{};
@@ -627,7 +633,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     IBM_LAUNCHED(c);
     CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
     Fields3 un{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
-    ++c->nlaunch, k_project_cells<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
+    ++c->nlaunch, k_project_cells<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
     IBM_LAUNCHED(c);
     int passes = 0;
     IBM_TRY(ghost_refresh_all(c, c->u, &passes));
@@ -663,15 +669,295 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
 ibm_status div_stat(Ctx *c, double *out) {
     CFields3 F{{c->F[0], c->F[1], c->ndim == 3 ? c->F[2] : c->F[1]}};
     double *d = c->rhs[1];
-    ++c->nlaunch, k_divergence<<<152 * 16, 256, 0, c->s>>>(c->g, c->type, F, 1.0, d);
+    ++c->nlaunch, k_divergence<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, F, 1.0, d);
     IBM_LAUNCHED(c);
     IBM_TRY(fluid_mean(c, d, false, nullptr));
-    ++c->nlaunch, k_div_stats<<<RED_BLOCKS, RED_THREADS, 0, c->s>>>(c->g, c->type, d, c->scal + 5, c->part);
-    ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, RED_BLOCKS, c->scal + 52);
+    ++c->nlaunch, k_div_stats<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, d, c->scal + 5, c->part);
+    ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, c->nred, c->scal + 52);
     IBM_LAUNCHED(c);
     IBM_TRY(sync_scalars(c, 53));
     *out = c->hscal[52];
     return IBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-controlled step (opts.graph == 2)
+//
+// The fractional step above, captured into one CUDA graph: the Helmholtz
+// sweeps and the velocity ghost refresh become WHILE nodes with the same
+// four-sweep trips and the same stopping tests, evaluated by one-thread
+// kernels; the Poisson solve is poisson_solve_dev. The host launches the
+// graph and reads the accumulated statistics once per ibm_step call.
+// ---------------------------------------------------------------------------
+
+struct HelmCtl {
+    int sweeps[3];
+    int status;   // IBM_ERR_DIVERGED / IBM_ERR_NOT_CONVERGED of the Helmholtz or ghost loops
+    double rhs2;
+    int passes;
+};
+
+__global__ void k_hc_reset(HelmCtl *H, int q, cudaGraphConditionalHandle h) {
+    if (q == 0) H->status = 0;
+    if (q >= 0) {
+        H->sweeps[q] = 0;
+        H->rhs2 = -1.0;
+    } else {
+        H->passes = 0;
+    }
+    cudaGraphSetConditional(h, 1u);
+}
+
+__global__ void k_helm_decide(HelmCtl *H, int q, const double *__restrict__ scal, int has_ghost, double tol,
+                              double scale, int maxit, int trip, cudaGraphConditionalHandle h) {
+    H->sweeps[q] += trip;
+    const double r2 = scal[48];
+    if (H->rhs2 < 0.0) H->rhs2 = scal[49];
+    const double gmax = has_ghost ? scal[50] : 0.0;
+    if (!isfinite(r2)) {
+        H->status = IBM_ERR_DIVERGED;
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const double bn = sqrt(H->rhs2) > 0.0 ? sqrt(H->rhs2) : 1.0;
+    const bool conv = sqrt(r2) <= tol * bn && gmax <= tol * scale;
+    const bool go = !conv && H->sweeps[q] < maxit;
+    if (!conv && !go && H->status == 0) H->status = IBM_ERR_NOT_CONVERGED;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_ghost_decide(HelmCtl *H, const double *__restrict__ d, double tol, int maxit, int trip,
+                               cudaGraphConditionalHandle h) {
+    H->passes += trip;
+    const double v = *d;
+    if (!isfinite(v)) {
+        H->status = IBM_ERR_DIVERGED;
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    cudaGraphSetConditional(h, (v > tol && H->passes < maxit) ? 1u : 0u);
+}
+
+static double u_scale(Ctx *c) {
+    double scale = 1.0;
+    for (int a = 0; a < 3; ++a) scale = fmax(scale, fabs(c->desc.u_inf[a]));
+    return scale;
+}
+
+static ibm_status helmholtz_dev(Ctx *c, int q) {
+    const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    HelmCtl *H = (HelmCtl *)c->hctl;
+    const double *hinv = c->hinv[q];
+    double *u = c->ustar[q];
+    const double *rhs = c->rhs[q];
+    const unsigned gb = (unsigned)((c->ng + 255) / 256);
+    Fields3 U{{u, u, u}};
+    const int trip = 4;
+    cudaGraphConditionalHandle h;
+    IBM_TRY(cond_handle(c, &h));
+    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, q, h);
+    CondScope sc;
+    IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
+    for (int t = 0; t < trip; ++t) {
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 0);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 1);
+        if (c->ng > 0) {
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
+        }
+    }
+    ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+    IBM_LAUNCHED(c);
+    IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
+    if (c->ng > 0) {
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
+        ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
+    }
+    ++c->nlaunch, k_helm_decide<<<1, 1, 0, c->s>>>(H, q, c->scal, c->ng > 0, c->opts.helm_rtol, u_scale(c),
+                                                 c->opts.helm_maxit, trip, h);
+    IBM_LAUNCHED(c);
+    IBM_TRY(cond_close(c, &sc));
+    return IBM_OK;
+}
+
+static ibm_status ghost_refresh_dev(Ctx *c) {
+    if (c->ng == 0) return IBM_OK;
+    HelmCtl *H = (HelmCtl *)c->hctl;
+    const int nc = c->ndim;
+    Fields3 U{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    const unsigned gb = (unsigned)((c->ng + 255) / 256);
+    const int trip = 4;
+    cudaGraphConditionalHandle h;
+    IBM_TRY(cond_handle(c, &h));
+    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, -1, h);
+    CondScope sc;
+    IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
+    for (int t = 0; t < trip; ++t) {
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, t == trip - 1);
+        ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
+    }
+    ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
+    ++c->nlaunch, k_ghost_decide<<<1, 1, 0, c->s>>>(H, c->scal + 40, c->opts.ghost_tol * u_scale(c),
+                                                  c->opts.ghost_maxit, trip, h);
+    IBM_LAUNCHED(c);
+    IBM_TRY(cond_close(c, &sc));
+    return IBM_OK;
+}
+
+// the captured body of one step (the first step after a classification
+// takes the Euler start, as in flow_step)
+static ibm_status flow_step_capture(Ctx *c) {
+    const int nc = c->ndim;
+    const double dt = c->desc.dt, alpha = dt / (2.0 * c->desc.Re);
+    CFields3 u{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    CFields3 F{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
+    CFields3 No{{c->Nold[0], c->Nold[1], nc == 3 ? c->Nold[2] : c->Nold[1]}};
+    Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
+    Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R,
+                                                       make_bc(c), dt, alpha, nc);
+    IBM_LAUNCHED(c);
+    for (int q = 0; q < nc; ++q) {
+        IBM_CUDA(c, cudaMemcpyAsync(c->ustar[q], c->u[q], sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->s));
+        IBM_TRY(helmholtz_dev(c, q));
+    }
+    IBM_TRY(faces_from(c, c->ustar));
+    CFields3 Fs{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
+    double *braw = c->rhs[0];
+    ++c->nlaunch, k_divergence<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
+    IBM_LAUNCHED(c);
+    IBM_TRY(poisson_solve_dev(c, braw, c->p, c->opts.rtol, c->opts.max_outer));
+    for (int a = 0; a < nc; ++a) {
+        const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
+        const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
+        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
+    }
+    CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
+    Fields3 un{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    ++c->nlaunch, k_project_cells<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->p, us, un, dt);
+    IBM_LAUNCHED(c);
+    IBM_TRY(ghost_refresh_dev(c));
+    IBM_TRY(step_stats_dev(c, ((HelmCtl *)c->hctl)->sweeps));
+    return IBM_OK;
+}
+
+// whether this step can run as a captured graph
+ibm_status step_graph_eligible(Ctx *c) {
+    const ibm_solver_opts &o = c->opts;
+    if (o.graph != 2 || c->kt.on || c->s == nullptr || c->s == cudaStreamLegacy) return IBM_ERR_STATE;
+    if (o.outer != IBM_OUTER_FGMRES || o.inner_iters != 1) return IBM_ERR_STATE;
+    return IBM_OK;
+}
+
+static uint64_t graph_key(Ctx *c) {
+    // FNV-1a over the options and the multigrid generation
+    uint64_t h = 1469598103934665603ull;
+    const unsigned char *b = (const unsigned char *)&c->opts;
+    for (size_t i = 0; i < sizeof(c->opts); ++i) h = (h ^ b[i]) * 1099511628211ull;
+    const unsigned char *g = (const unsigned char *)&c->mg_gen;
+    for (size_t i = 0; i < sizeof(c->mg_gen); ++i) h = (h ^ g[i]) * 1099511628211ull;
+    h = (h ^ (c->have_nold ? 1u : 2u)) * 1099511628211ull;
+    return h | 1ull;
+}
+
+static ibm_status capture_step(Ctx *c, cudaGraphExec_t *out) {
+    IBM_TRY(helm_prepare(c));
+    IBM_TRY(poisson_dev_prepare(c));
+    if (!c->hctl) {
+        c->hctl = dev_alloc(c, sizeof(HelmCtl));
+        if (!c->hctl) return c->fail(IBM_ERR_OOM, "control block allocation failed");
+        IBM_CUDA(c, cudaMemsetAsync(c->hctl, 0, sizeof(HelmCtl), c->s));
+    }
+    for (int i = 0; i < 8; ++i)
+        if (!c->side[i]) IBM_CUDA(c, cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking));
+    cudaStream_t s0 = c->s;
+    c->capturing = true;
+    c->side_depth = 0;
+    IBM_CUDA(c, cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    ibm_status st = flow_step_capture(c);
+    // unwind any body capture left open by an error
+    while (c->side_depth > 0) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(c->side[--c->side_depth], &g);
+    }
+    c->s = s0;
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s0, &g);
+    if (st != IBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    if (e != cudaSuccess || !g) return c->fail(IBM_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        *out = nullptr;
+        return c->fail(IBM_ERR_CUDA, std::string("step graph instantiation: ") + cudaGetErrorString(e2));
+    }
+    return IBM_OK;
+}
+
+// the graph slot for the current settings, start (Euler or AB2) and buffer
+// parity; captured if missing
+static ibm_status graph_for_state(Ctx *c, int *slot_out) {
+    const uint64_t key = graph_key(c);
+    int slot = -1;
+    for (int i = 0; i < Ctx::NSGRAPH; ++i)
+        if (c->sgraph[i] && c->sgraph_key[i] == key && c->sgraph_nold[i] == c->Nold[0]) slot = i;
+    if (slot < 0) {
+        for (int i = 0; i < Ctx::NSGRAPH && slot < 0; ++i)
+            if (!c->sgraph[i]) slot = i;
+        if (slot < 0) {
+            // all slots hold graphs of other settings: release them
+            IBM_CUDA(c, cudaStreamSynchronize(c->s));
+            for (int i = 0; i < Ctx::NSGRAPH; ++i) {
+                cudaGraphExecDestroy(c->sgraph[i]);
+                c->sgraph[i] = nullptr;
+            }
+            slot = 0;
+        }
+        IBM_TRY(capture_step(c, &c->sgraph[slot]));
+        c->sgraph_key[slot] = key;
+        c->sgraph_nold[slot] = c->Nold[0];
+    }
+    *slot_out = slot;
+    return IBM_OK;
+}
+
+static void swap_nold(Ctx *c) {
+    for (int q = 0; q < 3; ++q) {
+        double *t = c->Nold[q];
+        c->Nold[q] = c->Nnew[q];
+        c->Nnew[q] = t;
+    }
+}
+
+// one step through the captured graph of the current state
+ibm_status flow_step_graph(Ctx *c) {
+    int slot = 0;
+    IBM_TRY(graph_for_state(c, &slot));
+    IBM_CUDA(c, cudaGraphLaunch(c->sgraph[slot], c->s));
+    swap_nold(c);
+    c->have_nold = true;
+    c->nstep += 1;
+    return IBM_OK;
+}
+
+// capture the graphs of the next step and of both buffer parities of the
+// steps after it, without running anything
+ibm_status flow_graph_prepare(Ctx *c) {
+    const bool h0 = c->have_nold;
+    int slot = 0;
+    ibm_status st = graph_for_state(c, &slot);
+    c->have_nold = true;
+    if (st == IBM_OK) st = graph_for_state(c, &slot);
+    swap_nold(c);
+    if (st == IBM_OK) st = graph_for_state(c, &slot);
+    swap_nold(c);
+    c->have_nold = h0;
+    return st;
 }
 
 }  // namespace ibm

@@ -120,9 +120,9 @@ __global__ void k_sub_mean(int64_t n, const uint8_t *__restrict__ type, double *
 
 ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_host) {
     (void)ghosts_too;
-    KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, x, c->part);
+    KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, x, c->part);
     IBM_LAUNCHED(c);
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     if (mean_host) {
         IBM_TRY(sync_scalars(c, S_MEAN + 1));
         *mean_host = c->hscal[S_MEAN];
@@ -246,14 +246,14 @@ OpT<float> op_of<float>(Ctx *c) {
 template <typename T>
 static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
     const OpT<T> o = op_of<T>(c);
-    KL(K_APPLY_A, k_apply_A<T>, RED_BLOCKS, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    KL(K_APPLY_A, k_apply_A<T>, c->nred, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
         KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, b, sgn, y);
         IBM_LAUNCHED(c);
     }
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-    KL(-1, k_sub_meanT<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    KL(-1, k_sub_meanT<T>, c->nred, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -1428,21 +1428,21 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
     IBM_CUDA(c, cudaMemsetAsync(H.px, 0, sizeof(T) * (size_t)n, c->s));
     IBM_TRY(vcycle(c, H, H.pr, H.pz));
     IBM_CUDA(c, cudaMemcpyAsync(H.pp, H.pz, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, c->s));
-    KL(-1, k_dot<T>, RED_BLOCKS, RED_THREADS, n, H.pr, H.pz, c->part);
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZ));
+    KL(-1, k_dot<T>, c->nred, RED_THREADS, n, H.pr, H.pz, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_RZ));
     for (int it = 0; it < iters; ++it) {
-        if (H.fine0) KL(K_SPMV0, (k_spmv_dot<T, true>), RED_BLOCKS, RED_THREADS, L0, H.pp, H.pq, c->part);
-        else KL(K_SPMV0, (k_spmv_dot<T, false>), RED_BLOCKS, RED_THREADS, L0, H.pp, H.pq, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_PQ));
+        if (H.fine0) KL(K_SPMV0, (k_spmv_dot<T, true>), c->nred, RED_THREADS, L0, H.pp, H.pq, c->part);
+        else KL(K_SPMV0, (k_spmv_dot<T, false>), c->nred, RED_THREADS, L0, H.pp, H.pq, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_PQ));
         KL(-1, k_alpha, 1, 1, c->scal);
-        KL(-1, k_axpy2<T>, RED_BLOCKS, RED_THREADS, n, H.px, H.pr, H.pp, H.pq, c->scal);
+        KL(-1, k_axpy2<T>, c->nred, RED_THREADS, n, H.px, H.pr, H.pp, H.pq, c->scal);
         IBM_LAUNCHED(c);
         if (it + 1 < iters) {
             IBM_TRY(vcycle(c, H, H.pr, H.pz));
-            KL(-1, k_dot<T>, RED_BLOCKS, RED_THREADS, n, H.pr, H.pz, c->part);
-            IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_RZN));
+            KL(-1, k_dot<T>, c->nred, RED_THREADS, n, H.pr, H.pz, c->part);
+            IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_RZN));
             KL(-1, k_beta, 1, 1, c->scal);
-            KL(-1, k_pupd<T>, RED_BLOCKS, RED_THREADS, n, H.pp, H.pz, c->scal);
+            KL(-1, k_pupd<T>, c->nred, RED_THREADS, n, H.pp, H.pz, c->scal);
             IBM_LAUNCHED(c);
         }
     }
@@ -1453,20 +1453,21 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     const OpT<T> oin = op_of<T>(c);
-    KL(-1, k_pre_in<T>, RED_BLOCKS, RED_THREADS, c->g, oin, c->type, v, H.pr);
+    KL(-1, k_pre_in<T>, c->nred, RED_THREADS, c->g, oin, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     const T *xin = H.px;
     if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
         // one CG step is alpha times one V-cycle; FGMRES is invariant to
         // that scalar, so the V-cycle output is used directly
         // (the legacy default stream cannot be captured: launched directly there)
-        if (c->opts.graph && !c->kt.on && c->s != nullptr && c->s != cudaStreamLegacy) IBM_TRY(vcycle_graph(c, H));
+        if (c->opts.graph == 1 && !c->kt.on && !c->capturing && c->s != nullptr && c->s != cudaStreamLegacy)
+            IBM_TRY(vcycle_graph(c, H));
         else IBM_TRY(vcycle(c, H, H.pr, H.pz));
         xin = H.pz;
     } else {
         IBM_TRY(pcg(c, H, c->opts.inner_iters));
     }
-    KL(-1, k_pre_out<T>, RED_BLOCKS, RED_THREADS, c->N, c->type, xin, z);
+    KL(-1, k_pre_out<T>, c->nred, RED_THREADS, c->N, c->type, xin, z);
     IBM_LAUNCHED(c);
     const OpT<T> o = op_of<T>(c);
     if (c->ng > 0) {
@@ -1490,8 +1491,8 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
 // ||x||^2 over all cells (FP64 accumulation)
 template <typename T>
 static ibm_status norm2(Ctx *c, const T *x, double *out) {
-    KL(-1, k_dotT<T>, RED_BLOCKS, RED_THREADS, c->N, x, x, c->part);
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
+    KL(-1, k_dotT<T>, c->nred, RED_THREADS, c->N, x, x, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
     IBM_TRY(sync_scalars(c, S_TMP + 1));
     *out = c->hscal[S_TMP];
     return IBM_OK;
@@ -1531,7 +1532,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
         if (rel <= rtol || (single_cycle && cycles > 0)) break;
         if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
         ++cycles;
-        KL(-1, (k_scale<T, T>), RED_BLOCKS, RED_THREADS, n, K.V[0], K.r, 1.0 / beta);
+        KL(-1, (k_scale<T, T>), c->nred, RED_THREADS, n, K.V[0], K.r, 1.0 / beta);
         IBM_LAUNCHED(c);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
@@ -1547,16 +1548,16 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             double hcol[17] = {0};
             double wbefore2 = 0.0, wafter2 = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], RED_BLOCKS, RED_THREADS, n,
+                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, c->part);
-                IBM_TRY(finalize(c, c->part, RED_BLOCKS, j + 2, 1.0, c->scal + S_MD));
+                IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
                 IBM_TRY(sync_scalars(c, S_MD + j + 2));
                 Coef h{};
                 for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
                 wbefore2 = c->hscal[S_MD + j + 1];
-                KL(K_ORTH, orth_table<T>(std::make_integer_sequence<int, 17>())[j], RED_BLOCKS, RED_THREADS, n,
+                KL(K_ORTH, orth_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, h, c->part);
-                IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
+                IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
                 IBM_TRY(sync_scalars(c, S_TMP + 1));
                 wafter2 = c->hscal[S_TMP];
                 for (int i = 0; i <= j; ++i) hcol[i] += h.v[i];
@@ -1583,7 +1584,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             jlast = j;
             const double est = fabs(gv[j + 1]) / bnorm;
             if (hn > 0.0 && j + 1 < m) {
-                KL(-1, (k_scale<T, T>), RED_BLOCKS, RED_THREADS, n, K.V[j + 1], K.w, 1.0 / hn);
+                KL(-1, (k_scale<T, T>), c->nred, RED_THREADS, n, K.V[j + 1], K.w, 1.0 / hn);
                 IBM_LAUNCHED(c);
             }
             if (est <= rtol || hn == 0.0) break;
@@ -1597,7 +1598,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
         }
         Coef yc{};
         for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
-        KL(-1, k_xupd<T>, RED_BLOCKS, RED_THREADS, n, x, (const T *const *)K.Zdev, jlast + 1, yc);
+        KL(-1, k_xupd<T>, c->nred, RED_THREADS, n, x, (const T *const *)K.Zdev, jlast + 1, yc);
         IBM_LAUNCHED(c);
     }
     *outer_out = outer;
@@ -1680,7 +1681,7 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
         if (rel <= rtol) break;
         if (steps >= maxit || refinements >= 256) { status = IBM_ERR_NOT_CONVERGED; break; }
         ++refinements;
-        KL(-1, (k_scale<float, double>), RED_BLOCKS, RED_THREADS, n, c->b32, c->rr, 1.0 / rn);
+        KL(-1, (k_scale<float, double>), c->nred, RED_THREADS, n, c->b32, c->rr, 1.0 / rn);
         IBM_CUDA(c, cudaMemsetAsync(c->d32, 0, sizeof(float) * n, c->s));
         IBM_LAUNCHED(c);
         // inner target: the FP64 goal, but no tighter than FP32 can reach
@@ -1697,9 +1698,9 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
                     refinements, rel, target, o, irel, (int)s);
         steps += o;
         inner += in;
-        KL(-1, k_fluid_volsum32, RED_BLOCKS, RED_THREADS, c->g, c->type, c->d32, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-        KL(-1, k_add_scaled, RED_BLOCKS, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
+        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+        KL(-1, k_add_scaled, c->nred, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
         IBM_LAUNCHED(c);
         if (o == 0) { status = IBM_ERR_NOT_CONVERGED; break; }
         if (refinements > 1 && !(rel < 0.999 * last_rel)) stalls++;
@@ -1717,9 +1718,9 @@ static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
     if (c->opts.precision == IBM_MIXED) {
         // FP64 vectors through the FP32 multigrid: convert in and out
         IBM_TRY(ensure_mixed(c));
-        KL(-1, (k_scale<float, double>), RED_BLOCKS, RED_THREADS, c->N, c->b32, v, 1.0);
+        KL(-1, (k_scale<float, double>), c->nred, RED_THREADS, c->N, c->b32, v, 1.0);
         IBM_TRY(precond<float>(c, c->mg32, c->b32, c->d32));
-        KL(-1, (k_scale<double, float>), RED_BLOCKS, RED_THREADS, c->N, z, c->d32, 1.0);
+        KL(-1, (k_scale<double, float>), c->nred, RED_THREADS, c->N, z, c->d32, 1.0);
         IBM_LAUNCHED(c);
         return IBM_OK;
     }
@@ -1756,25 +1757,25 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
             fresh = false;
         }
         // rho1 = (rh, r); beta; p = r + beta (p - omega v)
-        KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, n, rh, r, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + B_RHO1));
+        KL(-1, k_dot64, c->nred, RED_THREADS, n, rh, r, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + B_RHO1));
         KL(-1, k_bicg_beta, 1, 1, c->scal);
-        KL(-1, k_bicg_p, RED_BLOCKS, RED_THREADS, n, r, p, v, c->scal);
+        KL(-1, k_bicg_p, c->nred, RED_THREADS, n, r, p, v, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, p, ph));
         IBM_TRY(apply_PA<double>(c, ph, nullptr, 1.0, v));
-        KL(-1, k_dot64, RED_BLOCKS, RED_THREADS, n, rh, v, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + B_DEN));
+        KL(-1, k_dot64, c->nred, RED_THREADS, n, rh, v, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + B_DEN));
         KL(-1, k_bicg_alpha, 1, 1, c->scal);
-        KL(-1, k_bicg_s, RED_BLOCKS, RED_THREADS, n, r, v, sv, c->scal);
+        KL(-1, k_bicg_s, c->nred, RED_THREADS, n, r, v, sv, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, sv, shv));
         IBM_TRY(apply_PA<double>(c, shv, nullptr, 1.0, t));
-        KL(-1, k_bicg_tdots, RED_BLOCKS, RED_THREADS, n, t, sv, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 2, 1.0, c->scal + B_TS));
+        KL(-1, k_bicg_tdots, c->nred, RED_THREADS, n, t, sv, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + B_TS));
         KL(-1, k_bicg_omega, 1, 1, c->scal);
-        KL(-1, k_bicg_xr, RED_BLOCKS, RED_THREADS, n, phi, ph, shv, r, sv, t, c->scal, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0, c->scal + S_TMP));
+        KL(-1, k_bicg_xr, c->nred, RED_THREADS, n, phi, ph, shv, r, sv, t, c->scal, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
         IBM_LAUNCHED(c);
         inner += 2 * c->opts.inner_iters;
         ++it;
@@ -1791,16 +1792,520 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
 }
 
 // Solve P A phi = P rhs. rhs: FLUID rows read; phi: guess in, solution out.
+// ---------------------------------------------------------------------------
+// Device-controlled Poisson solve (captured into the step graph)
+//
+// The same FGMRES(m) and mixed-precision refinement as above, with every
+// decision taken on the device: the Hessenberg column, Givens rotations,
+// residual estimate, restart and stopping tests run in one-thread kernels
+// on a control block in device memory, and the loops are conditional graph
+// nodes (a WHILE node per restart loop, an IF node per Arnoldi step and per
+// re-orthogonalisation pass) whose conditions those kernels set.
+// ---------------------------------------------------------------------------
+
+struct DevFG {
+    double H[17 * 16], cs[16], sn[16], g[17], y[16], hcol[17];
+    double beta, bnorm, rtol, rel, scale, wb, wa;
+    int outer, maxit, jlast, active, reorth, go, cycles, single, status, ncols, zero;
+    // mixed-precision refinement (outer block only)
+    double rn, last_rel, inner_rtol;
+    int refinements, stalls, steps, stop;
+};
+
+// statistics accumulated by the step graphs over one ibm_step call
+struct DevStats {
+    int steps, outer, helm_sweeps, status;
+    double rel;
+};
+
+static DevFG *dfg(Ctx *c, int i) { return reinterpret_cast<DevFG *>(c->dctl) + i; }
+
+ibm_status cond_handle(Ctx *c, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    IBM_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive || !g) return c->fail(IBM_ERR_CUDA, "conditional handle outside capture");
+    IBM_CUDA(c, cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault));
+    return IBM_OK;
+}
+
+// add an IF/WHILE node with handle h at the capture point of c->s and
+// capture its body on a side stream until cond_close
+ibm_status cond_open(Ctx *c, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle h, CondScope *sc) {
+    if (c->side_depth >= 8 || !c->side[c->side_depth]) return c->fail(IBM_ERR_ARG, "conditional nesting too deep");
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    IBM_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &g, &deps, &ed, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) return c->fail(IBM_ERR_CUDA, "conditional node outside capture");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    IBM_CUDA(c, cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+    IBM_CUDA(c, cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t side = c->side[c->side_depth];
+    IBM_CUDA(c, cudaStreamBeginCaptureToGraph(side, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+    ++c->side_depth;
+    sc->outer = c->s;
+    c->s = side;
+    return IBM_OK;
+}
+
+ibm_status cond_close(Ctx *c, CondScope *sc) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->s, &g);
+    c->s = sc->outer;
+    --c->side_depth;
+    if (e != cudaSuccess) return c->fail(IBM_ERR_CUDA, std::string("conditional body capture: ") + cudaGetErrorString(e));
+    return IBM_OK;
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int *flag) { cudaGraphSetConditional(h, *flag ? 1u : 0u); }
+
+template <typename T, typename S>
+__global__ void k_scale_dev(int64_t n, T *__restrict__ dst, const S *__restrict__ src, const double *__restrict__ a) {
+    const double f = *a;
+    GRID_STRIDE(c, n) dst[c] = (T)(f * (double)src[c]);
+}
+
+// w -= sum_q h_q V_q with h in device memory; partial (w, w)
+template <typename T, int NC>
+__global__ void __launch_bounds__(RED_THREADS) k_orth_dev(int64_t n, T *__restrict__ w, VPtrs<T> V,
+                                                          const double *__restrict__ h, double *__restrict__ part) {
+    typedef typename Acc<T>::type A;
+    typedef typename Vec16<T>::type VT;
+    constexpr int W = Vec16<T>::W;
+    __shared__ double sh[32];
+    T hv[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) hv[q] = (T)h[q];
+    A ww = A(0);
+    const int64_t nv = n / W;
+    GRID_STRIDE(v, nv) {
+        VT a = reinterpret_cast<const VT *>(w)[v];
+        VT b[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) b[q] = reinterpret_cast<const VT *>(V.p[q])[v];
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - hv[q] * vget(b[q], e));
+        reinterpret_cast<VT *>(w)[v] = a;
+#pragma unroll
+        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+    }
+    for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        T a = w[c];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) a -= hv[q] * V.p[q][c];
+        w[c] = a;
+        ww += (A)a * (A)a;
+    }
+    const double t = block_sum<RED_THREADS>((double)ww, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+template <typename T>
+using OrthDevFn = void (*)(int64_t, T *, VPtrs<T>, const double *, double *);
+template <typename T, int... I>
+static const OrthDevFn<T> *orth_dev_table(std::integer_sequence<int, I...>) {
+    static const OrthDevFn<T> t[] = {&k_orth_dev<T, I + 1>...};
+    return t;
+}
+
+// x += sum_{q < ncols} y_q Z_q with y and ncols from the control block
+template <typename T>
+__global__ void k_xupd_dev(int64_t n, T *__restrict__ x, VPtrs<T> Z, const DevFG *__restrict__ F) {
+    const int nc = F->ncols;
+    if (nc <= 0) return;
+    T yv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) yv[q] = q < nc ? (T)F->y[q] : T(0);
+    GRID_STRIDE(c, n) {
+        T a = x[c];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (q < nc) a += yv[q] * Z.p[q][c];
+        x[c] = a;
+    }
+}
+
+__global__ void k_zero_if(int64_t n, double *__restrict__ x, const int *__restrict__ flag) {
+    if (!*flag) return;
+    GRID_STRIDE(c, n) x[c] = 0.0;
+}
+
+// phi += rn * ((double) d - mean) on FLUID and GHOST cells, rn from the control block
+__global__ void k_add_scaled_dev(int64_t n, const uint8_t *__restrict__ type, double *__restrict__ phi,
+                                 const float *__restrict__ d, const DevFG *__restrict__ R,
+                                 const double *__restrict__ mean) {
+    const double a = R->rn, m = *mean;
+    GRID_STRIDE(c, n) if (type[c] != DEAD) phi[c] += a * ((double)d[c] - m);
+}
+
+__global__ void k_fg_setup(DevFG *F, const double *bn2, double rtol, int maxit) {
+    const double bnorm = sqrt(*bn2);
+    F->bnorm = bnorm;
+    F->zero = !(bnorm > 1e-300);
+    F->rtol = rtol;
+    F->maxit = maxit;
+    F->outer = 0;
+    F->cycles = 0;
+    F->single = 0;
+    F->status = 0;
+    F->rel = 0.0;
+    F->refinements = 0;
+    F->stalls = 0;
+    F->steps = 0;
+    F->stop = 0;
+    F->last_rel = 1e300;
+    F->ncols = 0;
+}
+
+__global__ void k_copy_inner_rtol(DevFG *R, double v) { R->inner_rtol = v; }
+
+// restart test at the top of a cycle: beta = ||r||, rel = beta / bnorm
+__global__ void k_fg_cycle(DevFG *F, const double *rn2, cudaGraphConditionalHandle h) {
+    const double beta = sqrt(*rn2);
+    F->rel = F->zero ? 0.0 : beta / F->bnorm;
+    if (!isfinite(F->rel)) F->status = IBM_ERR_DIVERGED;
+    int go = !F->zero && F->status == 0 && F->rel > F->rtol && !(F->single && F->cycles > 0);
+    if (go && F->outer >= F->maxit) {
+        go = 0;
+        F->status = IBM_ERR_NOT_CONVERGED;
+    }
+    F->go = go;
+    if (go) {
+        F->cycles += 1;
+        for (int i = 0; i < 17; ++i) F->g[i] = 0.0;
+        F->g[0] = beta;
+        F->scale = 1.0 / beta;
+        F->jlast = -1;
+        F->active = 1;
+        F->ncols = 0;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// after the first Gram-Schmidt pass of step j: h in md[0..j], ||w||^2 before
+// in md[j+1], after in *wa2; a second pass when the norm dropped by more
+// than a factor 0.7
+__global__ void k_fg_post1(DevFG *F, const double *md, const double *wa2, int j) {
+    for (int i = 0; i <= j; ++i) F->hcol[i] = md[i];
+    F->wb = md[j + 1];
+    F->wa = *wa2;
+    F->reorth = F->wa <= 0.49 * F->wb;
+}
+
+__global__ void k_fg_post2(DevFG *F, const double *md, const double *wa2, int j) {
+    for (int i = 0; i <= j; ++i) F->hcol[i] += md[i];
+    F->wa = *wa2;
+}
+
+// Hessenberg column j, Givens rotations, residual estimate and the decision
+// to take step j + 1
+__global__ void k_fg_givens(DevFG *F, int j, int m) {
+    const double hn = sqrt(F->wa);
+    F->outer += 1;
+    double *H = F->H;
+    for (int i = 0; i <= j; ++i) H[i * m + j] = F->hcol[i];
+    H[(j + 1) * m + j] = hn;
+    if (!isfinite(hn)) {
+        F->status = IBM_ERR_DIVERGED;
+        F->active = 0;
+        return;
+    }
+    for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], b = H[(i + 1) * m + j];
+        H[i * m + j] = F->cs[i] * a + F->sn[i] * b;
+        H[(i + 1) * m + j] = -F->sn[i] * a + F->cs[i] * b;
+    }
+    const double a = H[j * m + j], b = H[(j + 1) * m + j];
+    const double rho = hypot(a, b);
+    F->cs[j] = rho > 0 ? a / rho : 1.0;
+    F->sn[j] = rho > 0 ? b / rho : 0.0;
+    H[j * m + j] = rho;
+    H[(j + 1) * m + j] = 0.0;
+    F->g[j + 1] = -F->sn[j] * F->g[j];
+    F->g[j] = F->cs[j] * F->g[j];
+    F->jlast = j;
+    const double est = fabs(F->g[j + 1]) / F->bnorm;
+    F->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+    F->active = !(est <= F->rtol || hn == 0.0) && F->outer < F->maxit && j + 1 < m;
+}
+
+// back substitution H y = g over the steps taken
+__global__ void k_fg_ysolve(DevFG *F, int m) {
+    const int jl = F->jlast;
+    if (F->status != 0 || jl < 0) {
+        if (F->status == 0) F->status = IBM_ERR_NOT_CONVERGED;
+        F->ncols = 0;
+        return;
+    }
+    for (int i = jl; i >= 0; --i) {
+        double s = F->g[i];
+        for (int k = i + 1; k <= jl; ++k) s -= F->H[i * m + k] * F->y[k];
+        F->y[i] = s / F->H[i * m + i];
+    }
+    F->ncols = jl + 1;
+}
+
+// refinement test: rel = ||P(b - A phi)|| / ||b||; sets up the FP32 cycle
+__global__ void k_ref_start(DevFG *R, DevFG *F, const double *rn2, cudaGraphConditionalHandle h) {
+    const double rn = sqrt(*rn2);
+    R->rn = rn;
+    R->rel = R->zero ? 0.0 : rn / R->bnorm;
+    if (!isfinite(R->rel)) R->status = IBM_ERR_DIVERGED;
+    int go = !R->zero && R->status == 0 && !R->stop && R->rel > R->rtol;
+    if (go && (R->steps >= R->maxit || R->refinements >= 256)) {
+        go = 0;
+        R->status = IBM_ERR_NOT_CONVERGED;
+    }
+    if (go) {
+        R->refinements += 1;
+        R->scale = 1.0 / rn;
+        F->bnorm = 1.0;
+        F->zero = 0;
+        F->rtol = fmax(R->inner_rtol, 0.5 * R->rtol / R->rel);
+        F->maxit = R->maxit - R->steps;
+        F->outer = 0;
+        F->cycles = 0;
+        F->single = 1;
+        F->status = 0;
+        F->ncols = 0;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_ref_after(DevFG *R, const DevFG *F) {
+    R->steps += F->outer;
+    if (F->outer == 0) {
+        R->status = IBM_ERR_NOT_CONVERGED;
+        R->stop = 1;
+        return;
+    }
+    if (R->refinements > 1 && !(R->rel < 0.999 * R->last_rel)) R->stalls += 1;
+    else R->stalls = 0;
+    if (R->stalls >= 3) {
+        R->status = IBM_ERR_NOT_CONVERGED;
+        R->stop = 1;
+    }
+    R->last_rel = R->rel;
+}
+
+// ||x||^2 into scal[slot] without a host read
+template <typename T>
+static ibm_status norm2_dev(Ctx *c, const T *x, int slot) {
+    KL(-1, k_dotT<T>, c->nred, RED_THREADS, c->N, x, x, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + slot));
+    return IBM_OK;
+}
+
+// one restart cycle of device-controlled FGMRES on control block F (the
+// cycle's residual r must be in K.r and F->scale = 1 / ||r||), then x update
+template <typename T>
+static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
+    const int64_t n = c->N;
+    const int m = c->opts.restart;
+    VPtrs<T> vp{}, zp{};
+    for (int i = 0; i <= m && i < 17; ++i) vp.p[i] = K.V[i];
+    for (int i = 0; i < m; ++i) zp.p[i] = K.Z[i];
+    for (int j = 0; j < m; ++j) {
+        cudaGraphConditionalHandle hj, hr;
+        IBM_TRY(cond_handle(c, &hj));
+        KL(-1, k_set_cond, 1, 1, hj, &F->active);
+        CondScope sj;
+        IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hj, &sj));
+        {
+            // V_j = (j == 0 ? r : w) / norm
+            KL(-1, (k_scale_dev<T, T>), c->nred, RED_THREADS, n, K.V[j], j == 0 ? K.r : K.w, &F->scale);
+            IBM_TRY(precond<T>(c, *K.H, K.V[j], K.Z[j]));
+            IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
+            KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w, vp,
+               c->part);
+            IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
+            KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
+               vp, c->scal + S_MD, c->part);
+            IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
+            KL(-1, k_fg_post1, 1, 1, F, c->scal + S_MD, c->scal + S_TMP, j);
+            IBM_TRY(cond_handle(c, &hr));
+            KL(-1, k_set_cond, 1, 1, hr, &F->reorth);
+            CondScope sr;
+            IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hr, &sr));
+            {
+                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
+                   vp, c->part);
+                IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
+                KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
+                   K.w, vp, c->scal + S_MD, c->part);
+                IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
+                KL(-1, k_fg_post2, 1, 1, F, c->scal + S_MD, c->scal + S_TMP, j);
+            }
+            IBM_TRY(cond_close(c, &sr));
+            KL(-1, k_fg_givens, 1, 1, F, j, m);
+        }
+        IBM_TRY(cond_close(c, &sj));
+    }
+    KL(-1, k_fg_ysolve, 1, 1, F, m);
+    KL(-1, k_xupd_dev<T>, c->nred, RED_THREADS, n, x, zp, F);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+// FP64 FGMRES(m) with restarts, all on the device (control block 0)
+static ibm_status fgmres64_dev(Ctx *c, double *x, DevFG *F) {
+    Krylov<double> K = kry64(c);
+    cudaGraphConditionalHandle hw;
+    IBM_TRY(cond_handle(c, &hw));
+    IBM_TRY(apply_PA<double>(c, x, c->b, -1.0, K.r));
+    IBM_TRY(norm2_dev<double>(c, K.r, S_TMP));
+    KL(-1, k_fg_cycle, 1, 1, F, c->scal + S_TMP, hw);
+    CondScope sw;
+    IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, hw, &sw));
+    {
+        IBM_TRY(fgmres_dev_cycle<double>(c, K, x, F));
+        IBM_TRY(apply_PA<double>(c, x, c->b, -1.0, K.r));
+        IBM_TRY(norm2_dev<double>(c, K.r, S_TMP));
+        KL(-1, k_fg_cycle, 1, 1, F, c->scal + S_TMP, hw);
+    }
+    IBM_TRY(cond_close(c, &sw));
+    return IBM_OK;
+}
+
+// FP64 defect correction around one FP32 FGMRES cycle per pass (control
+// blocks 0: refinement, 1: FP32 cycle)
+static ibm_status mixed_dev(Ctx *c, double *phi, DevFG *R, DevFG *F) {
+    const int64_t n = c->N;
+    Krylov<float> K = kry32(c);
+    cudaGraphConditionalHandle hr;
+    IBM_TRY(cond_handle(c, &hr));
+    IBM_TRY(apply_PA<double>(c, phi, c->b, -1.0, c->rr));
+    IBM_TRY(norm2_dev<double>(c, c->rr, S_TMP));
+    KL(-1, k_ref_start, 1, 1, R, F, c->scal + S_TMP, hr);
+    CondScope sr;
+    IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, hr, &sr));
+    {
+        KL(-1, (k_scale_dev<float, double>), c->nred, RED_THREADS, n, c->b32, c->rr, &R->scale);
+        IBM_CUDA(c, cudaMemsetAsync(c->d32, 0, sizeof(float) * n, c->s));
+        // the FP32 cycle: r32 = P(b32 - A d32), then one restart cycle if needed
+        cudaGraphConditionalHandle hi;
+        IBM_TRY(cond_handle(c, &hi));
+        IBM_TRY(apply_PA<float>(c, c->d32, c->b32, -1.0f, K.r));
+        IBM_TRY(norm2_dev<float>(c, K.r, S_TMP));
+        KL(-1, k_fg_cycle, 1, 1, F, c->scal + S_TMP, hi);
+        CondScope si;
+        IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hi, &si));
+        IBM_TRY(fgmres_dev_cycle<float>(c, K, c->d32, F));
+        IBM_TRY(cond_close(c, &si));
+        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+        KL(-1, k_add_scaled_dev, c->nred, RED_THREADS, n, c->type, phi, c->d32, R, c->scal + S_MEAN);
+        KL(-1, k_ref_after, 1, 1, R, F);
+        IBM_TRY(apply_PA<double>(c, phi, c->b, -1.0, c->rr));
+        IBM_TRY(norm2_dev<double>(c, c->rr, S_TMP));
+        KL(-1, k_ref_start, 1, 1, R, F, c->scal + S_TMP, hr);
+    }
+    IBM_TRY(cond_close(c, &sr));
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+// buffers and control blocks the captured solve needs (outside capture)
+ibm_status poisson_dev_prepare(Ctx *c) {
+    if ((c->opts.precision == IBM_FP64 && !c->mg64.built) || (c->opts.precision == IBM_MIXED && !c->mg32.built))
+        IBM_TRY(mg_build(c));
+    if (c->opts.precision == IBM_MIXED) IBM_TRY(ensure_mixed(c));
+    else IBM_TRY(alloc_krylov(c, c->opts.restart));
+    if (!c->dctl) {
+        c->dctl = dev_alloc(c, sizeof(DevFG) * 2);
+        c->dstats = dev_alloc(c, sizeof(DevStats));
+        if (!c->dctl || !c->dstats) return c->fail(IBM_ERR_OOM, "control block allocation failed");
+        IBM_CUDA(c, cudaMemsetAsync(c->dctl, 0, sizeof(DevFG) * 2, c->s));
+        IBM_CUDA(c, cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->s));
+    }
+    return IBM_OK;
+}
+
+// the Poisson solve of poisson_solve with device-side control; capturable
+ibm_status poisson_solve_dev(Ctx *c, const double *rhs, double *phi, double rtol, int maxit) {
+    const int64_t n = c->N;
+    DevFG *R = dfg(c, 0), *F = dfg(c, 1);
+    KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, rhs, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
+    if (c->ng > 0) KL(-1, k_zero_at, (unsigned)((c->ng + 255) / 256), 256, c->ng, c->gidx, c->b);
+    IBM_TRY(norm2_dev<double>(c, c->b, S_TMP));
+    KL(-1, k_fg_setup, 1, 1, R, c->scal + S_TMP, rtol, maxit);
+    IBM_LAUNCHED(c);
+    if (c->opts.precision == IBM_MIXED) {
+        KL(-1, k_copy_inner_rtol, 1, 1, R, c->opts.mixed_inner_rtol);
+        IBM_TRY(mixed_dev(c, phi, R, F));
+    } else {
+        IBM_TRY(fgmres64_dev(c, phi, R));
+    }
+    KL(-1, k_zero_if, c->nred, RED_THREADS, n, phi, &R->zero);
+    KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, phi, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+// per-step statistics of the captured step: Poisson iterations and status,
+// Helmholtz sweeps (hsw[0..2], status in hsw[3]), ghost refresh status
+__global__ void k_step_stats(DevStats *S, const DevFG *R, const int *hsw) {
+    S->steps += 1;
+    S->outer += R->refinements > 0 ? R->steps : R->outer;
+    S->helm_sweeps += hsw[0] + hsw[1] + hsw[2];
+    S->rel = R->rel;
+    int st = R->status;
+    if (hsw[3] != 0 && (st == 0 || hsw[3] == IBM_ERR_DIVERGED)) st = hsw[3];
+    if (st == IBM_ERR_DIVERGED || S->status == 0) S->status = st ? st : S->status;
+}
+
+ibm_status step_stats_dev(Ctx *c, const int *hsw) {
+    KL(-1, k_step_stats, 1, 1, (DevStats *)c->dstats, dfg(c, 0), hsw);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+ibm_status step_stats_read(Ctx *c, ibm_step_stats *st) {
+    DevStats h{};
+    IBM_CUDA(c, cudaMemcpyAsync(&h, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    IBM_CUDA(c, cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->s));
+    if (st) {
+        st->steps += h.steps;
+        st->poisson_outer += h.outer;
+        st->poisson_inner += h.outer;
+        st->helm_sweeps += h.helm_sweeps;
+        if (h.steps > 0) st->rel_residual = h.rel;
+    }
+    if (h.status == IBM_ERR_DIVERGED) return c->fail(IBM_ERR_DIVERGED, "a solve in the step produced a non-finite value");
+    if (h.status == IBM_ERR_NOT_CONVERGED) {
+        c->fail(IBM_ERR_NOT_CONVERGED, "a solve in the step reached its iteration limit");
+        return IBM_ERR_NOT_CONVERGED;
+    }
+    return IBM_OK;
+}
+
 ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, int maxit, ibm_solve_stats *st) {
     if ((c->opts.precision == IBM_FP64 && !c->mg64.built) || (c->opts.precision == IBM_MIXED && !c->mg32.built))
         IBM_TRY(mg_build(c));
     const int64_t n = c->N;
-    IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
+    IBM_CUDA(c, cudaEventRecord(c->ev4, c->s));
     // b = P rhs on FLUID rows, 0 elsewhere
-    KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, rhs, c->part);
-    IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, rhs, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
+    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     // GHOST rows of b are 0 (homogeneous Neumann on the body)
     if (c->ng > 0) {
@@ -1823,16 +2328,16 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
         else status = fgmres<double>(c, kry64(c), phi, c->b, bnorm, rtol, maxit, false, &outer, &inner, &rel);
         if (status != IBM_OK && status != IBM_ERR_NOT_CONVERGED) return status;
         // normalise: zero volume-weighted FLUID mean, shift ghosts too
-        KL(-1, k_fluid_volsum, RED_BLOCKS, RED_THREADS, c->g, c->type, phi, c->part);
-        IBM_TRY(finalize(c, c->part, RED_BLOCKS, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-        KL(-1, k_sub_mean, RED_BLOCKS, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
+        KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, phi, c->part);
+        IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+        KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
         IBM_LAUNCHED(c);
     }
     IBM_TRY(kt_flush(c));
-    IBM_CUDA(c, cudaEventRecord(c->ev1, c->s));
-    IBM_CUDA(c, cudaEventSynchronize(c->ev1));
+    IBM_CUDA(c, cudaEventRecord(c->ev5, c->s));
+    IBM_CUDA(c, cudaEventSynchronize(c->ev5));
     float ms = 0.f;
-    IBM_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    IBM_CUDA(c, cudaEventElapsedTime(&ms, c->ev4, c->ev5));
     if (st) {
         st->outer_iters = outer;
         st->inner_iters = inner;

@@ -1,12 +1,18 @@
 """Batched ensemble of independent cases of uneven size on one GPU.
 
-The cases run through the request loop of include/ibm_serve.h: all of them
-stay resident while they advance, `slots` at a time, each slot on its own
-stream so their kernels overlap on the device, and each case's multigrid
-V-cycle replays as one captured CUDA graph. Options are picked per size
-class (cell count rounded to a power of two) by the library's autotuner,
-which times candidate tile widths and smoother sweep counts on the first
-case of each class.
+run_graphs (the batched path): every case is resident on its own stream
+with its fractional step captured as CUDA graphs whose loops (Helmholtz
+sweeps, ghost refresh, FGMRES and mixed-precision refinement) are decided on
+the device (opts graph=2); one host thread enqueues all steps of all cases
+with ibm_step_async and the GPU runs the cases' graphs concurrently, with
+no host round trip inside a step.
+
+run (the request-loop path): the cases go through include/ibm_serve.h,
+`slots` at a time, each slot a host worker thread driving its case.
+
+Options are picked per size class (cell count rounded to a power of two) by
+the library's autotuner, which times candidate multigrid tile widths and
+smoother sweep counts on the first case of each class.
 """
 from __future__ import annotations
 
@@ -78,3 +84,45 @@ def run(cases, slots=12, precision=ibm.IBM_MIXED, tuned=None):
     return {"results": out, "ok": ok, "makespan_s": last - first, "wall_s": wall,
             "mcell_steps_per_s": work / (last - first) / 1e6, "cell_steps": work,
             "peak_running": st["peak_running"]}
+
+
+def _opts_kw(o):
+    return {k: getattr(o, k) for k, _ in ibm.ibm_solver_opts._fields_}
+
+
+def run_graphs(cases, precision=ibm.IBM_MIXED, tuned=None):
+    """All cases resident at once, each on its own stream; the step graphs
+    are captured during setup (ibm_step_prepare), then every case's steps
+    are enqueued from this thread and run concurrently on the device."""
+    import torch
+    from . import synth
+    order = sorted(range(len(cases)), key=lambda i: -cases[i].ncells)
+    solvers = {}
+    t0 = time.perf_counter()
+    for i in order:
+        c = cases[i]
+        s = ibm.Solver(c, precision=precision, stream=torch.cuda.Stream())
+        kw = _opts_kw(tuned[size_class(c)][0]) if tuned and size_class(c) in tuned else {}
+        kw.update(precision=precision, graph=2)
+        s.set_opts(**kw)
+        for v, e in synth.case_bodies(c):
+            s.set_body(v, e)
+        s.classify()
+        s.step_prepare()
+        solvers[i] = s
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for i in order:
+        solvers[i].step_async(cases[i].nsteps)
+    enqueue_s = time.perf_counter() - t1
+    res = {i: solvers[i].step_wait() for i in order}
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t1
+    out = [res[i] for i in range(len(cases))]
+    work = sum(cases[i].ncells * out[i]["steps"] for i in range(len(cases)))
+    ok = all(r["status"] == ibm.IBM_OK for r in out)
+    for s in solvers.values():
+        s.close()
+    return {"results": out, "ok": ok, "wall_s": wall, "setup_s": setup_s, "enqueue_s": enqueue_s,
+            "mcell_steps_per_s": work / wall / 1e6, "cell_steps": work}

@@ -96,7 +96,7 @@ class ibm_server_stats(Structure):
                 ("peak_admitted_bytes", c_size_t)]
 
 
-EXPORTS = ["ibm_tune", "ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
+EXPORTS = ["ibm_step_async", "ibm_step_wait", "ibm_step_prepare", "ibm_tune", "ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
            "ibm_server_destroy",
            "ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
@@ -140,6 +140,9 @@ def load_library(path: str = LIB_PATH):
     L.ibm_server_wait.argtypes = [P, c_int64, c_double, POINTER(ibm_result)]
     L.ibm_server_get_stats.argtypes = [P, POINTER(ibm_server_stats)]
     L.ibm_server_destroy.argtypes = [P]
+    L.ibm_step_async.argtypes = [P, c_int]
+    L.ibm_step_wait.argtypes = [P, POINTER(ibm_step_stats)]
+    L.ibm_step_prepare.argtypes = [P]
     L.ibm_tune.argtypes = [POINTER(ibm_grid_desc), c_int, P, P, P, P, POINTER(ibm_solver_opts), c_int, c_int,
                            POINTER(c_int), P]
     for name in EXPORTS:
@@ -345,6 +348,21 @@ class Solver:
 
     def step(self, n=1):
         st, status = ibm_step(self.ctx, n)
+        out = {k: getattr(st, k) for k, _ in ibm_step_stats._fields_}
+        out["status"] = status
+        return out
+
+    def step_async(self, n=1):
+        """Enqueue n steps (captured graphs with opts graph=2) without waiting."""
+        return _check(load_library().ibm_step_async(self.ctx, int(n)), self.ctx)
+
+    def step_prepare(self):
+        """Capture the step graphs now (opts graph=2), outside any timed region."""
+        return _check(load_library().ibm_step_prepare(self.ctx), self.ctx)
+
+    def step_wait(self):
+        st = ibm_step_stats()
+        status = _check(load_library().ibm_step_wait(self.ctx, byref(st)), self.ctx, ok=(IBM_OK, IBM_ERR_NOT_CONVERGED))
         out = {k: getattr(st, k) for k, _ in ibm_step_stats._fields_}
         out["status"] = status
         return out

@@ -85,3 +85,85 @@ def test_ensemble_runs_every_case():
     assert out["ok"], [r["error"] for r in out["results"]]
     assert all(r["steps"] == 3 and r["step"]["rel_residual"] <= 1e-10 for r in out["results"])
     assert out["peak_running"] >= 2
+
+
+def _steps(case, precision, graph, n, stream, asynchronous=False, prepare=False):
+    s = ibm.Solver(case, precision=precision, stream=stream)
+    s.set_opts(precision=precision, graph=graph)
+    for v, e in synth.case_bodies(case):
+        s.set_body(v, e)
+    s.classify()
+    if prepare:
+        s.step_prepare()
+    if asynchronous:
+        s.step_async(n)
+        r = s.step_wait()
+    else:
+        r = s.step(n)
+    out = {k: s.get(k) for k in (("u", "v", "w", "p") if case.ndim == 3 else ("u", "v", "p"))}
+    s.close()
+    return r, out
+
+
+@pytest.mark.parametrize("precision", [ibm.IBM_FP64, ibm.IBM_MIXED])
+@pytest.mark.parametrize("which", ["cylinder", "spheres"])
+def test_device_controlled_step_matches_host_driven(precision, which):
+    """The captured step (every loop decided on the device) takes the same
+    kernels and stopping tests as the host-driven step; only the Givens
+    rotations are evaluated on the device instead of the host, so the fields
+    agree to rounding and the iteration counts exactly."""
+    case = (synth.cylinder_case(160, 80, 256, nsteps=4) if which == "cylinder" else
+            synth.multi_sphere_case(32, [(0.5, (0.5, 0.0, 0.0)), (0.4, (2.5, 0.3, 0.0))], 250.0, nsteps=4, level=3))
+    st = torch.cuda.Stream()
+    r0, a = _steps(case, precision, 0, 4, st)
+    r2, b = _steps(case, precision, 2, 4, st)
+    assert r0["status"] == ibm.IBM_OK and r2["status"] == ibm.IBM_OK
+    assert r2["steps"] == 4 and r2["poisson_outer"] == r0["poisson_outer"]
+    assert r2["helm_sweeps"] == r0["helm_sweeps"]
+    assert r2["rel_residual"] <= 1e-10
+    for k in a:
+        assert np.abs(a[k] - b[k]).max() <= 1e-11 * np.abs(a[k]).max(), k
+
+
+def test_async_steps_and_prepared_graphs():
+    case = synth.cylinder_case(128, 64, 128, nsteps=5)
+    st = torch.cuda.Stream()
+    r1, a = _steps(case, ibm.IBM_MIXED, 2, 5, st)
+    r2, b = _steps(case, ibm.IBM_MIXED, 2, 5, st, asynchronous=True, prepare=True)
+    assert r2["status"] == ibm.IBM_OK and r2["steps"] == 5
+    assert r2["poisson_outer"] == r1["poisson_outer"]
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_device_controlled_step_recaptures_after_option_change():
+    case = synth.cylinder_case(128, 64, 128, nsteps=4)
+    st = torch.cuda.Stream()
+    s = ibm.Solver(case, precision=ibm.IBM_MIXED, stream=st)
+    s.set_opts(precision=ibm.IBM_MIXED, graph=2)
+    s.set_body(case.verts, case.elems)
+    s.classify()
+    s.step(2)
+    s.set_opts(precision=ibm.IBM_MIXED, graph=2, nu1=1, nu2=1, tile_x=64)
+    r = s.step(2)
+    assert r["status"] == ibm.IBM_OK and r["steps"] == 2 and r["rel_residual"] <= 1e-10
+    u = s.get("u")
+    s.close()
+    ref = ibm.Solver(case, precision=ibm.IBM_MIXED, stream=st)
+    ref.set_opts(precision=ibm.IBM_MIXED, graph=0)
+    ref.set_body(case.verts, case.elems)
+    ref.classify()
+    ref.step(2)
+    ref.set_opts(precision=ibm.IBM_MIXED, graph=0, nu1=1, nu2=1, tile_x=64)
+    ref.step(2)
+    assert np.array_equal(u, ref.get("u"))
+    ref.close()
+
+
+def test_graph_ensemble_runs_every_case():
+    cases = synth.ensemble_2d(8, seed=5)
+    for c in cases:
+        c.nsteps = 4
+    out = ensemble.run_graphs(cases)
+    assert out["ok"], [r["status"] for r in out["results"]]
+    assert all(r["steps"] == 4 and r["rel_residual"] <= 1e-10 for r in out["results"])
