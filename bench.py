@@ -72,6 +72,8 @@ def parse():
                     help="requests of the 3D multi-sphere serving stream to replay (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=4, help="cases resident at once in the serving leg")
     ap.add_argument("--serve-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--compare", default="192,128,128",
+                    help="wing grid of the Poisson solver comparison ('' to skip)")
     ap.add_argument("--ensemble", type=int, default=64,
                     help="cases of the seeded 2D ensemble to run, 50 steps each (0: skip)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -239,6 +241,35 @@ def serve_leg(nreq, slots, precision):
             "workload": "seeded stream: Poisson arrivals 50/s; 1-8 icospheres (5120 triangles each, radii "
                         "0.2-0.6) in [-4,8]x[-3,3]^2; n^3 grids, log n uniform in [log 64, log 256], n a "
                         "multiple of 16; Re 100-500; CFL 0.2; 10 steps per request; Poisson rtol 1e-10"}
+
+
+def compare_leg(size):
+    """Poisson solvers on the same right-hand side (the wing's second step
+    on a smaller grid, from phi = 0, FP64, to a 1e-10 relative residual):
+    the paper's BiCGStab with scheduled relaxation Jacobi, BiCGStab with the
+    multigrid V-cycle, FGMRES with either."""
+    import numpy as np
+    import torch
+    from paper_2505_17287_gb300 import ibm
+    case = wing_case(size)
+    s = ibm.Solver(case)
+    s.set_body(case.verts, case.elems)
+    s.classify()
+    s.step(2)
+    rhs = torch.from_numpy(s.get("rhs").ravel()).cuda()
+    out = {"grid": size.replace(",", "x"), "cells": s.N, "rtol": 1e-10}
+    for name, kw in (("fgmres_mg", dict(outer=ibm.IBM_OUTER_FGMRES, precond=0)),
+                     ("bicgstab_mg", dict(outer=ibm.IBM_OUTER_BICGSTAB, precond=0)),
+                     ("bicgstab_srj", dict(outer=ibm.IBM_OUTER_BICGSTAB, precond=1)),
+                     ("fgmres_srj", dict(outer=ibm.IBM_OUTER_FGMRES, precond=1))):
+        s.set_opts(**kw)
+        phi = torch.zeros_like(rhs)
+        torch.cuda.synchronize()
+        st = s.poisson_solve(rhs, phi, rtol=1e-10, maxit=4000)
+        out[name] = {"iterations": st["outer_iters"], "ms": st["ms"], "rel_residual": st["rel_residual"],
+                     "status": ibm.STATUS_NAMES.get(st["status"], st["status"])}
+    s.close()
+    return out
 
 
 def ensemble_leg(ncases):
@@ -417,6 +448,10 @@ def main():
         except Exception as e:  # the oracle is optional on a box without it
             result["cpu_baseline"] = {"value": None, "error": str(e)}
     s.close()
+    if rank == 0 and args.compare:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        result["solver_compare"] = compare_leg(args.compare)
     if rank == 0 and args.ensemble > 0:
         torch.cuda.synchronize()
         torch.cuda.empty_cache()

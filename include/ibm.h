@@ -115,6 +115,15 @@ typedef struct {
                            timer runs); 2: the whole fractional step is one captured
                            graph with device-side loop control (ibm_step_async);
                            0: launched kernel by kernel */
+    int precond;        /* Poisson preconditioner: 0 multigrid V-cycle; 1 scheduled
+                           relaxation Jacobi (SRJ): srj_sweeps damped-Jacobi sweeps of
+                           the same staircase operator from a zero guess, relaxation
+                           factors 1/tau_k with tau_k the Chebyshev points of
+                           [srj_lmin, 2] (Section 2.1 names SRJ as the preconditioner
+                           of its BiCGStab) */
+    int srj_sweeps;     /* SRJ sweeps per preconditioner call, 1..64 */
+    double srj_lmin;    /* lower end of the damped interval of the Jacobi-scaled
+                           spectrum, in [0, 2); 0 = 2 / srj_sweeps^2 */
 } ibm_solver_opts;
 
 typedef struct {
@@ -171,7 +180,7 @@ enum {
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
-   tile_x 128, graph 1. */
+   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

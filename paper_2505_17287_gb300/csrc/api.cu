@@ -109,6 +109,9 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->mg_interp = 1;
     o->tile_x = 128;
     o->graph = 1;
+    o->precond = 0;
+    o->srj_sweeps = 16;
+    o->srj_lmin = 0.0;
     return IBM_OK;
 }
 
@@ -132,6 +135,9 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
         return false;
     }
     if (o->graph < 0 || o->graph > 2) { why = "graph must be 0, 1 or 2"; return false; }
+    if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 (multigrid) or 1 (SRJ)"; return false; }
+    if (o->srj_sweeps < 1 || o->srj_sweeps > 64) { why = "srj_sweeps must be in [1, 64]"; return false; }
+    if (!(o->srj_lmin >= 0.0 && o->srj_lmin < 2.0)) { why = "srj_lmin must be in [0, 2)"; return false; }
     return true;
 }
 

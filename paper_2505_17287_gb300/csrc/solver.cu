@@ -1419,6 +1419,73 @@ static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H) {
     return IBM_OK;
 }
 
+// Scheduled relaxation Jacobi on the staircase operator K of level 0:
+// x_new = x + w (f + sum T x_nb - D x) / D on active cells, from x = 0, with
+// relaxation factors w_k = 1 / tau_k, tau_k the Chebyshev points of
+// [lmin, 2] (the Jacobi-scaled spectrum of K lies in [0, 2]), taken in
+// bit-reversed order so large and small factors alternate. A fixed linear
+// operator: usable as the right preconditioner of BiCGStab.
+template <typename T, bool FINE>
+__global__ void k_srj_sweep(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, T *__restrict__ xn, T w) {
+    GRID_STRIDE(c, L.n) {
+        T v = T(0);
+        if (active<T, FINE>(L, c)) {
+            const uint32_t t = L.fnx.div((uint32_t)c);
+            const int i = (int)((uint32_t)c - t * (uint32_t)L.nx);
+            const uint32_t kk = L.fny.div(t);
+            const int j = (int)(t - kk * (uint32_t)L.ny), k = (int)kk;
+            T d;
+            const T s = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+            if (!FINE) d = L.d[c];
+            const T xc = x[c];
+            v = d > T(0) ? xc + w * ((f[c] + s) / d - xc) : xc;
+        }
+        xn[c] = v;
+    }
+}
+
+std::vector<double> srj_factors(int m, double lmin) {
+    if (!(lmin > 0.0)) lmin = 2.0 / ((double)m * m);
+    const double lmax = 2.0, pi = 3.14159265358979323846;
+    std::vector<double> w(m);
+    for (int k = 0; k < m; ++k) {
+        const double tau = 0.5 * (lmax + lmin) + 0.5 * (lmax - lmin) * cos(pi * (2.0 * k + 1.0) / (2.0 * m));
+        w[k] = 1.0 / tau;
+    }
+    // bit-reversed order when m is a power of two
+    if ((m & (m - 1)) == 0) {
+        int bits = 0;
+        while ((1 << bits) < m) ++bits;
+        std::vector<double> o(m);
+        for (int k = 0; k < m; ++k) {
+            int r = 0;
+            for (int b = 0; b < bits; ++b)
+                if (k & (1 << b)) r |= 1 << (bits - 1 - b);
+            o[r] = w[k];
+        }
+        return o;
+    }
+    return w;
+}
+
+template <typename T>
+static ibm_status srj(Ctx *c, MGHier<T> &H, const T *f, T **out) {
+    MGLevel<T> &L = H.lv[0];
+    const std::vector<double> w = srj_factors(c->opts.srj_sweeps, c->opts.srj_lmin);
+    T *x = H.px, *xn = H.pz;
+    IBM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(T) * (size_t)c->N, c->s));
+    for (size_t k = 0; k < w.size(); ++k) {
+        if (H.fine0) KL(K_RBGS0, (k_srj_sweep<T, true>), nblk(c->N), 256, L, f, x, xn, (T)w[k]);
+        else KL(K_RBGS0, (k_srj_sweep<T, false>), nblk(c->N), 256, L, f, x, xn, (T)w[k]);
+        T *t = x;
+        x = xn;
+        xn = t;
+    }
+    IBM_LAUNCHED(c);
+    *out = x;
+    return IBM_OK;
+}
+
 // MG-PCG with a fixed number of iterations: K x = f, with f in H.pr on
 // entry (it becomes the residual); the solution is left in H.px
 template <typename T>
@@ -1456,7 +1523,11 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     KL(-1, k_pre_in<T>, c->nred, RED_THREADS, c->g, oin, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     const T *xin = H.px;
-    if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
+    if (c->opts.precond == 1) {
+        T *xo = nullptr;
+        IBM_TRY(srj(c, H, H.pr, &xo));
+        xin = xo;
+    } else if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
         // one CG step is alpha times one V-cycle; FGMRES is invariant to
         // that scalar, so the V-cycle output is used directly
         // (the legacy default stream cannot be captured: launched directly there)

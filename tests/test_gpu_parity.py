@@ -89,6 +89,28 @@ def test_poisson_parity(name, precision):
     s.close()
 
 
+@pytest.mark.parametrize("name", ["ellipse_ragged", "sphere_ragged"])
+@pytest.mark.parametrize("precond", [0, 1])
+def test_poisson_parity_bicgstab(name, precond):
+    """The paper's own Poisson path (Section 2.1): BiCGStab, right
+    preconditioned by scheduled relaxation Jacobi (precond 1) or by the
+    multigrid V-cycle (0), reaches the oracle's discrete solution."""
+    import torch
+    case, T, g = _poisson_case(name)
+    rng = np.random.default_rng(11)
+    b = flow.project_rhs(g, T["type"], rng.uniform(-1, 1, g.shape))
+    phi_ref, _ = flow.solve_poisson(g, T["type"], T, b)
+    s = _solver(case, outer=ibm.IBM_OUTER_BICGSTAB, precond=precond, max_outer=6000)
+    rhs = torch.from_numpy(np.where(T["type"] == 0, b, -5.0).ravel()).cuda()
+    phi = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    st = s.poisson_solve(rhs, phi, rtol=1e-13, maxit=6000)
+    assert st["status"] == ibm.IBM_OK and st["rel_residual"] <= 1e-13, st
+    got = phi.cpu().numpy().reshape(g.shape)
+    err = np.linalg.norm(got - phi_ref) / np.linalg.norm(phi_ref)
+    assert err < 1e-9, err
+    s.close()
+
+
 def test_poisson_zero_rhs_gives_zero():
     import torch
     case, T, g = _poisson_case("ellipse_ragged")
