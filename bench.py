@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--serve-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--compare", default="192,128,128",
                     help="wing grid of the Poisson solver comparison ('' to skip)")
+    ap.add_argument("--ellipsoids", type=int, default=0,
+                    help="steps of the 208M-cell ellipsoid array to time per precision (0: skip)")
     ap.add_argument("--ensemble", type=int, default=64,
                     help="cases of the seeded 2D ensemble to run, 50 steps each (0: skip)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -272,6 +274,41 @@ def compare_leg(size):
     return out
 
 
+def ellipsoid_leg(nsteps):
+    """The 27-ellipsoid array on the 1300x400x400 grid (208M cells, the
+    paper's particulate-array case), FP64 and mixed: per step and per
+    Poisson outer iteration times after two warm-up steps."""
+    import torch
+    from paper_2505_17287_gb300 import ibm, synth
+    case = synth.ellipsoid_array_case()
+    out = {"grid": "1300x400x400", "cells": case.ncells, "bodies": case.meta["nbodies"],
+           "triangles": case.meta["ntri"], "Re": case.Re, "dt": case.dt}
+    for name, prec in (("mixed", ibm.IBM_MIXED), ("fp64", ibm.IBM_FP64)):
+        s = ibm.Solver(case, precision=prec)
+        s.set_opts(precision=prec)
+        t0 = time.perf_counter()
+        for v, e in synth.case_bodies(case):
+            s.set_body(v, e)
+        info = s.classify()
+        setup = time.perf_counter() - t0
+        s.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = s.step(nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": case.ncells * nsteps / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / nsteps,
+                     "poisson_outer_per_step": st["poisson_outer"] / nsteps,
+                     "ms_per_poisson_iteration": st["ms_poisson"] / max(1, st["poisson_outer"]),
+                     "ms_poisson_per_step": st["ms_poisson"] / nsteps, "rel_residual_last": st["rel_residual"],
+                     "classify_s": setup, "n_ghost": info["n_ghost"], "status": st["status"]}
+        s.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def ensemble_leg(ncases):
     """The seeded 2D ensemble (ellipses and circles, grids 128x64 to
     1024x512, Re 50-200, CFL 0.2, 50 steps each) in mixed precision: options
@@ -448,6 +485,10 @@ def main():
         except Exception as e:  # the oracle is optional on a box without it
             result["cpu_baseline"] = {"value": None, "error": str(e)}
     s.close()
+    if rank == 0 and args.ellipsoids > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        result["ellipsoid_array"] = ellipsoid_leg(args.ellipsoids)
     if rank == 0 and args.compare:
         torch.cuda.synchronize()
         torch.cuda.empty_cache()

@@ -371,6 +371,41 @@ def multi_sphere_case(n: int, spheres, Re: float, nsteps: int = 10, level: int =
                 meta={"bodies": bodies, "n": n, "spheres": [(float(r), tuple(map(float, c))) for r, c in spheres]})
 
 
+def ellipsoid(center, semi=(0.5, 0.15, 0.15), pitch_deg: float = 15.0, level: int = 3):
+    """Closed triangulated ellipsoid: the unit icosphere scaled by the
+    semi-axes, pitched by `pitch_deg` about z (angle of attack in the x-y
+    plane), then translated (outward orientation is kept)."""
+    V1, T1 = _unit_icosphere(level)
+    V = V1 * np.asarray(semi, dtype=np.float64)
+    a = math.radians(pitch_deg)
+    c, s = math.cos(a), math.sin(a)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    return V @ R.T + np.asarray(center, dtype=np.float64), T1.copy()
+
+
+def ellipsoid_array_case(nx: int = 1300, ny: int = 400, nz: int = 400, Re: float = 10000.0, dt: float = 0.0005,
+                         nsteps: int = 5, level: int = 3, ratio: float = 1.01) -> Case:
+    """Array of 27 ellipsoids (major axis D = 1, axis ratio 1 : 0.3, pitched
+    15 degrees), 3 x 3 x 3 with centre spacing 1.5 D streamwise and 0.9 D
+    across, in the box [-3, 10] x [-2.5, 2.5]^2 (Section 3.3 shaped: the
+    paper's 1300 x 400 x 400 grid of 208M points, Re 10,000, dt 0.0005).
+    The grid is uniform over the array's bounding box plus 0.1 D and
+    stretched by `ratio` per cell outside it."""
+    bodies = []
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                bodies.append(ellipsoid((1.5 * i, 0.9 * (j - 1), 0.9 * (k - 1)), level=level))
+    allv = np.concatenate([v for v, _ in bodies])
+    lo, hi = allv.min(0) - 0.1, allv.max(0) + 0.1
+    xf = stretched_faces(-3.0, 10.0, nx, lo[0], hi[0], ratio)
+    yf = stretched_faces(-2.5, 2.5, ny, lo[1], hi[1], ratio)
+    zf = stretched_faces(-2.5, 2.5, nz, lo[2], hi[2], ratio)
+    return Case("ellipsoid_array", 3, xf, yf, zf, bodies[0][0], bodies[0][1], Re, dt, nsteps,
+                meta={"bodies": bodies, "nx": nx, "ny": ny, "nz": nz, "nbodies": len(bodies),
+                      "ntri": int(sum(len(e) for _, e in bodies))})
+
+
 def case_bodies(case: Case):
     """The (verts, elems) of every body of a case."""
     return case.meta.get("bodies") or [(case.verts, case.elems)]

@@ -27,17 +27,29 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def combined_mesh(case):
+    """All bodies of a case as one mesh, elements in the order the bodies
+    were added (the library numbers them the same way)."""
+    vs, es, off = [], [], 0
+    for v, e in synth.case_bodies(case):
+        vs.append(v)
+        es.append(e + off)
+        off += len(v)
+    return np.concatenate(vs), np.concatenate(es).astype(np.int32)
+
+
 def oracle_inside_columns(case, I, J):
     """Oracle inside flags on the columns I x J (all k), quantised with the
     parameters of the full grid."""
-    lo, s = geom.quant_params(3, case.xf, case.yf, case.zf, case.verts)
+    verts, elems = combined_mesh(case)
+    lo, s = geom.quant_params(3, case.xf, case.yf, case.zf, verts)
     xc, yc, zc = geom.centres(case.xf), geom.centres(case.yf), geom.centres(case.zf)
     Xq = geom.quantize(xc[I], lo[0], s)
     Yq = geom.quantize(yc[J], lo[1], s)
     Zq = geom.quantize(zc, lo[2], s)
-    V = np.ascontiguousarray(case.verts, dtype=np.float64)
+    V = np.ascontiguousarray(verts, dtype=np.float64)
     Vq = np.ascontiguousarray(np.stack([geom.quantize(V[:, a], lo[a], s) for a in range(3)], 1))
-    E = np.ascontiguousarray(case.elems, dtype=np.int32)
+    E = np.ascontiguousarray(elems, dtype=np.int32)
     out = np.zeros(len(I) * len(J) * len(zc), dtype=np.uint8)
     geom.lib().orc_inside_3d(len(I), len(J), len(zc), _p(Xq), _p(Yq), _p(Zq), _p(Vq), E.shape[0], _p(E), _p(out))
     return out.reshape(len(zc), len(J), len(I))
@@ -69,7 +81,8 @@ def check_tables(case, s, rng, nsample):
     assert np.array_equal(T["gidx"], np.nonzero(typ.ravel() == 1)[0])
     # ghost tables on a sample
     q = np.sort(rng.choice(T["gidx"].size, size=min(nsample, T["gidx"].size), replace=False))
-    ref = geom.ghost_tables(3, case.xf, case.yf, case.zf, typ, T["gidx"][q], case.verts, case.elems)
+    verts, elems = combined_mesh(case)
+    ref = geom.ghost_tables(3, case.xf, case.yf, case.zf, typ, T["gidx"][q], verts, elems)
     for k in ("base", "kind", "cmask", "sidx", "bi", "nrm", "ip", "dist", "wv", "wp", "bv", "bp"):
         assert np.array_equal(T[k][q], ref[k]), k
     return T
@@ -144,6 +157,24 @@ def test_wing_201m_mixed_step():
     s = ibm.Solver(case, precision=ibm.IBM_MIXED)
     s.set_opts(precision=ibm.IBM_MIXED)
     s.set_body(case.verts, case.elems)
+    info = s.classify()
+    assert info["n_ghost"] > 10000
+    T = check_tables(case, s, rng, 200)
+    out = s.step(1)
+    assert out["status"] == ibm.IBM_OK and out["rel_residual"] <= 1e-10, out
+    check_step(case, s, T, rng, nrows=2000)
+    s.close()
+
+
+def test_ellipsoid_array_208m_mixed_step():
+    """27 pitched ellipsoids on the 1300x400x400 grid (208,000,000 cells) of
+    the paper's particulate-array case, mixed precision, one GB300."""
+    case = synth.ellipsoid_array_case()
+    rng = np.random.default_rng(2026)
+    s = ibm.Solver(case, precision=ibm.IBM_MIXED)
+    s.set_opts(precision=ibm.IBM_MIXED)
+    for v, e in synth.case_bodies(case):
+        s.set_body(v, e)
     info = s.classify()
     assert info["n_ghost"] > 10000
     T = check_tables(case, s, rng, 200)
