@@ -328,6 +328,8 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     {
         const int64_t r = (c->N + 8 * RED_THREADS - 1) / (8 * RED_THREADS);
         c->nred = (int)(r < 1 ? 1 : (r > RED_BLOCKS ? RED_BLOCKS : r));
+        const int64_t w = (c->N + 2 * RED_THREADS - 1) / (2 * RED_THREADS);
+        c->nred_wide = (int)(w < 1 ? 1 : (w > RED_BLOCKS_MAX ? RED_BLOCKS_MAX : w));
         const int64_t e = (c->N + 255) / 256;
         c->nelem = (unsigned)(e < 1 ? 1 : (e > 152 * 16 ? 152 * 16 : e));
     }
@@ -401,7 +403,7 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     c->b = (double *)dev_alloc(c, nb);
     c->w = (double *)dev_alloc(c, nb);
     c->rr = (double *)dev_alloc(c, nb);
-    c->part = (double *)dev_alloc(c, sizeof(double) * RED_BLOCKS * 40);
+    c->part = (double *)dev_alloc(c, sizeof(double) * RED_BLOCKS_MAX * 40);
     c->scal = (double *)dev_alloc(c, sizeof(double) * 64);
     if (!c->p || !c->b || !c->w || !c->rr || !c->part || !c->scal) return c->fail(IBM_ERR_OOM, "solver vector allocation failed");
     IBM_CUDA(c, cudaMemsetAsync(c->p, 0, nb, c->s));

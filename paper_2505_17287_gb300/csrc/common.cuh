@@ -20,6 +20,11 @@ constexpr uint8_t FLUID = IBM_FLUID, GHOST = IBM_GHOST, DEAD = IBM_DEAD;
 // and a single block then adds the partials in a fixed order.
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 152 * 8;   // 8 blocks of 256 threads per SM on a 152-SM GB300
+// Reduction grids grow with the cell count up to RED_BLOCKS blocks (about
+// eight cells per thread); the FP32 operator product, whose threads
+// otherwise walk tens of cells on dependent loads, takes up to RED_BLOCKS_MAX.
+// The partial-sum buffer is sized for that maximum.
+constexpr int RED_BLOCKS_MAX = 152 * 32;
 
 // host-side status carrier: message + code
 struct Err {

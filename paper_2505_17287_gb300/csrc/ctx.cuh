@@ -167,10 +167,12 @@ struct Ctx {
     const double *sgraph_nold[NSGRAPH] = {nullptr};
     int64_t nlaunch = 0;   // kernels launched by this context so far
     // launch sizes that follow the grid: reduction kernels run nred blocks of
-    // RED_THREADS (at most RED_BLOCKS, about 8 cells per thread below that;
-    // a function of N only, so reductions stay deterministic), elementwise
+    // RED_THREADS (about 8 cells per thread, at most RED_BLOCKS; a function
+    // of N only, so reductions stay deterministic), the FP32 operator product
+    // nred_wide (about 2 cells per thread, at most RED_BLOCKS_MAX), elementwise
     // grid-stride kernels nelem blocks of 256
     int nred = RED_BLOCKS;
+    int nred_wide = RED_BLOCKS;
     unsigned nelem = 152 * 16;
     uint64_t mg_gen = 0;   // multigrid rebuild counter (invalidates captured V-cycles)
 

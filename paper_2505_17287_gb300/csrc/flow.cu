@@ -572,8 +572,8 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
             double gmax = 0.0;
             if (c->ng > 0) {
                 // ghost-row residual: largest change a further Jacobi pass would make
-                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
-                ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+                ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
                 IBM_LAUNCHED(c);
             }
             IBM_TRY(sync_scalars(c, 51));
@@ -770,8 +770,8 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
     IBM_LAUNCHED(c);
     IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
     if (c->ng > 0) {
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS, 1);
-        ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS, (int)gb, c->scal + 50);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+        ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
     }
     ++c->nlaunch, k_helm_decide<<<1, 1, 0, c->s>>>(H, q, c->scal, c->ng > 0, c->opts.helm_rtol, u_scale(c),
                                                  c->opts.helm_maxit, trip, h);

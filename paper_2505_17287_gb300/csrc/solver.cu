@@ -61,20 +61,20 @@ static inline dim3 rows_grid(int nx, int ny, int nz, int per_thread, int bx) {
 // reductions
 // ---------------------------------------------------------------------------
 
-// out[col] = scale * sum_i part[col*nparts + i], in a fixed order
-__global__ void k_finalize(const double *__restrict__ part, int nparts, int ncols, double scale,
-                           double *__restrict__ out) {
+// out[col] = scale * sum_i part[col*nparts + i], in a fixed order; one block
+// per column
+__global__ void k_finalize(const double *__restrict__ part, int nparts, double scale, double *__restrict__ out) {
     __shared__ double sh[32];
-    for (int col = 0; col < ncols; ++col) {
-        double v = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(size_t)col * nparts + i];
-        v = block_sum<RED_THREADS>(v, sh);
-        if (threadIdx.x == 0) out[col] = v * scale;
-    }
+    const int col = blockIdx.x;
+    double v = 0.0;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[(size_t)col * nparts + i];
+    v = block_sum<RED_THREADS>(v, sh);
+    if (threadIdx.x == 0) out[col] = v * scale;
 }
 
 ibm_status finalize(Ctx *c, const double *part, int nparts, int ncols, double scale, double *out_dev) {
-    KL(-1, k_finalize, 1, RED_THREADS, part, nparts, ncols, scale, out_dev);
+    KL(-1, k_finalize, (unsigned)ncols, RED_THREADS, part, nparts, scale, out_dev);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -246,13 +246,14 @@ OpT<float> op_of<float>(Ctx *c) {
 template <typename T>
 static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
     const OpT<T> o = op_of<T>(c);
-    KL(K_APPLY_A, k_apply_A<T>, c->nred, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    const int nb = sizeof(T) == 4 ? c->nred_wide : c->nred;
+    KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
         KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, b, sgn, y);
         IBM_LAUNCHED(c);
     }
-    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
+    IBM_TRY(finalize(c, c->part, nb, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     KL(-1, k_sub_meanT<T>, c->nred, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     return IBM_OK;
