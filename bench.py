@@ -270,6 +270,17 @@ def compare_leg(size):
         st = s.poisson_solve(rhs, phi, rtol=1e-10, maxit=4000)
         out[name] = {"iterations": st["outer_iters"], "ms": st["ms"], "rel_residual": st["rel_residual"],
                      "status": ibm.STATUS_NAMES.get(st["status"], st["status"])}
+    # the Crank-Nicolson Helmholtz step from the same state: red-black
+    # Gauss-Seidel against scheduled relaxation Jacobi (sweeps over the three
+    # components and predictor time of one step)
+    s.set_opts(outer=ibm.IBM_OUTER_FGMRES, precond=0)
+    state = s.get_state()
+    for name, hs in (("helmholtz_rbgs", 0), ("helmholtz_srj", 1)):
+        s.set_state(state)
+        s.set_opts(helm_solver=hs)
+        r = s.step(1)
+        out[name] = {"sweeps": r["helm_sweeps"], "ms_predictor": r["ms_predictor"],
+                     "status": ibm.STATUS_NAMES.get(r["status"], r["status"])}
     s.close()
     return out
 

@@ -102,6 +102,7 @@ struct Ctx {
     double *b = nullptr, *gtmp = nullptr;
     double *hinv[3] = {nullptr, nullptr, nullptr};   // Helmholtz inverse diagonals per component
     bool hinv_ok = false;
+    double *htmp = nullptr;   // second buffer of the Jacobi (SRJ) Helmholtz sweeps
     int64_t nstep = 0;
     bool have_nold = false;
 

@@ -176,6 +176,20 @@ __global__ void k_helm_rb(GridDev g, const uint8_t *__restrict__ type, const dou
     u[c] = (rhs[c] + alpha * visc_off(g, u, c, i, j, k)) * hinv[c];
 }
 
+// one damped-Jacobi sweep of the Helmholtz system: out = u + w (D^{-1}(rhs +
+// alpha L_off u) - u) on FLUID cells, u elsewhere (ghost rows are refreshed after)
+__global__ void k_helm_jacobi(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+                              const double *__restrict__ hinv, const double *__restrict__ u, double *__restrict__ out,
+                              double alpha, double w) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double uc = u[c];
+        if (type[c] != FLUID) { out[c] = uc; continue; }
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        out[c] = uc + w * ((rhs[c] + alpha * visc_off(g, u, c, i, j, k)) * hinv[c] - uc);
+    }
+}
+
 // residual of the Helmholtz system on FLUID rows; partial columns |r|^2, |rhs|^2
 __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
                              const double *__restrict__ hinv, const double *__restrict__ u, double alpha,
@@ -540,9 +554,86 @@ static ibm_status helm_prepare(Ctx *c) {
     return IBM_OK;
 }
 
+// Helmholtz by scheduled relaxation Jacobi: cycles of 8 sweeps with factors
+// 1/tau_k, tau_k the Chebyshev points of [1 - rho, 1 + rho] (the spectrum of
+// D^{-1} H for H = I - alpha L, rho = alpha S / (1 + alpha S) with S the
+// largest diagonal of L, bounded per axis from the 1D coefficients), the
+// ghost rows refreshed after every sweep; the residual test after each
+// cycle is the one of the Gauss-Seidel path
+static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
+    const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    if (!c->htmp) {
+        c->htmp = (double *)dev_alloc(c, sizeof(double) * c->N);
+        if (!c->htmp) return c->fail(IBM_ERR_OOM, "Helmholtz buffer allocation failed");
+    }
+    auto axis_max = [](const std::vector<double> &w, const std::vector<double> &h) {
+        // largest c_m + c_p + 2 / w^2 (a Dirichlet wall) of one axis
+        double m = 0.0;
+        const size_t n = w.size();
+        for (size_t i = 0; i < n; ++i) {
+            const double cm = i > 0 ? 1.0 / (h[i] * w[i]) : 2.0 / (w[i] * w[i]);
+            const double cp = i + 1 < n ? 1.0 / (h[i + 1] * w[i]) : 2.0 / (w[i] * w[i]);
+            m = fmax(m, cm + cp);
+        }
+        return m;
+    };
+    double S = axis_max(c->hdx, c->hhx) + axis_max(c->hdy, c->hhy);
+    if (c->ndim == 3) S += axis_max(c->hdz, c->hhz);
+    const double rho = alpha * S / (1.0 + alpha * S), pi = 3.14159265358979323846;
+    const int M = 8;
+    double w[M];
+    const int order[M] = {0, 4, 2, 6, 1, 5, 3, 7};   // bit-reversed
+    for (int k = 0; k < M; ++k) w[order[k]] = 1.0 / (1.0 + rho * cos(pi * (2.0 * k + 1.0) / (2.0 * M)));
+    const double *hinv = c->hinv[q];
+    double *u = c->ustar[q], *t = c->htmp;
+    const double *rhs = c->rhs[q];
+    const unsigned gb = (unsigned)((c->ng + 255) / 256);
+    *sweeps = 0;
+    double rhs2 = -1.0;
+    for (int it = 0; it < c->opts.helm_maxit; it += M) {
+        for (int k = 0; k < M; ++k) {
+            kt_begin(c, K_HELM);
+            ++c->nlaunch, k_helm_jacobi<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, rhs, hinv, u, t, alpha, w[k]);
+            kt_end(c, K_HELM);
+            if (c->ng > 0) {
+                Fields3 T3{{t, t, t}};
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, c->gtmp, c->part, 0);
+                ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, c->gtmp);
+            }
+            IBM_LAUNCHED(c);
+            double *x = u;
+            u = t;
+            t = x;
+            ++*sweeps;
+        }
+        // M is even: the iterate is back in ustar[q]
+        Fields3 U{{u, u, u}};
+        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+        IBM_LAUNCHED(c);
+        IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
+        double gmax = 0.0;
+        if (c->ng > 0) {
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
+            IBM_LAUNCHED(c);
+        }
+        IBM_TRY(sync_scalars(c, 51));
+        const double r2 = c->hscal[48];
+        if (rhs2 < 0) rhs2 = c->hscal[49];
+        if (c->ng > 0) gmax = c->hscal[50];
+        if (!isfinite(r2)) return c->fail(IBM_ERR_DIVERGED, "Helmholtz residual is not finite");
+        const double bn = sqrt(rhs2) > 0 ? sqrt(rhs2) : 1.0;
+        double scale = 1.0;
+        for (int a = 0; a < 3; ++a) scale = fmax(scale, fabs(c->desc.u_inf[a]));
+        if (sqrt(r2) <= c->opts.helm_rtol * bn && gmax <= c->opts.helm_rtol * scale) return IBM_OK;
+    }
+    return IBM_ERR_NOT_CONVERGED;
+}
+
 static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     const double alpha = c->desc.dt / (2.0 * c->desc.Re);
     IBM_TRY(helm_prepare(c));
+    if (c->opts.helm_solver == 1) return helmholtz_srj(c, q, sweeps);
     const double *hinv = c->hinv[q];
     double *u = c->ustar[q];
     const double *rhs = c->rhs[q];
@@ -845,7 +936,7 @@ static ibm_status flow_step_capture(Ctx *c) {
 ibm_status step_graph_eligible(Ctx *c) {
     const ibm_solver_opts &o = c->opts;
     if (o.graph != 2 || c->kt.on || c->s == nullptr || c->s == cudaStreamLegacy) return IBM_ERR_STATE;
-    if (o.outer != IBM_OUTER_FGMRES || o.inner_iters != 1) return IBM_ERR_STATE;
+    if (o.outer != IBM_OUTER_FGMRES || o.inner_iters != 1 || o.helm_solver != 0) return IBM_ERR_STATE;
     return IBM_OK;
 }
 
