@@ -129,12 +129,6 @@ typedef struct {
                            advection-diffusion step): cycles of 8 damped-Jacobi sweeps
                            with Chebyshev factors over the Jacobi-scaled spectrum
                            [1 - rho, 1 + rho], rho bounded from the grid; host-driven */
-    int vblock_cells;   /* FP32 multigrid (IBM_MIXED): from the first coarse level with at
-                           most this many cells down, the V-cycle runs inside one
-                           1024-thread block (same arithmetic, one launch instead of
-                           ~8 per level); 0 = off (default: measured no faster, the
-                           block's passes wait on L2 latency as the launches did).
-                           FP64 hierarchies never do. */
 } ibm_solver_opts;
 
 typedef struct {
@@ -191,7 +185,7 @@ enum {
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
-   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, vblock_cells 0. */
+   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -113,7 +113,6 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->srj_sweeps = 16;
     o->srj_lmin = 0.0;
     o->helm_solver = 0;
-    o->vblock_cells = 0;
     return IBM_OK;
 }
 
@@ -140,7 +139,6 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 (multigrid) or 1 (SRJ)"; return false; }
     if (o->srj_sweeps < 1 || o->srj_sweeps > 64) { why = "srj_sweeps must be in [1, 64]"; return false; }
     if (!(o->srj_lmin >= 0.0 && o->srj_lmin < 2.0)) { why = "srj_lmin must be in [0, 2)"; return false; }
-    if (o->vblock_cells < 0 || o->vblock_cells > (1 << 20)) { why = "vblock_cells must be in [0, 2^20]"; return false; }
     if (o->helm_solver != 0 && o->helm_solver != 1) { why = "helm_solver must be 0 or 1"; return false; }
     return true;
 }

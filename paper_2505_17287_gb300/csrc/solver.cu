@@ -892,158 +892,6 @@ __global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const
     coarse_solve_dev<T>(L, f, x, sweeps, S);
 }
 
-// ---------------------------------------------------------------------------
-// The bottom of the V-cycle in one block. Levels with few cells cost a launch
-// per smoothing pass and transfer while doing almost no work; from the first
-// level at or below vblock_cells down, one block of VB_THREADS threads runs
-// the same passes in the same order (block-wide barriers between them), with
-// the same arithmetic, so the V-cycle's output is unchanged bit for bit.
-// ---------------------------------------------------------------------------
-
-constexpr int VB_THREADS = 1024;
-constexpr int VB_MAXLV = 8;
-
-template <typename T>
-struct VBlock {
-    int nlv;                      // levels handled, lv[0] = entry level
-    int nu1, nu2, sweeps;
-    MGLevel<T> lv[VB_MAXLV];
-    Xfer<T> X[VB_MAXLV];          // X[l]: transfer between lv[l - 1] and lv[l]
-    int fx[VB_MAXLV];             // x coarsening factor of lv[l] from lv[l - 1]
-    T *pn[VB_MAXLV];              // pn of lv[l] (fine side of X[l + 1])
-    T *scr[VB_MAXLV];             // scratch of lv[l]'s size
-};
-
-template <typename T>
-__device__ __forceinline__ void vb_rbgs(const MGLevel<T> &L, int col) {
-    for (int64_t c = threadIdx.x; c < L.n; c += blockDim.x) {
-        const uint32_t t = L.fnx.div((uint32_t)c);
-        const int i = (int)((uint32_t)c - t * (uint32_t)L.nx);
-        const uint32_t kk = L.fny.div(t);
-        const int j = (int)(t - kk * (uint32_t)L.ny), k = (int)kk;
-        if (((i + j + k) & 1) != col) continue;
-        if (!(L.dinv[c] > T(0))) continue;
-        T d;
-        const T s = L.f[c] + k_offdiag<T, false>(L, L.x, c, i, j, k, d);
-        L.x[c] = s * L.dinv[c];
-    }
-    __syncthreads();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(VB_THREADS) k_vcycle_block(VBlock<T> P) {
-    __shared__ CoarseSmem<T> S;
-    const int zcol = P.nu1 > 0 ? 1 : -1;
-    for (int l = 0; l + 1 < P.nlv; ++l) {
-        const MGLevel<T> &L = P.lv[l];
-        const MGLevel<T> &C = P.lv[l + 1];
-        const Xfer<T> &X = P.X[l + 1];
-        for (int s = 0; s < P.nu1; ++s) {
-            vb_rbgs<T>(L, 0);
-            vb_rbgs<T>(L, 1);
-        }
-        // x-pass of the restriction of pn r (as k_resid_rx)
-        T *tA = P.scr[l];
-        const T *pn = P.pn[l];
-        const int64_t na = (int64_t)C.nx * L.ny * L.nz;
-        for (int64_t q = threadIdx.x; q < na; q += blockDim.x) {
-            const int I = (int)(q % C.nx);
-            const int64_t row = q / C.nx;
-            const int j = (int)(row % L.ny), k = (int)(row / L.ny);
-            T acc = T(0);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const int i = X.Gx[4 * I + s];
-                if (i < 0) continue;
-                const int64_t c = row * L.nx + i;
-                const bool relaxed = ((i + j + k) & 1) == zcol;
-                const T p = relaxed ? T(0) : pn[c];
-                T g = T(0);
-                if (p > T(0)) {
-                    T d;
-                    const T off = k_offdiag<T, false>(L, L.x, c, i, j, k, d);
-                    g = p * (L.f[c] - (d * L.x[c] - off));
-                }
-                acc += X.gwx[4 * I + s] * g;
-            }
-            tA[q] = acc;
-        }
-        __syncthreads();
-        // y, z passes (as k_restrict_yz)
-        for (int64_t cc = threadIdx.x; cc < C.n; cc += blockDim.x) {
-            const int Ic = (int)(cc % C.nx);
-            const int64_t row = cc / C.nx;
-            const int Jc = (int)(row % C.ny), Kc = (int)(row / C.ny);
-            C.x[cc] = T(0);
-            if (!(C.dinv[cc] > T(0))) {
-                C.f[cc] = T(0);
-                continue;
-            }
-            T acc = T(0);
-#pragma unroll
-            for (int s3 = 0; s3 < 4; ++s3) {
-                const int k = X.Gz[4 * Kc + s3];
-                if (k < 0) continue;
-                T a2 = T(0);
-#pragma unroll
-                for (int s2 = 0; s2 < 4; ++s2) {
-                    const int j = X.Gy[4 * Jc + s2];
-                    if (j >= 0) a2 += X.gwy[4 * Jc + s2] * tA[((int64_t)k * L.ny + j) * C.nx + Ic];
-                }
-                acc += X.gwz[4 * Kc + s3] * a2;
-            }
-            C.f[cc] = acc;
-        }
-        __syncthreads();
-    }
-    const MGLevel<T> &B = P.lv[P.nlv - 1];
-    coarse_solve_dev<T>(B, B.f, B.x, P.sweeps, S);
-    for (int l = P.nlv - 2; l >= 0; --l) {
-        const MGLevel<T> &L = P.lv[l];
-        const MGLevel<T> &C = P.lv[l + 1];
-        const Xfer<T> &X = P.X[l + 1];
-        // x-interpolation of the coarse rows (as k_prolong_x)
-        T *tB = P.scr[l];
-        const int64_t nb = (int64_t)L.nx * C.ny * C.nz;
-        for (int64_t q = threadIdx.x; q < nb; q += blockDim.x) {
-            const int i = (int)(q % L.nx);
-            const int64_t row = q / L.nx;
-            const T *xr = C.x + row * C.nx;
-            const int J2 = X.Jx[i];
-            const T w = X.wx[i];
-            T v = w * xr[X.Ix[i]];
-            if (J2 >= 0) v += (T(1) - w) * xr[J2];
-            tB[q] = v;
-        }
-        __syncthreads();
-        // y, z interpolation and the correction (as k_prolong_yz)
-        const T *pn = P.pn[l];
-        for (int64_t c = threadIdx.x; c < L.n; c += blockDim.x) {
-            const T p = pn[c];
-            if (!(p > T(0))) continue;
-            const int i = (int)(c % L.nx);
-            const int64_t row = c / L.nx;
-            const int j = (int)(row % L.ny), k = (int)(row / L.ny);
-            int ib[2], ic[2];
-            T wb[2], wc[2];
-            const int nbv = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
-            const int ncv = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
-            T acc = T(0);
-            for (int q3 = 0; q3 < ncv; ++q3) {
-                T a2 = T(0);
-                for (int q2 = 0; q2 < nbv; ++q2) a2 += wb[q2] * tB[((int64_t)ic[q3] * C.ny + ib[q2]) * L.nx + i];
-                acc += wc[q3] * a2;
-            }
-            L.x[c] += acc * p;
-        }
-        __syncthreads();
-        for (int s = 0; s < P.nu2; ++s) {
-            vb_rbgs<T>(L, 1);
-            vb_rbgs<T>(L, 0);
-        }
-    }
-}
-
 // q = K p ; partial (p, q) in FP64
 template <typename T, bool FINE>
 __global__ void k_spmv_dot(MGLevel<T> L, const T *__restrict__ p, T *__restrict__ q, double *__restrict__ part) {
@@ -1493,18 +1341,7 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         return IBM_OK;
     }
     IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
-    // first level run inside the block-wide bottom kernel (FP32 only: one SM
-    // of FP64 is slower than the launches it would replace); L = none
-    int lb = L;
-    if (sizeof(T) == 4 && c->opts.vblock_cells > 0 && c->opts.mg_interp == 1)
-        for (int l = 1; l < L; ++l)
-            if (H.lv[l].n <= c->opts.vblock_cells) {
-                lb = l;
-                break;
-            }
-    if (lb >= L - 1 || L - lb > VB_MAXLV) lb = L;
-    const int ldown = lb < L ? lb : L - 1;   // levels smoothed by separate launches
-    for (int l = 0; l < ldown; ++l) {
+    for (int l = 0; l < L - 1; ++l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         for (int s = 0; s < nu1; ++s) {
@@ -1535,24 +1372,9 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         }
         IBM_LAUNCHED(c);
     }
-    if (lb < L) {
-        VBlock<T> P{};
-        P.nlv = L - lb;
-        P.nu1 = nu1;
-        P.nu2 = nu2;
-        P.sweeps = cs;
-        for (int q = 0; q < P.nlv; ++q) {
-            P.lv[q] = H.lv[lb + q];
-            if (q > 0) P.X[q] = xfer_of<T>(c, lb + q);
-            P.pn[q] = q + 1 < P.nlv ? H.pn[lb + q] : nullptr;
-            P.scr[q] = q + 1 < P.nlv ? H.res[lb + q] : nullptr;
-        }
-        KL(K_RBGS_C, k_vcycle_block<T>, 1, VB_THREADS, P);
-    } else {
-        KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
-    }
+    KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
     IBM_LAUNCHED(c);
-    for (int l = ldown - 1; l >= 0; --l) {
+    for (int l = L - 2; l >= 0; --l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         MGLevel<T> &Lf = H.lv[l];

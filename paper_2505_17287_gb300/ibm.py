@@ -47,8 +47,7 @@ class ibm_solver_opts(Structure):
                 ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
                 ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
                 ("mixed_inner_rtol", c_double), ("mg_interp", c_int), ("tile_x", c_int), ("graph", c_int),
-                ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
-                ("vblock_cells", c_int)]
+                ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int)]
 
 
 class ibm_table_info(Structure):

@@ -167,29 +167,3 @@ def test_graph_ensemble_runs_every_case():
     out = ensemble.run_graphs(cases)
     assert out["ok"], [r["status"] for r in out["results"]]
     assert all(r["steps"] == 4 and r["rel_residual"] <= 1e-10 for r in out["results"])
-
-
-@pytest.mark.parametrize("which", ["cylinder", "spheres", "wing"])
-@pytest.mark.parametrize("graph", [0, 2])
-def test_block_bottom_vcycle_is_bitwise_identical(which, graph):
-    """The coarse levels run inside one block with the same passes in the
-    same order and the same arithmetic as the launched kernels: the mixed-
-    precision step gives the same bits with it on and off (the default)."""
-    case = {"cylinder": lambda: synth.cylinder_case(256, 128, 256, nsteps=3),
-            "spheres": lambda: synth.multi_sphere_case(48, [(0.4, (0.5, 0.0, 0.0))], 200.0, nsteps=3, level=3),
-            "wing": lambda: synth.wing_case(96, 64, 64, n_chord=30, n_span=10)}[which]()
-    st = torch.cuda.Stream()
-    res = []
-    for vb in (0, 16384):
-        s = ibm.Solver(case, precision=ibm.IBM_MIXED, stream=st)
-        s.set_opts(precision=ibm.IBM_MIXED, graph=graph, vblock_cells=vb)
-        for v, e in synth.case_bodies(case):
-            s.set_body(v, e)
-        s.classify()
-        r = s.step(3)
-        assert r["status"] == ibm.IBM_OK
-        res.append((r, {k: s.get(k) for k in ("u", "v", "p")}))
-        s.close()
-    assert res[0][0]["poisson_outer"] == res[1][0]["poisson_outer"]
-    for k in res[0][1]:
-        assert np.array_equal(res[0][1][k], res[1][1][k]), k
