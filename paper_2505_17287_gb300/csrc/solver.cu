@@ -1631,7 +1631,8 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             inner += c->opts.inner_iters;
             IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
             // classical Gram-Schmidt, with a second pass when the norm drops
-            // by more than a factor 0.7 (Daniel, Gragg, Kaufman, Stewart 1976)
+            // below reorth_eta (default 0.3) of its value (the test of Daniel,
+            // Gragg, Kaufman and Stewart 1976, with a looser threshold)
             VPtrs<T> vp{};
             for (int i = 0; i <= j; ++i) vp.p[i] = K.V[i];
             double hcol[17] = {0};
@@ -1650,7 +1651,8 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
                 IBM_TRY(sync_scalars(c, S_TMP + 1));
                 wafter2 = c->hscal[S_TMP];
                 for (int i = 0; i <= j; ++i) hcol[i] += h.v[i];
-                if (wafter2 > 0.49 * wbefore2) break;
+                const double eta = c->opts.reorth_eta;
+                if (!(wafter2 <= eta * eta * wbefore2)) break;
             }
             const double hn = sqrt(wafter2);
             ++outer;
@@ -2083,13 +2085,13 @@ __global__ void k_fg_cycle(DevFG *F, const double *rn2, cudaGraphConditionalHand
 }
 
 // after the first Gram-Schmidt pass of step j: h in md[0..j], ||w||^2 before
-// in md[j+1], after in *wa2; a second pass when the norm dropped by more
-// than a factor 0.7
-__global__ void k_fg_post1(DevFG *F, const double *md, const double *wa2, int j) {
+// in md[j+1], after in *wa2; a second pass when ||w||^2 dropped to eta2 of
+// its value or below
+__global__ void k_fg_post1(DevFG *F, const double *md, const double *wa2, int j, double eta2) {
     for (int i = 0; i <= j; ++i) F->hcol[i] = md[i];
     F->wb = md[j + 1];
     F->wa = *wa2;
-    F->reorth = F->wa <= 0.49 * F->wb;
+    F->reorth = F->wa <= eta2 * F->wb;
 }
 
 __global__ void k_fg_post2(DevFG *F, const double *md, const double *wa2, int j) {
@@ -2222,7 +2224,8 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
             KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
                vp, c->scal + S_MD, c->part);
             IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
-            KL(-1, k_fg_post1, 1, 1, F, c->scal + S_MD, c->scal + S_TMP, j);
+            KL(-1, k_fg_post1, 1, 1, F, c->scal + S_MD, c->scal + S_TMP, j,
+               c->opts.reorth_eta * c->opts.reorth_eta);
             IBM_TRY(cond_handle(c, &hr));
             KL(-1, k_set_cond, 1, 1, hr, &F->reorth);
             CondScope sr;

@@ -47,7 +47,8 @@ class ibm_solver_opts(Structure):
                 ("helm_maxit", c_int), ("ghost_tol", c_double), ("ghost_maxit", c_int), ("precision", c_int),
                 ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
                 ("mixed_inner_rtol", c_double), ("mg_interp", c_int), ("tile_x", c_int), ("graph", c_int),
-                ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int)]
+                ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
+                ("reorth_eta", c_double)]
 
 
 class ibm_table_info(Structure):
