@@ -90,7 +90,8 @@ typedef struct {
                            FGMRES steps over all restarts) */
     int restart;        /* Poisson: FGMRES restart length (1..16) */
     int inner_iters;    /* Poisson: MG-PCG iterations per preconditioner call */
-    int nu1, nu2;       /* multigrid pre/post red-black Gauss-Seidel sweeps */
+    int nu1, nu2;       /* multigrid pre/post red-black Gauss-Seidel sweeps, 1..8; equal
+                           when inner_iters > 1 (CG needs a symmetric V-cycle) */
     int coarse_sweeps;  /* red-black sweep pairs on the coarsest level */
     double helm_rtol;   /* Crank-Nicolson Helmholtz: relative residual target */
     int helm_maxit;     /* Helmholtz: sweep limit */

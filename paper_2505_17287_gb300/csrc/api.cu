@@ -122,7 +122,10 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->max_outer < 1) { why = "max_outer must be >= 1"; return false; }
     if (o->restart < 1 || o->restart > 16) { why = "restart must be in [1, 16]"; return false; }
     if (o->inner_iters < 1 || o->inner_iters > 64) { why = "inner_iters must be in [1, 64]"; return false; }
-    if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 != o->nu2) { why = "nu1 = nu2 >= 1 is required (symmetric V-cycle)"; return false; }
+    if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) { why = "nu1, nu2 must be in [1, 8]"; return false; }
+    // the inner MG-PCG (inner_iters > 1) needs a symmetric V-cycle; FGMRES and
+    // BiCGStab accept any preconditioner
+    if (o->inner_iters > 1 && o->nu1 != o->nu2) { why = "nu1 = nu2 is required when inner_iters > 1 (CG needs a symmetric V-cycle)"; return false; }
     if (o->coarse_sweeps < 1) { why = "coarse_sweeps must be >= 1"; return false; }
     if (!(o->helm_rtol > 0.0) || o->helm_maxit < 1) { why = "bad Helmholtz tolerance or limit"; return false; }
     if (!(o->ghost_tol > 0.0) || o->ghost_maxit < 1) { why = "bad ghost refresh tolerance or limit"; return false; }

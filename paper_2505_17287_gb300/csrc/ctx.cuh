@@ -169,9 +169,10 @@ struct Ctx {
     int64_t nlaunch = 0;   // kernels launched by this context so far
     // launch sizes that follow the grid: reduction kernels run nred blocks of
     // RED_THREADS (about 8 cells per thread, at most RED_BLOCKS; a function
-    // of N only, so reductions stay deterministic), the FP32 operator product
-    // nred_wide (about 2 cells per thread, at most RED_BLOCKS_MAX), elementwise
-    // grid-stride kernels nelem blocks of 256
+    // of N only, so reductions stay deterministic); the FP32 operator product
+    // and the Krylov/preconditioner vector kernels nred_wide (about 2 cells
+    // per thread, at most RED_BLOCKS_MAX: a thread walking tens of cells is
+    // latency-bound); the flow kernels nelem blocks of 256
     int nred = RED_BLOCKS;
     int nred_wide = RED_BLOCKS;
     unsigned nelem = 152 * 16;

@@ -254,7 +254,7 @@ static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
         IBM_LAUNCHED(c);
     }
     IBM_TRY(finalize(c, c->part, nb, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-    KL(-1, k_sub_meanT<T>, c->nred, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
+    KL(-1, k_sub_meanT<T>, c->nred_wide, RED_THREADS, c->N, c->type, y, c->scal + S_MEAN);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -1520,14 +1520,14 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
         else KL(K_SPMV0, (k_spmv_dot<T, false>), c->nred, RED_THREADS, L0, H.pp, H.pq, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_PQ));
         KL(-1, k_alpha, 1, 1, c->scal);
-        KL(-1, k_axpy2<T>, c->nred, RED_THREADS, n, H.px, H.pr, H.pp, H.pq, c->scal);
+        KL(-1, k_axpy2<T>, c->nred_wide, RED_THREADS, n, H.px, H.pr, H.pp, H.pq, c->scal);
         IBM_LAUNCHED(c);
         if (it + 1 < iters) {
             IBM_TRY(vcycle(c, H, H.pr, H.pz));
             KL(-1, k_dot<T>, c->nred, RED_THREADS, n, H.pr, H.pz, c->part);
             IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_RZN));
             KL(-1, k_beta, 1, 1, c->scal);
-            KL(-1, k_pupd<T>, c->nred, RED_THREADS, n, H.pp, H.pz, c->scal);
+            KL(-1, k_pupd<T>, c->nred_wide, RED_THREADS, n, H.pp, H.pz, c->scal);
             IBM_LAUNCHED(c);
         }
     }
@@ -1538,7 +1538,7 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     const OpT<T> oin = op_of<T>(c);
-    KL(-1, k_pre_in<T>, c->nred, RED_THREADS, c->g, oin, c->type, v, H.pr);
+    KL(-1, k_pre_in<T>, c->nred_wide, RED_THREADS, c->g, oin, c->type, v, H.pr);
     IBM_LAUNCHED(c);
     const T *xin = H.px;
     if (c->opts.precond == 1) {
@@ -1556,7 +1556,7 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     } else {
         IBM_TRY(pcg(c, H, c->opts.inner_iters));
     }
-    KL(-1, k_pre_out<T>, c->nred, RED_THREADS, c->N, c->type, xin, z);
+    KL(-1, k_pre_out<T>, c->nred_wide, RED_THREADS, c->N, c->type, xin, z);
     IBM_LAUNCHED(c);
     const OpT<T> o = op_of<T>(c);
     if (c->ng > 0) {
@@ -1621,7 +1621,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
         if (rel <= rtol || (single_cycle && cycles > 0)) break;
         if (outer >= maxit) { status = IBM_ERR_NOT_CONVERGED; break; }
         ++cycles;
-        KL(-1, (k_scale<T, T>), c->nred, RED_THREADS, n, K.V[0], K.r, 1.0 / beta);
+        KL(-1, (k_scale<T, T>), c->nred_wide, RED_THREADS, n, K.V[0], K.r, 1.0 / beta);
         IBM_LAUNCHED(c);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
@@ -1675,7 +1675,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             jlast = j;
             const double est = fabs(gv[j + 1]) / bnorm;
             if (hn > 0.0 && j + 1 < m) {
-                KL(-1, (k_scale<T, T>), c->nred, RED_THREADS, n, K.V[j + 1], K.w, 1.0 / hn);
+                KL(-1, (k_scale<T, T>), c->nred_wide, RED_THREADS, n, K.V[j + 1], K.w, 1.0 / hn);
                 IBM_LAUNCHED(c);
             }
             if (est <= rtol || hn == 0.0) break;
@@ -1689,7 +1689,7 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
         }
         Coef yc{};
         for (int i = 0; i <= jlast; ++i) yc.v[i] = y[i];
-        KL(-1, k_xupd<T>, c->nred, RED_THREADS, n, x, (const T *const *)K.Zdev, jlast + 1, yc);
+        KL(-1, k_xupd<T>, c->nred_wide, RED_THREADS, n, x, (const T *const *)K.Zdev, jlast + 1, yc);
         IBM_LAUNCHED(c);
     }
     *outer_out = outer;
@@ -1772,7 +1772,7 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
         if (rel <= rtol) break;
         if (steps >= maxit || refinements >= 256) { status = IBM_ERR_NOT_CONVERGED; break; }
         ++refinements;
-        KL(-1, (k_scale<float, double>), c->nred, RED_THREADS, n, c->b32, c->rr, 1.0 / rn);
+        KL(-1, (k_scale<float, double>), c->nred_wide, RED_THREADS, n, c->b32, c->rr, 1.0 / rn);
         IBM_CUDA(c, cudaMemsetAsync(c->d32, 0, sizeof(float) * n, c->s));
         IBM_LAUNCHED(c);
         // inner target: the FP64 goal, but no tighter than FP32 can reach
@@ -1791,7 +1791,7 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
         inner += in;
         KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-        KL(-1, k_add_scaled, c->nred, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
+        KL(-1, k_add_scaled, c->nred_wide, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
         IBM_LAUNCHED(c);
         if (o == 0) { status = IBM_ERR_NOT_CONVERGED; break; }
         if (refinements > 1 && !(rel < 0.999 * last_rel)) stalls++;
@@ -1809,9 +1809,9 @@ static ibm_status apply_prec(Ctx *c, const double *v, double *z) {
     if (c->opts.precision == IBM_MIXED) {
         // FP64 vectors through the FP32 multigrid: convert in and out
         IBM_TRY(ensure_mixed(c));
-        KL(-1, (k_scale<float, double>), c->nred, RED_THREADS, c->N, c->b32, v, 1.0);
+        KL(-1, (k_scale<float, double>), c->nred_wide, RED_THREADS, c->N, c->b32, v, 1.0);
         IBM_TRY(precond<float>(c, c->mg32, c->b32, c->d32));
-        KL(-1, (k_scale<double, float>), c->nred, RED_THREADS, c->N, z, c->d32, 1.0);
+        KL(-1, (k_scale<double, float>), c->nred_wide, RED_THREADS, c->N, z, c->d32, 1.0);
         IBM_LAUNCHED(c);
         return IBM_OK;
     }
@@ -1851,14 +1851,14 @@ static ibm_status bicgstab(Ctx *c, double *phi, double bnorm, double rtol, int m
         KL(-1, k_dot64, c->nred, RED_THREADS, n, rh, r, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + B_RHO1));
         KL(-1, k_bicg_beta, 1, 1, c->scal);
-        KL(-1, k_bicg_p, c->nred, RED_THREADS, n, r, p, v, c->scal);
+        KL(-1, k_bicg_p, c->nred_wide, RED_THREADS, n, r, p, v, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, p, ph));
         IBM_TRY(apply_PA<double>(c, ph, nullptr, 1.0, v));
         KL(-1, k_dot64, c->nred, RED_THREADS, n, rh, v, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + B_DEN));
         KL(-1, k_bicg_alpha, 1, 1, c->scal);
-        KL(-1, k_bicg_s, c->nred, RED_THREADS, n, r, v, sv, c->scal);
+        KL(-1, k_bicg_s, c->nred_wide, RED_THREADS, n, r, v, sv, c->scal);
         IBM_LAUNCHED(c);
         IBM_TRY(apply_prec(c, sv, shv));
         IBM_TRY(apply_PA<double>(c, shv, nullptr, 1.0, t));
@@ -2215,7 +2215,7 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
         IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hj, &sj));
         {
             // V_j = (j == 0 ? r : w) / norm
-            KL(-1, (k_scale_dev<T, T>), c->nred, RED_THREADS, n, K.V[j], j == 0 ? K.r : K.w, &F->scale);
+            KL(-1, (k_scale_dev<T, T>), c->nred_wide, RED_THREADS, n, K.V[j], j == 0 ? K.r : K.w, &F->scale);
             IBM_TRY(precond<T>(c, *K.H, K.V[j], K.Z[j]));
             IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
             KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w, vp,
@@ -2245,7 +2245,7 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
         IBM_TRY(cond_close(c, &sj));
     }
     KL(-1, k_fg_ysolve, 1, 1, F, m);
-    KL(-1, k_xupd_dev<T>, c->nred, RED_THREADS, n, x, zp, F);
+    KL(-1, k_xupd_dev<T>, c->nred_wide, RED_THREADS, n, x, zp, F);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -2283,7 +2283,7 @@ static ibm_status mixed_dev(Ctx *c, double *phi, DevFG *R, DevFG *F) {
     CondScope sr;
     IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, hr, &sr));
     {
-        KL(-1, (k_scale_dev<float, double>), c->nred, RED_THREADS, n, c->b32, c->rr, &R->scale);
+        KL(-1, (k_scale_dev<float, double>), c->nred_wide, RED_THREADS, n, c->b32, c->rr, &R->scale);
         IBM_CUDA(c, cudaMemsetAsync(c->d32, 0, sizeof(float) * n, c->s));
         // the FP32 cycle: r32 = P(b32 - A d32), then one restart cycle if needed
         cudaGraphConditionalHandle hi;
@@ -2297,7 +2297,7 @@ static ibm_status mixed_dev(Ctx *c, double *phi, DevFG *R, DevFG *F) {
         IBM_TRY(cond_close(c, &si));
         KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-        KL(-1, k_add_scaled_dev, c->nred, RED_THREADS, n, c->type, phi, c->d32, R, c->scal + S_MEAN);
+        KL(-1, k_add_scaled_dev, c->nred_wide, RED_THREADS, n, c->type, phi, c->d32, R, c->scal + S_MEAN);
         KL(-1, k_ref_after, 1, 1, R, F);
         IBM_TRY(apply_PA<double>(c, phi, c->b, -1.0, c->rr));
         IBM_TRY(norm2_dev<double>(c, c->rr, S_TMP));
@@ -2331,7 +2331,7 @@ ibm_status poisson_solve_dev(Ctx *c, const double *rhs, double *phi, double rtol
     KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, rhs, c->part);
     IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
+    KL(-1, k_sub_mean, c->nred_wide, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
     if (c->ng > 0) KL(-1, k_zero_at, (unsigned)((c->ng + 255) / 256), 256, c->ng, c->gidx, c->b);
     IBM_TRY(norm2_dev<double>(c, c->b, S_TMP));
     KL(-1, k_fg_setup, 1, 1, R, c->scal + S_TMP, rtol, maxit);
@@ -2342,10 +2342,10 @@ ibm_status poisson_solve_dev(Ctx *c, const double *rhs, double *phi, double rtol
     } else {
         IBM_TRY(fgmres64_dev(c, phi, R));
     }
-    KL(-1, k_zero_if, c->nred, RED_THREADS, n, phi, &R->zero);
+    KL(-1, k_zero_if, c->nred_wide, RED_THREADS, n, phi, &R->zero);
     KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, phi, c->part);
     IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
+    KL(-1, k_sub_mean, c->nred_wide, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -2397,7 +2397,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, rhs, c->part);
     IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
     IBM_CUDA(c, cudaMemcpyAsync(c->b, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
-    KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
+    KL(-1, k_sub_mean, c->nred_wide, RED_THREADS, n, c->type, c->b, c->scal + S_MEAN, 0);
     IBM_LAUNCHED(c);
     // GHOST rows of b are 0 (homogeneous Neumann on the body)
     if (c->ng > 0) {
@@ -2422,7 +2422,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
         // normalise: zero volume-weighted FLUID mean, shift ghosts too
         KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, phi, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
-        KL(-1, k_sub_mean, c->nred, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
+        KL(-1, k_sub_mean, c->nred_wide, RED_THREADS, n, c->type, phi, c->scal + S_MEAN, 1);
         IBM_LAUNCHED(c);
     }
     IBM_TRY(kt_flush(c));
