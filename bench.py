@@ -360,7 +360,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     case = wing_case(args.size)
-    stream = torch.cuda.current_stream()
+    # the solver runs on its own stream (not the legacy default stream), so
+    # its multigrid V-cycle is captured once and replayed as a CUDA graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     main_prec = ibm.IBM_MIXED if args.precision == "mixed" else ibm.IBM_FP64
     s = ibm.Solver(case, precision=main_prec)
     s.set_opts(precision=main_prec)

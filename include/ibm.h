@@ -130,6 +130,8 @@ typedef struct {
                            advection-diffusion step): cycles of 8 damped-Jacobi sweeps
                            with Chebyshev factors over the Jacobi-scaled spectrum
                            [1 - rho, 1 + rho], rho bounded from the grid; host-driven */
+    double smooth_omega; /* relaxation factor of the multigrid red-black smoother, in
+                           (0, 2): 1 = Gauss-Seidel, > 1 over-relaxed */
     double reorth_eta;  /* FGMRES classical Gram-Schmidt: a second orthogonalisation pass
                            when ||w|| drops below reorth_eta times its value before the
                            first pass, in [0, 1] (0 = never, 1 = always). Default 0.3:
@@ -192,7 +194,7 @@ enum {
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
-   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, reorth_eta 0.3. */
+   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -571,9 +571,10 @@ __global__ void k_open_mask(GridDev g, const uint8_t *__restrict__ type, uint8_t
 }
 
 // red-black Gauss-Seidel, one colour: x_c = (f_c + sum T x_nb) / D_c on the
-// cells of colour col ((i + j + k) even = 0) with D_c > 0
-template <typename T, bool FINE>
-__global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col) {
+// cells of colour col ((i + j + k) even = 0) with D_c > 0; with OMEGA the
+// over-relaxed update x_c += w ((f_c + sum T x_nb) / D_c - x_c)
+template <typename T, bool FINE, bool OMEGA = false>
+__global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col, T w = T(1)) {
     const int64_t row = blockIdx.x;
     const int j = (int)(row % L.ny), k = (int)(row / L.ny);
     const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
@@ -583,9 +584,9 @@ __global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x,
     T d;
     const T s = f[c] + k_offdiag<T, FINE>(L, x, c, i, j, k, d);
     if (FINE) {
-        if (d > T(0)) x[c] = s / d;
+        if (d > T(0)) x[c] = OMEGA ? x[c] + w * (s / d - x[c]) : s / d;
     } else {
-        x[c] = s * L.dinv[c];
+        x[c] = OMEGA ? x[c] + w * (s * L.dinv[c] - x[c]) : s * L.dinv[c];
     }
 }
 
@@ -1324,8 +1325,12 @@ static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col) {
     MGLevel<T> &L = H.lv[l];
     const int bx = c->opts.tile_x;
     const dim3 grid = rows_grid(L.nx, L.ny, L.nz, 2, bx);
-    if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true>), grid, bx, L, f, x, col);
-    else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false>), grid, bx, L, f, x, col);
+    const double w = c->opts.smooth_omega;
+    if (w != 1.0) {
+        if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true, true>), grid, bx, L, f, x, col, (T)w);
+        else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false, true>), grid, bx, L, f, x, col, (T)w);
+    } else if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true>), grid, bx, L, f, x, col, T(1));
+    else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false>), grid, bx, L, f, x, col, T(1));
     IBM_LAUNCHED(c);
     return IBM_OK;
 }

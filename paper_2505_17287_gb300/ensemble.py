@@ -28,16 +28,19 @@ def size_class(case) -> int:
     return int(round(math.log2(case.ncells)))
 
 
-def candidates(precision=ibm.IBM_MIXED, tiles=(32, 64, 128, 256), nus=(1, 2)):
+def candidates(precision=ibm.IBM_MIXED, tiles=(32, 64, 128, 256), nus=(1, 2), omegas=(1.0, 1.1)):
     """Option sets the autotuner chooses from: multigrid row-tile width x
-    smoother sweeps per V-cycle half, all with the V-cycle graph; the last
-    one is the library default without the graph (the reference point)."""
+    smoother sweeps per V-cycle half x smoother relaxation factor (over-
+    relaxation helps uniform grids, not strongly stretched ones), all with the
+    V-cycle graph; the last one is the library default without the graph
+    (the reference point)."""
     out = []
     for t in tiles:
         for nu in nus:
-            o = ibm.ibm_default_opts()
-            o.precision, o.tile_x, o.nu1, o.nu2, o.graph = precision, t, nu, nu, 1
-            out.append(o)
+            for om in omegas:
+                o = ibm.ibm_default_opts()
+                o.precision, o.tile_x, o.nu1, o.nu2, o.graph, o.smooth_omega = precision, t, nu, nu, 1, om
+                out.append(o)
     o = ibm.ibm_default_opts()
     o.precision, o.graph = precision, 0
     out.append(o)
@@ -58,7 +61,7 @@ def tune(cases, precision=ibm.IBM_MIXED, steps=3):
 
 
 def describe(o):
-    return {"tile_x": o.tile_x, "nu": o.nu1, "graph": o.graph}
+    return {"tile_x": o.tile_x, "nu": o.nu1, "omega": o.smooth_omega, "graph": o.graph}
 
 
 def run(cases, slots=12, precision=ibm.IBM_MIXED, tuned=None):

@@ -64,7 +64,7 @@ def test_graph_recaptured_after_reclassification():
 
 def test_autotuner_picks_a_valid_candidate():
     case = synth.cylinder_case(256, 128, 256)
-    cand = ensemble.candidates(ibm.IBM_MIXED, tiles=(32, 128), nus=(2,))
+    cand = ensemble.candidates(ibm.IBM_MIXED, tiles=(32, 128), nus=(2,), omegas=(1.0,))
     bad = ibm.ibm_default_opts()
     bad.tile_x = 48                     # invalid: must be reported as failed
     cand.append(bad)
