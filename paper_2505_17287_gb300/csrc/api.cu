@@ -695,6 +695,45 @@ static ibm_status field_ptr(Ctx *c, int field, void **p, size_t *bytes) {
     }
 }
 
+// Host <-> device copy of a field. A pinned host buffer is visible to the GPU
+// (GB300 reaches host memory over NVLink-C2C), so a kernel on every SM pulls
+// or pushes it, faster than one copy engine; pageable memory goes through
+// cudaMemcpyAsync. Both are ordered on the context stream.
+__global__ void k_copy_bytes(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, size_t nb) {
+    const size_t n16 = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0 ? nb / 16 : 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    size_t q = t0;
+    for (; q + 3 * stride < n16; q += 4 * stride) {
+        const uint4 a = s4[q], b = s4[q + stride], c = s4[q + 2 * stride], d = s4[q + 3 * stride];
+        d4[q] = a;
+        d4[q + stride] = b;
+        d4[q + 2 * stride] = c;
+        d4[q + 3 * stride] = d;
+    }
+    for (; q < n16; q += stride) d4[q] = s4[q];
+    for (size_t b = n16 * 16 + t0; b < nb; b += stride) dst[b] = src[b];
+}
+
+static ibm_status host_copy(Ctx *c, void *dst, const void *src, size_t nb, bool to_device) {
+    const void *host = to_device ? src : dst;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, host);
+    if (e == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+        const uint8_t *s8 = (const uint8_t *)(to_device ? a.devicePointer : src);
+        uint8_t *d8 = (uint8_t *)(to_device ? dst : a.devicePointer);
+        ++c->nlaunch;
+        k_copy_bytes<<<152 * 8, 256, 0, c->s>>>(s8, d8, nb);
+        IBM_LAUNCHED(c);
+    } else {
+        cudaGetLastError();
+        IBM_CUDA(c, cudaMemcpyAsync(dst, src, nb, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, c->s));
+    }
+    return IBM_OK;
+}
+
 extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_device, size_t bytes) {
     if (!c || !dst) return IBM_ERR_ARG;
     if (field == IBM_FIELD_STEP) {
@@ -708,7 +747,8 @@ extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_dev
     size_t nb = 0;
     IBM_TRY(field_ptr(c, field, &p, &nb));
     if (bytes != nb) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
-    IBM_CUDA(c, cudaMemcpyAsync(dst, p, nb, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+    if (is_device) IBM_CUDA(c, cudaMemcpyAsync(dst, p, nb, cudaMemcpyDeviceToDevice, c->s));
+    else IBM_TRY(host_copy(c, dst, p, nb, false));
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
     return IBM_OK;
 }
@@ -730,7 +770,8 @@ extern "C" ibm_status ibm_set_field(ibm_ctx *c, int field, const void *src, int 
     size_t nb = 0;
     IBM_TRY(field_ptr(c, field, &p, &nb));
     if (bytes != nb) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
-    IBM_CUDA(c, cudaMemcpyAsync(p, src, nb, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+    if (is_device) IBM_CUDA(c, cudaMemcpyAsync(p, src, nb, cudaMemcpyDeviceToDevice, c->s));
+    else IBM_TRY(host_copy(c, p, src, nb, true));
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
     return IBM_OK;
 }

@@ -269,3 +269,24 @@ def test_error_paths():
         s.set_opts(restart=99)
     assert e.value.status == ibm.IBM_ERR_ARG
     s.close()
+
+
+def test_field_copies_pinned_and_pageable_agree():
+    """ibm_get_field / ibm_set_field through pinned host buffers (copied by a
+    kernel over the host link) and through pageable ones (cudaMemcpyAsync)
+    move the same bytes, including a length that is not a multiple of 16."""
+    import torch
+    case = synth.cylinder_case(97, 53)
+    s = _solver(case)
+    s.step(2)
+    for name in ("u", "face_u", "face_v", "p"):
+        shape = s.field_size(name)
+        ref = s.get(name)                                   # pageable numpy
+        pinned = torch.empty(shape, dtype=torch.float64).pin_memory()
+        ibm.ibm_get_field(s.ctx, ibm.FIELDS[name], pinned.data_ptr(), 0, pinned.numel() * 8)
+        assert np.array_equal(pinned.numpy(), ref), name
+        new = np.random.default_rng(3).uniform(-1, 1, shape)
+        src = torch.from_numpy(new).pin_memory()
+        ibm.ibm_set_field(s.ctx, ibm.FIELDS[name], src.data_ptr(), 0, src.numel() * 8)
+        assert np.array_equal(s.get(name), new), name
+    s.close()
