@@ -245,6 +245,8 @@ static ibm_status build_levels(Ctx *c) {
         c->tJ[a].assign(c->lg.size(), nullptr);
         c->tw64[a].assign(c->lg.size(), nullptr);
         c->tw32[a].assign(c->lg.size(), nullptr);
+        c->tv64[a].assign(c->lg.size(), nullptr);
+        c->tv32[a].assign(c->lg.size(), nullptr);
         c->gI[a].assign(c->lg.size(), nullptr);
         c->gw64[a].assign(c->lg.size(), nullptr);
         c->gw32[a].assign(c->lg.size(), nullptr);
@@ -286,6 +288,21 @@ static ibm_status build_levels(Ctx *c) {
             c->tJ[a][l] = dJ;
             c->tw64[a][l] = dw;
             c->tw32[a][l] = dw32;
+            {
+                std::vector<double> v(nf);
+                std::vector<float> v32(nf);
+                for (int i = 0; i < nf; ++i) {
+                    v[i] = 1.0 - w[i];
+                    v32[i] = 1.0f - w32[i];
+                }
+                double *dv = (double *)dev_alloc(c, sizeof(double) * nf);
+                float *dv32 = (float *)dev_alloc(c, sizeof(float) * nf);
+                if (!dv || !dv32) return c->fail(IBM_ERR_OOM, "transfer table allocation failed");
+                IBM_CUDA(c, cudaMemcpy(dv, v.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+                IBM_CUDA(c, cudaMemcpy(dv32, v32.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
+                c->tv64[a][l] = dv;
+                c->tv32[a][l] = dv32;
+            }
             // transpose: the weight of fine i in coarse I[i] is w, in J[i] it
             // is 1 - w, rounded in each precision as the prolongation rounds it
             std::vector<int> gi((size_t)4 * nc, -1);
@@ -317,6 +334,19 @@ static ibm_status build_levels(Ctx *c) {
         }
     }
     return IBM_OK;
+}
+
+// per-cell volume and FP64 operator diagonal, in the operation order the
+// operator used when it computed them per call: (dx dy) dz, (cxs + cys) + czs
+__global__ void k_cell_metrics(GridDev g, double *__restrict__ vol, double *__restrict__ dg) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        vol[c] = g.dx[i] * g.dy[j] * g.dz[k];
+        double s = g.cxs[i] + g.cys[j];
+        if (g.ndim == 3) s += g.czs[k];
+        dg[c] = s;
+    }
 }
 
 static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
@@ -391,6 +421,12 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
                    c->dx, c->dy, c->dz, c->hx, c->hy, c->hz, cxm, cxp, cxs, cym, cyp, cys, czm, czp, czs,
                    FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny), rdx, rdy, rdz};
     const size_t nb = sizeof(double) * c->N;
+    c->vol_c = (double *)dev_alloc(c, nb);
+    c->dg_c = (double *)dev_alloc(c, nb);
+    if (!c->vol_c || !c->dg_c) return c->fail(IBM_ERR_OOM, "cell metric allocation failed");
+    ++c->nlaunch;
+    k_cell_metrics<<<c->nelem, 256, 0, c->s>>>(c->g, c->vol_c, c->dg_c);
+    IBM_LAUNCHED(c);
     c->type = (uint8_t *)dev_alloc(c, c->N);
     c->inside = (uint8_t *)dev_alloc(c, c->N);
     if (!c->type || !c->inside) return c->fail(IBM_ERR_OOM, "cell arrays allocation failed");

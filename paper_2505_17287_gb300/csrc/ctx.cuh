@@ -102,6 +102,9 @@ struct Ctx {
     double *b = nullptr, *gtmp = nullptr;
     double *hinv[3] = {nullptr, nullptr, nullptr};   // Helmholtz inverse diagonals per component
     bool hinv_ok = false;
+    // per-cell FP64 volume (dx dy dz) and operator diagonal (cxs + cys + czs),
+    // stored so the FP64 operator spends no FP64 instructions rebuilding them
+    double *vol_c = nullptr, *dg_c = nullptr;
     double *htmp = nullptr;   // second buffer of the Jacobi (SRJ) Helmholtz sweeps
     int64_t nstep = 0;
     bool have_nold = false;
@@ -135,8 +138,8 @@ struct Ctx {
     // fine index i interpolates coarse tI[i] with weight tw[i] and coarse
     // tJ[i] (-1: none) with 1 - tw[i]
     std::vector<int *> tI[3], tJ[3];
-    std::vector<double *> tw64[3];
-    std::vector<float *> tw32[3];
+    std::vector<double *> tw64[3], tv64[3];   // tv = 1 - tw, rounded as the kernels did
+    std::vector<float *> tw32[3], tv32[3];
     // the transpose, for restriction: coarse index I gathers from up to four
     // fine indices gI[4I+s] (-1: none) with weights gw[4I+s]
     std::vector<int *> gI[3];

@@ -147,6 +147,7 @@ struct OpT {
     const T *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
     const T *dx, *dy, *dz;
     const T *wp;     // ghost weights, 8 per ghost
+    const T *vol, *dg;   // FP64 only: per-cell volume and diagonal
 };
 
 // (A x)_c of a FLUID cell with the per-axis coefficients; boundary faces
@@ -167,15 +168,13 @@ __device__ __forceinline__ T A_row(const GridDev &g, const OpT<T> &o, const T *_
         }
         return s;
     }
-    // FP64: fewest FP64 instructions (one FMA per neighbour)
+    // FP64: fewest FP64 instructions (one FMA per neighbour, stored diagonal)
     T s = o.cxm[i] * xm + o.cxp[i] * xp + o.cym[j] * ym + o.cyp[j] * yp;
-    T dsum = o.cxs[i] + o.cys[j];
     if (g.ndim == 3) {
         const T zm = k > 0 ? x[c - sz] : xc, zp = k < g.nz - 1 ? x[c + sz] : xc;
         s += o.czm[k] * zm + o.czp[k] * zp;
-        dsum += o.czs[k];
     }
-    return s - dsum * xc;
+    return s - o.dg[c] * xc;
 }
 
 // y = sgn * (A x) + b  on FLUID and DEAD rows (b may be null = 0); GHOST rows
@@ -193,7 +192,8 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
         split3(g, (uint32_t)c, i, j, k);
         const T v = sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
         y[c] = v;
-        acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
+        if constexpr (sizeof(T) == 8) acc += o.vol[c] * v;
+        else acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
     }
     const double tot = block_sum<RED_THREADS>((double)acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -234,12 +234,13 @@ static OpT<T> op_of(Ctx *c);
 template <>
 OpT<double> op_of<double>(Ctx *c) {
     return OpT<double>{c->g.cxm, c->g.cxp, c->g.cxs, c->g.cym, c->g.cyp, c->g.cys, c->g.czm, c->g.czp, c->g.czs,
-                       c->g.dx, c->g.dy, c->g.dz, c->wp};
+                       c->g.dx, c->g.dy, c->g.dz, c->wp, c->vol_c, c->dg_c};
 }
 template <>
 OpT<float> op_of<float>(Ctx *c) {
     const float *const *a = (const float *const *)c->op32;
-    return OpT<float>{a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], c->wp32};
+    return OpT<float>{a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], c->wp32,
+                      nullptr, nullptr};
 }
 
 // y = P(sgn * A x + b)
@@ -645,19 +646,21 @@ __global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx,
 template <typename T>
 struct Xfer {
     const int *Ix, *Jx, *Iy, *Jy, *Iz, *Jz;   // scatter: fine index -> coarse
-    const T *wx, *wy, *wz;
+    const T *wx, *wy, *wz;                    // weight of coarse I
     const int *Gx, *Gy, *Gz;                  // gather: coarse index -> 4 fine
     const T *gwx, *gwy, *gwz;
+    const T *vx, *vy, *vz;                    // weight of coarse J (1 - w)
 };
 
 // the up-to-two coarse indices and weights of fine index i along one axis
 template <typename T>
-__device__ __forceinline__ int xfer_axis(const int *I, const int *J, const T *w, int i, int *idx, T *wt) {
+__device__ __forceinline__ int xfer_axis(const int *I, const int *J, const T *w, const T *v, int i, int *idx,
+                                         T *wt) {
     idx[0] = I[i];
     wt[0] = w[i];
     if (J[i] >= 0) {
         idx[1] = J[i];
-        wt[1] = T(1) - w[i];
+        wt[1] = v[i];
         return 2;
     }
     return 1;
@@ -674,9 +677,9 @@ __global__ void k_pnorm(MGLevel<T> L, MGLevel<T> C, Xfer<T> X, T *__restrict__ p
     if (!active<T, FINE>(L, c)) { pn[c] = T(0); return; }
     int ia[2], ib[2], ic[2];
     T wa[2], wb[2], wc[2];
-    const int na = xfer_axis(X.Ix, X.Jx, X.wx, i, ia, wa);
-    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
-    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
+    const int na = xfer_axis(X.Ix, X.Jx, X.wx, X.vx, i, ia, wa);
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
     T sum = T(0);
     for (int q3 = 0; q3 < nc; ++q3)
         for (int q2 = 0; q2 < nb; ++q2)
@@ -773,9 +776,8 @@ __global__ void k_prolong_x(int fnx, MGLevel<T> C, Xfer<T> X, T *__restrict__ tB
     if (i >= fnx) return;
     const T *xr = C.x + row * C.nx;
     const int J2 = X.Jx[i];
-    const T w = X.wx[i];
-    T v = w * xr[X.Ix[i]];
-    if (J2 >= 0) v += (T(1) - w) * xr[J2];
+    T v = X.wx[i] * xr[X.Ix[i]];
+    if (J2 >= 0) v += X.vx[i] * xr[J2];
     tB[row * fnx + i] = v;
 }
 
@@ -793,8 +795,8 @@ __global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restric
     if (!(p > T(0))) return;
     int ib[2], ic[2];
     T wb[2], wc[2];
-    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, j, ib, wb);
-    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, k, ic, wc);
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
     T acc = T(0);
     for (int q3 = 0; q3 < nc; ++q3) {
         T a2 = T(0);
@@ -960,7 +962,8 @@ __global__ void k_pre_in(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, 
         if (type[c] != FLUID) { f[c] = T(0); continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        f[c] = -(o.dx[i] * o.dy[j] * o.dz[k]) * v[c];
+        if constexpr (sizeof(T) == 8) f[c] = -o.vol[c] * v[c];
+        else f[c] = -(o.dx[i] * o.dy[j] * o.dz[k]) * v[c];
     }
 }
 template <typename T>
@@ -1134,13 +1137,15 @@ template <>
 Xfer<double> xfer_of<double>(Ctx *c, int l) {
     return Xfer<double>{c->tI[0][l],   c->tJ[0][l],   c->tI[1][l],   c->tJ[1][l],   c->tI[2][l],
                         c->tJ[2][l],   c->tw64[0][l], c->tw64[1][l], c->tw64[2][l], c->gI[0][l],
-                        c->gI[1][l],   c->gI[2][l],   c->gw64[0][l], c->gw64[1][l], c->gw64[2][l]};
+                        c->gI[1][l],   c->gI[2][l],   c->gw64[0][l], c->gw64[1][l], c->gw64[2][l],
+                        c->tv64[0][l], c->tv64[1][l], c->tv64[2][l]};
 }
 template <>
 Xfer<float> xfer_of<float>(Ctx *c, int l) {
     return Xfer<float>{c->tI[0][l],   c->tJ[0][l],   c->tI[1][l],   c->tJ[1][l],   c->tI[2][l],
                        c->tJ[2][l],   c->tw32[0][l], c->tw32[1][l], c->tw32[2][l], c->gI[0][l],
-                       c->gI[1][l],   c->gI[2][l],   c->gw32[0][l], c->gw32[1][l], c->gw32[2][l]};
+                       c->gI[1][l],   c->gI[2][l],   c->gw32[0][l], c->gw32[1][l], c->gw32[2][l],
+                       c->tv32[0][l], c->tv32[1][l], c->tv32[2][l]};
 }
 
 template <typename T>
