@@ -519,9 +519,9 @@ __global__ void k_bicg_xr(int64_t n, double *__restrict__ x, const double *__res
 // of a level (FINE: derived from the cell types and 1D metrics)
 template <typename T, bool FINE>
 __device__ __forceinline__ T k_offdiag(const MGLevel<T> &L, const T *__restrict__ x, int64_t c, int i, int j, int k,
-                                       T &d) {
+                                       T &d, T s0 = T(0)) {
     const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
-    T s = T(0);
+    T s = s0;
     if (FINE) {
         d = T(0);
         const unsigned msk = L.omask[c];
@@ -583,7 +583,8 @@ __global__ void k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x,
     const int64_t c = row * L.nx + i;
     if (!active<T, FINE>(L, c)) return;
     T d;
-    const T s = f[c] + k_offdiag<T, FINE>(L, x, c, i, j, k, d);
+    // the stored-coefficient levels accumulate onto f (one FP64 add fewer)
+    const T s = FINE ? f[c] + k_offdiag<T, FINE>(L, x, c, i, j, k, d) : k_offdiag<T, FINE>(L, x, c, i, j, k, d, f[c]);
     if (FINE) {
         if (d > T(0)) x[c] = OMEGA ? x[c] + w * (s / d - x[c]) : s / d;
     } else {
