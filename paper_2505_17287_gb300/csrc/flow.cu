@@ -63,8 +63,9 @@ struct CFields3 {
 // over the volume is 1/width, and the viscous face coefficients are the
 // pressure operator's per-axis coefficients; a Dirichlet wall contributes
 // 2 (value - u_c) / width^2.
-__global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3 u, CFields3 F, CFields3 Nold,
-                           int first, Fields3 Nnew, Fields3 rhs, BCInfo bc, double dt, double alpha, int ncomp) {
+__global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ dg, CFields3 u,
+                           CFields3 F, CFields3 Nold, int first, Fields3 Nnew, Fields3 rhs, BCInfo bc, double dt,
+                           double alpha, int ncomp) {
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) {
@@ -77,6 +78,7 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3
         const int nn[3] = {g.nx, g.ny, g.nz};
         const int64_t st[3] = {1, sy, sz};
         const double rw[3] = {g.rdx[i], g.rdy[j], g.rdz[k]};
+        const double hrw[3] = {0.5 * rw[0], 0.5 * rw[1], 0.5 * rw[2]};
         const double cm[3] = {g.cxm[i], g.cym[j], g.czm[k]}, cp[3] = {g.cxp[i], g.cyp[j], g.czp[k]};
         double Flo[3], Fhi[3];
         Flo[0] = F.p[0][fx_lo(g, i, j, k)];
@@ -89,40 +91,48 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, CFields3
         } else {
             Flo[2] = Fhi[2] = 0.0;
         }
+        const double dint = dg[c];   // sum of the interior face coefficients
         for (int q = 0; q < ncomp; ++q) {
             const double *uq = u.p[q];
             const double uc = uq[c];
-            double N = 0.0, lap = 0.0, src = 0.0;
+            // N: sum over axes of (F_hi * 2 u_hi - F_lo * 2 u_lo) / (2 w), 2 u_f the
+            // sum of the two values at face f. lap = off - D uc with off the
+            // neighbour (and Dirichlet wall) terms and D the diagonal; src is the
+            // wall values' share of the implicit half of Crank-Nicolson.
+            double N = 0.0, off = 0.0, D = dint, src = 0.0;
             for (int a = 0; a < g.ndim; ++a) {
-                double ulo, uhi;
-                const double w2 = 2.0 * rw[a] * rw[a];
+                double slo, shi;
                 if (idx[a] > 0) {
                     const double un = uq[c - st[a]];
-                    ulo = 0.5 * (uc + un);
-                    lap += cm[a] * (un - uc);
+                    slo = uc + un;
+                    off += cm[a] * un;
                 } else if (bc.dir[q][2 * a]) {
-                    ulo = bc.val[q][2 * a];
-                    lap += w2 * (ulo - uc);
-                    src += w2 * ulo;
+                    const double v = bc.val[q][2 * a], w2 = 2.0 * rw[a] * rw[a];
+                    slo = 2.0 * v;
+                    off += w2 * v;
+                    D += w2;
+                    src += w2 * v;
                 } else {
-                    ulo = uc;
+                    slo = 2.0 * uc;
                 }
                 if (idx[a] < nn[a] - 1) {
                     const double un = uq[c + st[a]];
-                    uhi = 0.5 * (uc + un);
-                    lap += cp[a] * (un - uc);
+                    shi = uc + un;
+                    off += cp[a] * un;
                 } else if (bc.dir[q][2 * a + 1]) {
-                    uhi = bc.val[q][2 * a + 1];
-                    lap += w2 * (uhi - uc);
-                    src += w2 * uhi;
+                    const double v = bc.val[q][2 * a + 1], w2 = 2.0 * rw[a] * rw[a];
+                    shi = 2.0 * v;
+                    off += w2 * v;
+                    D += w2;
+                    src += w2 * v;
                 } else {
-                    uhi = uc;
+                    shi = 2.0 * uc;
                 }
-                N += rw[a] * (Fhi[a] * uhi - Flo[a] * ulo);
+                N += hrw[a] * (Fhi[a] * shi - Flo[a] * slo);
             }
             const double No = first ? N : Nold.p[q][c];
             Nnew.p[q][c] = N;
-            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * lap + alpha * src;
+            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * ((off - D * uc) + src);
         }
     }
 }
@@ -691,7 +701,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
     kt_begin(c, K_CONV);
-    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
                                            alpha, nc);
     kt_end(c, K_CONV);
     IBM_LAUNCHED(c);
@@ -905,7 +915,7 @@ static ibm_status flow_step_capture(Ctx *c) {
     CFields3 No{{c->Nold[0], c->Nold[1], nc == 3 ? c->Nold[2] : c->Nold[1]}};
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
-    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, u, F, No, c->have_nold ? 0 : 1, Nn, R,
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, Nn, R,
                                                        make_bc(c), dt, alpha, nc);
     IBM_LAUNCHED(c);
     for (int q = 0; q < nc; ++q) {

@@ -574,10 +574,11 @@ __global__ void k_open_mask(GridDev g, const uint8_t *__restrict__ type, uint8_t
 // red-black Gauss-Seidel, one colour: x_c = (f_c + sum T x_nb) / D_c on the
 // cells of colour col ((i + j + k) even = 0) with D_c > 0; with OMEGA the
 // over-relaxed update x_c += w ((f_c + sum T x_nb) / D_c - x_c)
-// (at most 32 registers: 16 blocks of 128 threads per SM, which the
-// latency-bound FP32 pass needs; no spills)
+// (at most 32 registers, so that 2048 threads fit an SM, which the
+// latency-bound FP32 pass needs; no spills. The bound admits every block
+// size tile_x allows, up to 512 threads.)
 template <typename T, bool FINE, bool OMEGA = false>
-__global__ void __launch_bounds__(128, 16)
+__global__ void __launch_bounds__(512, 4)
     k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col, T w = T(1)) {
     const int64_t row = blockIdx.x;
     const int j = (int)(row % L.ny), k = (int)(row / L.ny);
