@@ -286,10 +286,9 @@ struct VPtrs {
     const T *p[17];
 };
 
-// partial dots: col q < NC: (w, V_q); col NC: (w, w). The column count is a
-// template parameter so every loop is unrolled without predicates; 16-byte
-// loads (the vectors come from cudaMalloc or PyTorch's allocator, 256-byte
-// aligned)
+// partial dots: col q < NC: (w, V_q). The column count is a template
+// parameter so every loop is unrolled without predicates; 16-byte loads (the
+// vectors come from cudaMalloc or PyTorch's allocator, 256-byte aligned)
 template <typename T, int NC>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__restrict__ w, VPtrs<T> V,
                                                       double *__restrict__ part) {
@@ -297,9 +296,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__rest
     typedef typename Vec16<T>::type VT;
     constexpr int W = Vec16<T>::W;
     __shared__ double sh[32];
-    A acc[NC + 1];
+    A acc[NC];
 #pragma unroll
-    for (int q = 0; q <= NC; ++q) acc[q] = A(0);
+    for (int q = 0; q < NC; ++q) acc[q] = A(0);
     const int64_t nv = n / W;
     GRID_STRIDE(v, nv) {
         const VT a = reinterpret_cast<const VT *>(w)[v];
@@ -307,20 +306,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__rest
 #pragma unroll
         for (int q = 0; q < NC; ++q) b[q] = reinterpret_cast<const VT *>(V.p[q])[v];
 #pragma unroll
-        for (int e = 0; e < W; ++e) acc[NC] += (A)vget(a, e) * (A)vget(a, e);
-#pragma unroll
         for (int q = 0; q < NC; ++q)
 #pragma unroll
             for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b[q], e);
     }
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const A a = (A)w[c];
-        acc[NC] += a * a;
 #pragma unroll
         for (int q = 0; q < NC; ++q) acc[q] += a * (A)V.p[q][c];
     }
 #pragma unroll
-    for (int q = 0; q <= NC; ++q) {
+    for (int q = 0; q < NC; ++q) {
         const double t = block_sum<RED_THREADS>((double)acc[q], sh);
         if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
     }
@@ -723,8 +719,9 @@ __global__ void __launch_bounds__(RX_THREADS)
             const T p = relaxed ? T(0) : pn[c];
             if (p > T(0)) {
                 T d;
-                const T off = k_offdiag<T, FINE>(L, x, c, i, j, k, d);
-                g = p * (f[c] - (d * x[c] - off));
+                // r = (f + sum T x_nb) - D x, accumulated onto f
+                const T s = k_offdiag<T, FINE>(L, x, c, i, j, k, d, f[c]);
+                g = p * (s - d * x[c]);
             }
         }
         sg[t] = g;
@@ -1655,16 +1652,21 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             for (int pass = 0; pass < 2; ++pass) {
                 KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, c->part);
-                IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
-                IBM_TRY(sync_scalars(c, S_MD + j + 2));
+                IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
+                IBM_TRY(sync_scalars(c, S_MD + j + 1));
                 Coef h{};
-                for (int i = 0; i <= j; ++i) h.v[i] = c->hscal[S_MD + i];
-                wbefore2 = c->hscal[S_MD + j + 1];
+                double h2 = 0.0;
+                for (int i = 0; i <= j; ++i) {
+                    h.v[i] = c->hscal[S_MD + i];
+                    h2 += h.v[i] * h.v[i];
+                }
                 KL(K_ORTH, orth_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, h, c->part);
                 IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
                 IBM_TRY(sync_scalars(c, S_TMP + 1));
                 wafter2 = c->hscal[S_TMP];
+                // ||w||^2 before the pass, from the orthogonal decomposition
+                wbefore2 = wafter2 + h2;
                 for (int i = 0; i <= j; ++i) hcol[i] += h.v[i];
                 const double eta = c->opts.reorth_eta;
                 if (!(wafter2 <= eta * eta * wbefore2)) break;
@@ -2099,13 +2101,17 @@ __global__ void k_fg_cycle(DevFG *F, const double *rn2, cudaGraphConditionalHand
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-// after the first Gram-Schmidt pass of step j: h in md[0..j], ||w||^2 before
-// in md[j+1], after in *wa2; a second pass when ||w||^2 dropped to eta2 of
-// its value or below
+// after the first Gram-Schmidt pass of step j: h in md[0..j], ||w||^2 after
+// in *wa2; a second pass when ||w||^2 dropped to eta2 of its value before the
+// pass (||w_after||^2 + sum h^2) or below
 __global__ void k_fg_post1(DevFG *F, const double *md, const double *wa2, int j, double eta2) {
-    for (int i = 0; i <= j; ++i) F->hcol[i] = md[i];
-    F->wb = md[j + 1];
+    double h2 = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        F->hcol[i] = md[i];
+        h2 += md[i] * md[i];
+    }
     F->wa = *wa2;
+    F->wb = F->wa + h2;   // ||w||^2 before the pass, from the orthogonal decomposition
     F->reorth = F->wa <= eta2 * F->wb;
 }
 
@@ -2235,7 +2241,7 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
             IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
             KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w, vp,
                c->part);
-            IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
+            IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
             KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
                vp, c->scal + S_MD, c->part);
             IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
@@ -2248,7 +2254,7 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
             {
                 KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
                    vp, c->part);
-                IBM_TRY(finalize(c, c->part, c->nred, j + 2, 1.0, c->scal + S_MD));
+                IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
                 KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, c->scal + S_MD, c->part);
                 IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
