@@ -419,7 +419,10 @@ def main():
     else:
         ms_kt, stats_kt, _, kt = timed(args.steps, kernel_timer=True)
     rb_ms, rb_n = kt["rbgs0"]
-    rb_bytes = rbgs_pass_bytes(N, 8)
+    mixed_main = main_prec == ibm.IBM_MIXED
+    # the finest-level FP32 pass derives its coefficients from the open-face
+    # mask (one byte per cell) instead of reading stored ones
+    rb_bytes = rbgs_pass_bytes(N, 4, stored_coeffs=False) + N * 1.0 if mixed_main else rbgs_pass_bytes(N, 8)
     achieved = rb_bytes / (rb_ms / rb_n / 1e3) / 1e9 if rb_n else None
     peaks = {}
     try:
@@ -430,15 +433,17 @@ def main():
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if mixed_main else "f64", "data": "synthetic",
         "config": {"workload": f"wing NACA0012 AR2 15deg, stretched {args.size.replace(',', 'x')} grid "
-                               f"({N} cells), Re 1000, dt 0.002, Poisson rtol 1e-10, FP64",
+                               f"({N} cells), Re 1000, dt 0.002, Poisson rtol 1e-10, "
+                               + ("mixed (FP32 multigrid cycles inside FP64 refinement)" if mixed_main else "FP64"),
                    "cells": N, "n_ghost": info["n_ghost"], "n_dead": info["n_dead"],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (no flush)"},
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": {"bound": "hbm", "kernel": "k_rbgs<double> (finest level, one colour pass)",
+        "roofline": {"bound": "hbm", "kernel": ("k_rbgs<float, fine>" if mixed_main else "k_rbgs<double>")
+                     + " (finest level, one colour pass)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": RBGS64_TRAFFIC_BYTES if args.size == "384,256,256" and main_prec == ibm.IBM_FP64 else None,

@@ -78,7 +78,9 @@ typedef struct {
     int precision;         /* IBM_FP64 or IBM_MIXED */
     void *stream;          /* cudaStream_t to run on (borrowed); NULL = default stream */
     /* optional device allocator; both NULL = cudaMalloc/cudaFree. The
-       context frees everything it allocated through the same hook. */
+       context frees everything it allocated through the same hook. Blocks
+       must be 16-byte aligned (the streaming kernels use 16-byte accesses);
+       a misaligned block is freed and reported as IBM_ERR_OOM. */
     void *(*alloc)(size_t bytes, void *alloc_ctx);
     void (*free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;

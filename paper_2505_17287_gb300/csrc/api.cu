@@ -23,6 +23,11 @@ void *dev_alloc(Ctx *c, size_t bytes) {
     void *p = nullptr;
     if (c->desc.alloc) {
         p = c->desc.alloc(bytes, c->desc.alloc_ctx);
+        if (p && ((uintptr_t)p & 15u)) {
+            // the vector kernels load and store 16 bytes at a time
+            if (c->desc.free) c->desc.free(p, c->desc.alloc_ctx);
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;

@@ -137,15 +137,15 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
     }
 }
 
-// inverse diagonal of (I - alpha L0) for component q on FLUID cells
-__global__ void k_helm_diag(GridDev g, const uint8_t *__restrict__ type, BCInfo bc, int q, double alpha,
-                            double *__restrict__ hinv) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
-        if (type[c] != FLUID) { hinv[c] = 0.0; continue; }
-        int i, j, k;
-        split3(g, (uint32_t)c, i, j, k);
-        double d = g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0);
-        const double rx2 = 2.0 * g.rdx[i] * g.rdx[i], ry2 = 2.0 * g.rdy[j] * g.rdy[j], rz2 = 2.0 * g.rdz[k] * g.rdz[k];
+// diagonal of (I - alpha L0) for component q at FLUID cell (i, j, k)
+__device__ __forceinline__ double helm_D(const GridDev &g, const BCInfo &bc, int q, double alpha, int i, int j,
+                                         int k) {
+    double d = g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0);
+    const bool edge = i == 0 || i == g.nx - 1 || j == 0 || j == g.ny - 1 ||
+                      (g.ndim == 3 && (k == 0 || k == g.nz - 1));
+    if (edge) {
+        const double rx2 = 2.0 * g.rdx[i] * g.rdx[i], ry2 = 2.0 * g.rdy[j] * g.rdy[j];
+        const double rz2 = 2.0 * g.rdz[k] * g.rdz[k];
         if (i == 0 && bc.dir[q][0]) d += rx2;
         if (i == g.nx - 1 && bc.dir[q][1]) d += rx2;
         if (j == 0 && bc.dir[q][2]) d += ry2;
@@ -154,7 +154,18 @@ __global__ void k_helm_diag(GridDev g, const uint8_t *__restrict__ type, BCInfo 
             if (k == 0 && bc.dir[q][4]) d += rz2;
             if (k == g.nz - 1 && bc.dir[q][5]) d += rz2;
         }
-        hinv[c] = 1.0 / (1.0 + alpha * d);
+    }
+    return 1.0 + alpha * d;
+}
+
+// inverse diagonal of (I - alpha L0) for component q on FLUID cells
+__global__ void k_helm_diag(GridDev g, const uint8_t *__restrict__ type, BCInfo bc, int q, double alpha,
+                            double *__restrict__ hinv) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (type[c] != FLUID) { hinv[c] = 0.0; continue; }
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        hinv[c] = 1.0 / helm_D(g, bc, q, alpha, i, j, k);
     }
 }
 
@@ -201,8 +212,10 @@ __global__ void k_helm_jacobi(GridDev g, const uint8_t *__restrict__ type, const
 }
 
 // residual of the Helmholtz system on FLUID rows; partial columns |r|^2, |rhs|^2
+// (the diagonal is formed again rather than divided out of hinv: an FP64
+// division costs several times the few adds)
 __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                             const double *__restrict__ hinv, const double *__restrict__ u, double alpha,
+                             BCInfo bc, int q, const double *__restrict__ u, double alpha,
                              double *__restrict__ part) {
     __shared__ double sh[32];
     double rr = 0.0, bb = 0.0;
@@ -210,7 +223,7 @@ __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const 
         if (type[c] != FLUID) continue;
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double r = rhs[c] - (u[c] / hinv[c] - alpha * visc_off(g, u, c, i, j, k));
+        const double r = rhs[c] - (u[c] * helm_D(g, bc, q, alpha, i, j, k) - alpha * visc_off(g, u, c, i, j, k));
         rr += r * r;
         bb += rhs[c] * rhs[c];
     }
@@ -618,7 +631,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
         }
         // M is even: the iterate is back in ustar[q]
         Fields3 U{{u, u, u}};
-        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
         IBM_LAUNCHED(c);
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         double gmax = 0.0;
@@ -667,7 +680,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
         }
         ++*sweeps;
         if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
-            ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+            ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
             IBM_LAUNCHED(c);
             IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
             double gmax = 0.0;
@@ -867,7 +880,7 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
         }
     }
-    ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, c->part);
+    ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
     IBM_LAUNCHED(c);
     IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
     if (c->ng > 0) {

@@ -199,6 +199,71 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+// FP32 operator product four cells at a time, for grids whose rows hold a
+// multiple of four cells (16-byte aligned vectors): one 16-byte load per
+// neighbour direction and the four cell types in one word, so each thread
+// keeps several loads in flight where the one-cell loop stalls on load
+// latency. Each cell gets the same expression as A_row<float>; GHOST cells
+// are computed but not stored. The partial sums add a quad's cells in x order.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float f4get(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ uint8_t u4get(const uchar4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_apply_A4(GridDev g, OpT<float> o, const uint8_t *__restrict__ type, const float *__restrict__ x,
+               const float *__restrict__ b, float sgn, float *__restrict__ y, double *__restrict__ part) {
+    __shared__ double sh[32];
+    float acc = 0.f;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    GRID_STRIDE(q, g.n / 4) {
+        const int64_t c = 4 * q;
+        const uchar4 t4 = reinterpret_cast<const uchar4 *>(type)[q];
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        const float4 xc = ld4(x + c);
+        const float xl = i > 0 ? x[c - 1] : xc.x;
+        const float xr = i + 4 < g.nx ? x[c + 4] : xc.w;
+        const float4 ym = j > 0 ? ld4(x + c - sy) : xc;
+        const float4 yp = j < g.ny - 1 ? ld4(x + c + sy) : xc;
+        float4 zm = xc, zp = xc;
+        if (g.ndim == 3) {
+            if (k > 0) zm = ld4(x + c - sz);
+            if (k < g.nz - 1) zp = ld4(x + c + sz);
+        }
+        const float4 bb = b ? ld4(b + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 cm = ld4(o.cxm + i), cp = ld4(o.cxp + i), dxv = ld4(o.dx + i);
+        const float cym = o.cym[j], cyp = o.cyp[j], dyj = o.dy[j], dzk = o.dz[k];
+        const float czm = g.ndim == 3 ? o.czm[k] : 0.f, czp = g.ndim == 3 ? o.czp[k] : 0.f;
+        float out[4];
+        bool ghost = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float xe = f4get(xc, e);
+            const float xm = e == 0 ? xl : f4get(xc, e - 1);
+            const float xp = e == 3 ? xr : f4get(xc, e + 1);
+            float s = f4get(cm, e) * (xm - xe) + f4get(cp, e) * (xp - xe) + cym * (f4get(ym, e) - xe) +
+                      cyp * (f4get(yp, e) - xe);
+            if (g.ndim == 3) s += czm * (f4get(zm, e) - xe) + czp * (f4get(zp, e) - xe);
+            const float v = sgn * s + f4get(bb, e);
+            const uint8_t t = u4get(t4, e);
+            ghost |= t == GHOST;
+            out[e] = t == DEAD ? 0.f : v;
+            if (t == FLUID) acc += (f4get(dxv, e) * dyj * dzk) * v;
+        }
+        if (!ghost) {
+            *reinterpret_cast<float4 *>(y + c) = make_float4(out[0], out[1], out[2], out[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (u4get(t4, e) != GHOST) y[c + e] = out[e];
+        }
+    }
+    const double tot = block_sum<RED_THREADS>((double)acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+static inline bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 // GHOST rows: y_g = sgn * (x_g - sum_m wp_m x_m) + b_g (b may be null = 0;
 // the pressure equation has b_g = 0, a defect-correction right-hand side not)
 template <typename T>
@@ -218,11 +283,25 @@ __global__ void k_zero_at(int64_t m, const int64_t *__restrict__ idx, double *__
 }
 
 // x -= mean on FLUID cells (precision T); DEAD cells set to 0
+// (FP32: four cells per 16-byte access, the tail one by one)
 template <typename T>
 __global__ void k_sub_meanT(int64_t n, const uint8_t *__restrict__ type, T *__restrict__ x,
                             const double *__restrict__ mean) {
     const T m = (T)*mean;
-    GRID_STRIDE(c, n) {
+    int64_t n0 = 0;
+    if constexpr (sizeof(T) == 4) {
+        n0 = n / 4 * 4;
+        GRID_STRIDE(q, n / 4) {
+            const uchar4 t4 = reinterpret_cast<const uchar4 *>(type)[q];
+            float4 a = reinterpret_cast<const float4 *>(x)[q];
+            a.x = t4.x == FLUID ? a.x - m : (t4.x == DEAD ? 0.f : a.x);
+            a.y = t4.y == FLUID ? a.y - m : (t4.y == DEAD ? 0.f : a.y);
+            a.z = t4.z == FLUID ? a.z - m : (t4.z == DEAD ? 0.f : a.z);
+            a.w = t4.w == FLUID ? a.w - m : (t4.w == DEAD ? 0.f : a.w);
+            reinterpret_cast<float4 *>(x)[q] = a;
+        }
+    }
+    for (int64_t c = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t == FLUID) x[c] -= m;
         else if (t == DEAD) x[c] = T(0);
@@ -248,7 +327,14 @@ template <typename T>
 static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
     const OpT<T> o = op_of<T>(c);
     const int nb = sizeof(T) == 4 ? c->nred_wide : c->nred;
-    KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    if constexpr (sizeof(T) == 4) {
+        if (c->g.nx % 4 == 0 && al16(x) && al16(y) && (!b || al16(b)))
+            KL(K_APPLY_A, k_apply_A4, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+        else
+            KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    } else {
+        KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    }
     IBM_LAUNCHED(c);
     if (c->ng > 0) {
         KL(-1, k_ghost_rows<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o, x, b, sgn, y);
@@ -372,9 +458,27 @@ static const OrthFn<T> *orth_table(std::integer_sequence<int, I...>) {
     return t;
 }
 
+// dst = a src. FP32 to FP32 in FP32 arithmetic, four elements per 16-byte
+// access (per-element FP64 arithmetic makes an FP32 stream FP64-bound)
+__device__ __forceinline__ void scale_f32(int64_t n, float *__restrict__ dst, const float *__restrict__ src,
+                                          float a) {
+    GRID_STRIDE(q, n / 4) {
+        float4 v = reinterpret_cast<const float4 *>(src)[q];
+        v.x *= a;
+        v.y *= a;
+        v.z *= a;
+        v.w *= a;
+        reinterpret_cast<float4 *>(dst)[q] = v;
+    }
+    for (int64_t c = n / 4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        dst[c] = a * src[c];
+}
+
 template <typename T, typename S>
 __global__ void k_scale(int64_t n, T *__restrict__ dst, const S *__restrict__ src, double a) {
-    GRID_STRIDE(c, n) dst[c] = (T)(a * (double)src[c]);
+    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) scale_f32(n, dst, src, (float)a);
+    else GRID_STRIDE(c, n) dst[c] = (T)(a * (double)src[c]);
 }
 
 // x += sum_i y_i Z_i
@@ -968,9 +1072,37 @@ __global__ void k_pre_in(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, 
         else f[c] = -(o.dx[i] * o.dy[j] * o.dz[k]) * v[c];
     }
 }
+// FP32 input four cells at a time (rows of a multiple of four cells)
+__global__ void k_pre_in4(GridDev g, OpT<float> o, const uint8_t *__restrict__ type, const float *__restrict__ v,
+                          float *__restrict__ f) {
+    GRID_STRIDE(q, g.n / 4) {
+        const int64_t c = 4 * q;
+        const uchar4 t4 = reinterpret_cast<const uchar4 *>(type)[q];
+        int i, j, k;
+        split3(g, (uint32_t)c, i, j, k);
+        const float4 vv = ld4(v + c), dxv = ld4(o.dx + i);
+        const float dyj = o.dy[j], dzk = o.dz[k];
+        float out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            out[e] = u4get(t4, e) == FLUID ? -(f4get(dxv, e) * dyj * dzk) * f4get(vv, e) : 0.f;
+        *reinterpret_cast<float4 *>(f + c) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+}
 template <typename T>
 __global__ void k_pre_out(int64_t n, const uint8_t *__restrict__ type, const T *__restrict__ x, T *__restrict__ z) {
-    GRID_STRIDE(c, n) z[c] = type[c] == FLUID ? x[c] : T(0);
+    int64_t n0 = 0;
+    if constexpr (sizeof(T) == 4) {
+        n0 = n / 4 * 4;
+        GRID_STRIDE(q, n / 4) {
+            const uchar4 t4 = reinterpret_cast<const uchar4 *>(type)[q];
+            const float4 a = reinterpret_cast<const float4 *>(x)[q];
+            reinterpret_cast<float4 *>(z)[q] = make_float4(t4.x == FLUID ? a.x : 0.f, t4.y == FLUID ? a.y : 0.f,
+                                                           t4.z == FLUID ? a.z : 0.f, t4.w == FLUID ? a.w : 0.f);
+        }
+    }
+    for (int64_t c = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        z[c] = type[c] == FLUID ? x[c] : T(0);
 }
 // ghost rows of the preconditioner: z_g = v_g + sum over FLUID corners wp z_m
 template <typename T>
@@ -1550,7 +1682,14 @@ static ibm_status pcg(Ctx *c, MGHier<T> &H, int iters) {
 template <typename T>
 static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
     const OpT<T> oin = op_of<T>(c);
-    KL(-1, k_pre_in<T>, c->nred_wide, RED_THREADS, c->g, oin, c->type, v, H.pr);
+    if constexpr (sizeof(T) == 4) {
+        if (c->g.nx % 4 == 0 && al16(v) && al16(H.pr))
+            KL(-1, k_pre_in4, c->nred_wide, RED_THREADS, c->g, oin, c->type, v, H.pr);
+        else
+            KL(-1, k_pre_in<T>, c->nred_wide, RED_THREADS, c->g, oin, c->type, v, H.pr);
+    } else {
+        KL(-1, k_pre_in<T>, c->nred_wide, RED_THREADS, c->g, oin, c->type, v, H.pr);
+    }
     IBM_LAUNCHED(c);
     const T *xin = H.px;
     if (c->opts.precond == 1) {
@@ -1979,7 +2118,8 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, const int *flag) { cuda
 template <typename T, typename S>
 __global__ void k_scale_dev(int64_t n, T *__restrict__ dst, const S *__restrict__ src, const double *__restrict__ a) {
     const double f = *a;
-    GRID_STRIDE(c, n) dst[c] = (T)(f * (double)src[c]);
+    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) scale_f32(n, dst, src, (float)f);
+    else GRID_STRIDE(c, n) dst[c] = (T)(f * (double)src[c]);
 }
 
 // w -= sum_q h_q V_q with h in device memory; partial (w, w)
