@@ -897,19 +897,28 @@ __global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restric
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
-    const T p = pn[c];
-    if (!(p > T(0))) return;
+    // pn, x and the (up to four) tB values are loaded together; the
+    // interpolation indices depend on the row only
     int ib[2], ic[2];
     T wb[2], wc[2];
     const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
     const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
+    T tv[2][2];
+#pragma unroll
+    for (int q3 = 0; q3 < 2; ++q3)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+            tv[q3][q2] = tB[((int64_t)ic[q3 < nc ? q3 : 0] * cny + ib[q2 < nb ? q2 : 0]) * L.nx + i];
+    const T p = pn[c];
+    const T xc = x[c];
+    if (!(p > T(0))) return;
     T acc = T(0);
     for (int q3 = 0; q3 < nc; ++q3) {
         T a2 = T(0);
-        for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * tB[((int64_t)ic[q3] * cny + ib[q2]) * L.nx + i];
+        for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * tv[q3][q2];
         acc += wc[q3] * a2;
     }
-    x[c] += acc * p;
+    x[c] = xc + acc * p;
 }
 
 // coarsest level: red-black sweeps in one block, all data in shared memory.
