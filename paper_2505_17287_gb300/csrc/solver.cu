@@ -179,7 +179,9 @@ __device__ __forceinline__ T A_row(const GridDev &g, const OpT<T> &o, const T *_
 
 // y = sgn * (A x) + b  on FLUID and DEAD rows (b may be null = 0); GHOST rows
 // are written by k_ghost_rows. Partials (FP64): sum over FLUID of vol * y.
-template <typename T>
+// (PLAIN: b null and sgn = 1, the product of every Krylov step; two FP64
+// operations per cell fewer)
+template <typename T, bool PLAIN = false>
 __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type, const T *__restrict__ x,
                           const T *__restrict__ b, T sgn, T *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
@@ -190,7 +192,7 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
         if (t == DEAD) { y[c] = T(0); continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const T v = sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
+        const T v = PLAIN ? A_row<T>(g, o, x, c, i, j, k) : sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
         y[c] = v;
         if constexpr (sizeof(T) == 8) acc += o.vol[c] * v;
         else acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
@@ -332,6 +334,8 @@ static ibm_status apply_PA(Ctx *c, const T *x, const T *b, T sgn, T *y) {
             KL(K_APPLY_A, k_apply_A4, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
         else
             KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
+    } else if (!b && sgn == T(1)) {
+        KL(K_APPLY_A, (k_apply_A<T, true>), nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     } else {
         KL(K_APPLY_A, k_apply_A<T>, nb, RED_THREADS, c->g, o, c->type, x, b, sgn, y, c->part);
     }
@@ -615,6 +619,12 @@ __global__ void k_bicg_xr(int64_t n, double *__restrict__ x, const double *__res
 // multigrid on the staircase operator, precision T
 // ---------------------------------------------------------------------------
 
+// v > 0 for the non-negative tables pn and dinv: an integer test of the bit
+// pattern for FP64 (an FP64 compare occupies GB300's slow FP64 pipe; -0 and
+// +0 both read as not positive)
+__device__ __forceinline__ bool pos(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool pos(float v) { return v > 0.f; }
+
 // sum over the open faces of T_f x_nb, and the diagonal sum T_f, at cell c
 // of a level (FINE: derived from the cell types and 1D metrics)
 template <typename T, bool FINE>
@@ -648,7 +658,7 @@ __device__ __forceinline__ T k_offdiag(const MGLevel<T> &L, const T *__restrict_
 template <typename T, bool FINE>
 __device__ __forceinline__ bool active(const MGLevel<T> &L, int64_t c) {
     if (FINE) return (L.omask[c] & 0x80u) != 0;
-    return L.dinv[c] > T(0);
+    return pos(L.dinv[c]);
 }
 
 // open-face mask of the finest level
@@ -814,21 +824,39 @@ __global__ void __launch_bounds__(RX_THREADS)
     const int I0 = blockIdx.y * RX_THREADS;
     const int lo = fx == 2 ? 2 * I0 - 1 : I0;
     const int cnt = fx == 2 ? 2 * RX_THREADS + 2 : RX_THREADS;
-    for (int t = threadIdx.x; t < cnt; t += RX_THREADS) {
+    // pn r at fine cell lo + t (0 outside the row)
+    auto pr = [&](int t) -> T {
         const int i = lo + t;
-        T g = T(0);
-        if (i >= 0 && i < L.nx) {
-            const int64_t c = row * L.nx + i;
-            const bool relaxed = ((i + j + k) & 1) == zcol && (FINE ? (L.omask[c] & 0x3fu) != 0 : true);
-            const T p = relaxed ? T(0) : pn[c];
-            if (p > T(0)) {
-                T d;
-                // r = (f + sum T x_nb) - D x, accumulated onto f
-                const T s = k_offdiag<T, FINE>(L, x, c, i, j, k, d, f[c]);
-                g = p * (s - d * x[c]);
-            }
+        if (i < 0 || i >= L.nx) return T(0);
+        const int64_t c = row * L.nx + i;
+        const T p = pn[c];
+        if (!pos(p)) return T(0);
+        T d;
+        // r = (f + sum T x_nb) - D x, accumulated onto f
+        const T s = k_offdiag<T, FINE>(L, x, c, i, j, k, d, f[c]);
+        return p * (s - d * x[c]);
+    };
+    if (!FINE && zcol >= 0) {
+        // The lanes of a warp take cells of one colour, so that the skipped
+        // colour leaves no idle lanes in the warps that evaluate the other
+        // (with alternating colours per lane every warp paid the full
+        // stencil: on GB300's FP64 pipe that doubled the cost).
+        const int r0 = ((lo + j + k) & 1) == zcol ? 0 : 1;   // first relaxed slot
+        for (int u = threadIdx.x; 2 * u + (1 - r0) < cnt; u += RX_THREADS) {
+            const int t = 2 * u + (1 - r0);
+            sg[t] = pr(t);
         }
-        sg[t] = g;
+        for (int u = threadIdx.x; 2 * u + r0 < cnt; u += RX_THREADS) sg[2 * u + r0] = T(0);
+    } else {
+        // the finest FP32 level (latency-bound, not pipe-bound) keeps one
+        // slot per lane: the colour split cost it registers and warps. A
+        // relaxed cell is skipped only if it has an open face (it was updated).
+        for (int t = threadIdx.x; t < cnt; t += RX_THREADS) {
+            const int i = lo + t;
+            const bool relaxed = FINE && ((i + j + k) & 1) == zcol && i >= 0 && i < L.nx &&
+                                 (L.omask[row * L.nx + i] & 0x3fu) != 0;
+            sg[t] = relaxed ? T(0) : pr(t);
+        }
     }
     __syncthreads();
     const int I = I0 + threadIdx.x;
@@ -854,7 +882,7 @@ __global__ void k_restrict_yz(MGLevel<T> C, const T *__restrict__ tA, int fny, X
     if (Ic >= C.nx) return;
     const int64_t cc = row * C.nx + Ic;
     C.x[cc] = T(0);
-    if (!(C.dinv[cc] > T(0))) { C.f[cc] = T(0); return; }
+    if (!pos(C.dinv[cc])) { C.f[cc] = T(0); return; }
     T acc = T(0);
 #pragma unroll
     for (int s3 = 0; s3 < 4; ++s3) {
@@ -911,7 +939,7 @@ __global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restric
             tv[q3][q2] = tB[((int64_t)ic[q3 < nc ? q3 : 0] * cny + ib[q2 < nb ? q2 : 0]) * L.nx + i];
     const T p = pn[c];
     const T xc = x[c];
-    if (!(p > T(0))) return;
+    if (!pos(p)) return;
     T acc = T(0);
     for (int q3 = 0; q3 < nc; ++q3) {
         T a2 = T(0);
