@@ -140,6 +140,12 @@ typedef struct {
                            the usual 1/sqrt(2) fires in most steps here, where the
                            multigrid-preconditioned vectors lie close to the basis, and
                            buys no iteration */
+    int helm_check_first; /* Helmholtz red-black solve: sweeps before the first residual
+                           test, >= 1; later tests follow at s + max(2, s / 4) sweeps
+                           (s the sweep count of the previous test), so that a solve
+                           needing n sweeps takes O(log n) tests. Each test costs
+                           about one and a half sweeps in FP64; default 6, the count
+                           the 3D wing's components need at helm_rtol 1e-12 */
 } ibm_solver_opts;
 
 typedef struct {
@@ -196,7 +202,8 @@ enum {
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
-   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3. */
+   tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
+   helm_check_first 6. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

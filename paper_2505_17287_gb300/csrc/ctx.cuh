@@ -102,6 +102,7 @@ struct Ctx {
     double *b = nullptr, *gtmp = nullptr;
     double *hinv[3] = {nullptr, nullptr, nullptr};   // Helmholtz inverse diagonals per component
     bool hinv_ok = false;
+    double *hac = nullptr;   // alpha-scaled viscous face coefficients: x-, x+ (nx each), y-, y+, z-, z+
     // per-cell FP64 volume (dx dy dz) and operator diagonal (cxs + cys + czs),
     // stored so the FP64 operator spends no FP64 instructions rebuilding them
     double *vol_c = nullptr, *dg_c = nullptr;

@@ -92,47 +92,57 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
             Flo[2] = Fhi[2] = 0.0;
         }
         const double dint = dg[c];   // sum of the interior face coefficients
+        // N = sum over axes of (F_hi (u_c + u_hi) - F_lo (u_c + u_lo)) / (2 w)
+        //   = u_c sum_a (fh_a - fl_a) + sum_a (fh_a u_hi - fl_a u_lo),
+        // fh = F_hi / (2 w), fl = F_lo / (2 w) shared by the components (the
+        // factored form takes a third of the FP64 operations per component);
+        // at a wall u_lo (u_hi) is 2 v - u_c for a Dirichlet value v and u_c
+        // otherwise (zero gradient)
+        double fl[3], fh[3], dF = 0.0;
+        for (int a = 0; a < g.ndim; ++a) {
+            fl[a] = hrw[a] * Flo[a];
+            fh[a] = hrw[a] * Fhi[a];
+            dF += fh[a] - fl[a];
+        }
+        const double c15 = 1.5 * dt, c05 = 0.5 * dt;
         for (int q = 0; q < ncomp; ++q) {
             const double *uq = u.p[q];
             const double uc = uq[c];
-            // N: sum over axes of (F_hi * 2 u_hi - F_lo * 2 u_lo) / (2 w), 2 u_f the
-            // sum of the two values at face f. lap = off - D uc with off the
-            // neighbour (and Dirichlet wall) terms and D the diagonal; src is the
-            // wall values' share of the implicit half of Crank-Nicolson.
-            double N = 0.0, off = 0.0, D = dint, src = 0.0;
+            // lap = off - D uc with off the neighbour (and Dirichlet wall)
+            // terms and D the diagonal; src is the wall values' share of the
+            // implicit half of Crank-Nicolson
+            double N = dF * uc, off = 0.0, D = dint, src = 0.0;
             for (int a = 0; a < g.ndim; ++a) {
-                double slo, shi;
+                double ulo, uhi;
                 if (idx[a] > 0) {
-                    const double un = uq[c - st[a]];
-                    slo = uc + un;
-                    off += cm[a] * un;
+                    ulo = uq[c - st[a]];
+                    off += cm[a] * ulo;
                 } else if (bc.dir[q][2 * a]) {
                     const double v = bc.val[q][2 * a], w2 = 2.0 * rw[a] * rw[a];
-                    slo = 2.0 * v;
+                    ulo = 2.0 * v - uc;
                     off += w2 * v;
                     D += w2;
                     src += w2 * v;
                 } else {
-                    slo = 2.0 * uc;
+                    ulo = uc;
                 }
                 if (idx[a] < nn[a] - 1) {
-                    const double un = uq[c + st[a]];
-                    shi = uc + un;
-                    off += cp[a] * un;
+                    uhi = uq[c + st[a]];
+                    off += cp[a] * uhi;
                 } else if (bc.dir[q][2 * a + 1]) {
                     const double v = bc.val[q][2 * a + 1], w2 = 2.0 * rw[a] * rw[a];
-                    shi = 2.0 * v;
+                    uhi = 2.0 * v - uc;
                     off += w2 * v;
                     D += w2;
                     src += w2 * v;
                 } else {
-                    shi = 2.0 * uc;
+                    uhi = uc;
                 }
-                N += hrw[a] * (Fhi[a] * shi - Flo[a] * slo);
+                N += fh[a] * uhi - fl[a] * ulo;
             }
             const double No = first ? N : Nold.p[q][c];
             Nnew.p[q][c] = N;
-            rhs.p[q][c] = uc - dt * (1.5 * N - 0.5 * No) + alpha * ((off - D * uc) + src);
+            rhs.p[q][c] = (uc - c15 * N + c05 * No) + alpha * ((off - D * uc) + src);
         }
     }
 }
@@ -169,52 +179,64 @@ __global__ void k_helm_diag(GridDev g, const uint8_t *__restrict__ type, BCInfo 
     }
 }
 
-// off-diagonal sum sum_f c_f u_nb of the viscous operator (interior faces)
-__device__ __forceinline__ double visc_off(const GridDev &g, const double *__restrict__ u, int64_t c, int i, int j,
-                                           int k) {
+// the viscous face coefficients times alpha (per axis, low and high face)
+struct HelmCoef {
+    const double *xm, *xp, *ym, *yp, *zm, *zp;
+};
+
+// s0 + alpha sum_f c_f u_nb over the interior faces, accumulated onto s0
+// (one FP64 FMA per face: the scaling by alpha is folded into the stored
+// coefficients)
+__device__ __forceinline__ double visc_sum(const GridDev &g, const HelmCoef &h, const double *__restrict__ u,
+                                           int64_t c, int i, int j, int k, double s0) {
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    double s = 0.0;
-    if (i > 0) s += g.cxm[i] * u[c - 1];
-    if (i < g.nx - 1) s += g.cxp[i] * u[c + 1];
-    if (j > 0) s += g.cym[j] * u[c - sy];
-    if (j < g.ny - 1) s += g.cyp[j] * u[c + sy];
+    double s = s0;
+    if (i > 0) s += h.xm[i] * u[c - 1];
+    if (i < g.nx - 1) s += h.xp[i] * u[c + 1];
+    if (j > 0) s += h.ym[j] * u[c - sy];
+    if (j < g.ny - 1) s += h.yp[j] * u[c + sy];
     if (g.ndim == 3) {
-        if (k > 0) s += g.czm[k] * u[c - sz];
-        if (k < g.nz - 1) s += g.czp[k] * u[c + sz];
+        if (k > 0) s += h.zm[k] * u[c - sz];
+        if (k < g.nz - 1) s += h.zp[k] * u[c + sz];
     }
     return s;
 }
 
+__global__ void k_scaled_copy(int n, const double *__restrict__ src, double a, double *__restrict__ dst) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = a * src[t];
+}
+
 // Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
-__global__ void k_helm_rb(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                          const double *__restrict__ hinv, double *__restrict__ u, double alpha, int col) {
+__global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+                          const double *__restrict__ hinv, double *__restrict__ u, int col) {
     const int64_t row = blockIdx.x;
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
     const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
     if (i >= g.nx) return;
     const int64_t c = row * g.nx + i;
     if (type[c] != FLUID) return;
-    u[c] = (rhs[c] + alpha * visc_off(g, u, c, i, j, k)) * hinv[c];
+    u[c] = visc_sum(g, h, u, c, i, j, k, rhs[c]) * hinv[c];
 }
 
 // one damped-Jacobi sweep of the Helmholtz system: out = u + w (D^{-1}(rhs +
 // alpha L_off u) - u) on FLUID cells, u elsewhere (ghost rows are refreshed after)
-__global__ void k_helm_jacobi(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+__global__ void k_helm_jacobi(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
                               const double *__restrict__ hinv, const double *__restrict__ u, double *__restrict__ out,
-                              double alpha, double w) {
+                              double w) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         const double uc = u[c];
         if (type[c] != FLUID) { out[c] = uc; continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        out[c] = uc + w * ((rhs[c] + alpha * visc_off(g, u, c, i, j, k)) * hinv[c] - uc);
+        out[c] = uc + w * (visc_sum(g, h, u, c, i, j, k, rhs[c]) * hinv[c] - uc);
     }
 }
 
 // residual of the Helmholtz system on FLUID rows; partial columns |r|^2, |rhs|^2
 // (the diagonal is formed again rather than divided out of hinv: an FP64
 // division costs several times the few adds)
-__global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+__global__ void k_helm_resid(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
                              BCInfo bc, int q, const double *__restrict__ u, double alpha,
                              double *__restrict__ part) {
     __shared__ double sh[32];
@@ -223,7 +245,7 @@ __global__ void k_helm_resid(GridDev g, const uint8_t *__restrict__ type, const 
         if (type[c] != FLUID) continue;
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double r = rhs[c] - (u[c] * helm_D(g, bc, q, alpha, i, j, k) - alpha * visc_off(g, u, c, i, j, k));
+        const double r = visc_sum(g, h, u, c, i, j, k, rhs[c]) - u[c] * helm_D(g, bc, q, alpha, i, j, k);
         rr += r * r;
         bb += rhs[c] * rhs[c];
     }
@@ -561,11 +583,32 @@ ibm_status flow_init(Ctx *c) {
     return IBM_OK;
 }
 
+// sweep count of the residual test after one at s sweeps (the first test
+// comes after opts.helm_check_first sweeps): gaps grow with s, so a solve
+// that needs n sweeps takes O(log n) tests and overshoots by at most n / 4
+__host__ __device__ __forceinline__ int helm_next_check(int s) { return s + (s / 4 > 2 ? s / 4 : 2); }
+
+static HelmCoef helm_coef(const Ctx *c) {
+    const int nx = c->desc.nx, ny = c->desc.ny, nz = c->desc.ndim == 3 ? c->desc.nz : 1;
+    const double *h = c->hac;
+    return HelmCoef{h, h + nx, h + 2 * nx, h + 2 * nx + ny, h + 2 * nx + 2 * ny, h + 2 * nx + 2 * ny + nz};
+}
+
 // Helmholtz solve for component q, u = ustar (initial guess u^n)
 static ibm_status helm_prepare(Ctx *c) {
     const BCInfo bc = make_bc(c);
     const double alpha = c->desc.dt / (2.0 * c->desc.Re);
     if (!c->hinv_ok) {
+        const int nx = c->desc.nx, ny = c->desc.ny, nz = c->desc.ndim == 3 ? c->desc.nz : 1;
+        if (!c->hac) c->hac = (double *)dev_alloc(c, sizeof(double) * 2 * (size_t)(nx + ny + nz));
+        if (!c->hac) return c->fail(IBM_ERR_OOM, "Helmholtz coefficient allocation failed");
+        const double *src[6] = {c->g.cxm, c->g.cxp, c->g.cym, c->g.cyp, c->g.czm, c->g.czp};
+        const int len[6] = {nx, nx, ny, ny, nz, nz};
+        size_t off = 0;
+        for (int a = 0; a < 6; ++a) {
+            ++c->nlaunch, k_scaled_copy<<<(len[a] + 255) / 256, 256, 0, c->s>>>(len[a], src[a], alpha, c->hac + off);
+            off += (size_t)len[a];
+        }
         for (int cq = 0; cq < c->ndim; ++cq) {
             if (!c->hinv[cq]) c->hinv[cq] = (double *)dev_alloc(c, sizeof(double) * c->N);
             if (!c->hinv[cq]) return c->fail(IBM_ERR_OOM, "Helmholtz diagonal allocation failed");
@@ -616,7 +659,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
     for (int it = 0; it < c->opts.helm_maxit; it += M) {
         for (int k = 0; k < M; ++k) {
             kt_begin(c, K_HELM);
-            ++c->nlaunch, k_helm_jacobi<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, rhs, hinv, u, t, alpha, w[k]);
+            ++c->nlaunch, k_helm_jacobi<<<c->nelem, 256, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, t, w[k]);
             kt_end(c, K_HELM);
             if (c->ng > 0) {
                 Fields3 T3{{t, t, t}};
@@ -631,7 +674,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
         }
         // M is even: the iterate is back in ustar[q]
         Fields3 U{{u, u, u}};
-        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
+        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, make_bc(c), q, u, alpha, c->part);
         IBM_LAUNCHED(c);
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         double gmax = 0.0;
@@ -660,17 +703,17 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     const double *hinv = c->hinv[q];
     double *u = c->ustar[q];
     const double *rhs = c->rhs[q];
-    const int check_every = 4;
+    int next_check = c->opts.helm_check_first;
     *sweeps = 0;
     double rhs2 = -1.0;
     const unsigned gb = (unsigned)((c->ng + 255) / 256);
     Fields3 U{{u, u, u}};
     for (int it = 0; it < c->opts.helm_maxit; ++it) {
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 0);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 0);
         kt_end(c, K_HELM);
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 1);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 1);
         kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
@@ -679,8 +722,9 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
             IBM_LAUNCHED(c);
         }
         ++*sweeps;
-        if ((it + 1) % check_every == 0 || it + 1 == c->opts.helm_maxit) {
-            ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
+        if (*sweeps == next_check || it + 1 == c->opts.helm_maxit) {
+            next_check = helm_next_check(next_check);
+            ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, make_bc(c), q, u, alpha, c->part);
             IBM_LAUNCHED(c);
             IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
             double gmax = 0.0;
@@ -809,22 +853,37 @@ struct HelmCtl {
     int status;   // IBM_ERR_DIVERGED / IBM_ERR_NOT_CONVERGED of the Helmholtz or ghost loops
     double rhs2;
     int passes;
+    int next_check;   // sweep count of the next Helmholtz residual test
+    int due;          // a test runs after the current sweep
 };
 
-__global__ void k_hc_reset(HelmCtl *H, int q, cudaGraphConditionalHandle h) {
+__global__ void k_hc_reset(HelmCtl *H, int q, int first_check, cudaGraphConditionalHandle h) {
     if (q == 0) H->status = 0;
     if (q >= 0) {
         H->sweeps[q] = 0;
         H->rhs2 = -1.0;
+        H->next_check = first_check;
     } else {
         H->passes = 0;
     }
     cudaGraphSetConditional(h, 1u);
 }
 
+// after each sweep: count it and open the residual test when it is due
+__global__ void k_helm_tick(HelmCtl *H, int q, int maxit, cudaGraphConditionalHandle hif) {
+    const int s = ++H->sweeps[q];
+    const bool due = s == H->next_check || s >= maxit;
+    if (due) H->next_check = helm_next_check(H->next_check);
+    H->due = due;
+    cudaGraphSetConditional(hif, due ? 1u : 0u);
+}
+
 __global__ void k_helm_decide(HelmCtl *H, int q, const double *__restrict__ scal, int has_ghost, double tol,
-                              double scale, int maxit, int trip, cudaGraphConditionalHandle h) {
-    H->sweeps[q] += trip;
+                              double scale, int maxit, cudaGraphConditionalHandle h) {
+    if (!H->due) {
+        cudaGraphSetConditional(h, 1u);
+        return;
+    }
     const double r2 = scal[48];
     if (H->rhs2 < 0.0) H->rhs2 = scal[49];
     const double gmax = has_ghost ? scal[50] : 0.0;
@@ -866,30 +925,39 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
     const double *rhs = c->rhs[q];
     const unsigned gb = (unsigned)((c->ng + 255) / 256);
     Fields3 U{{u, u, u}};
-    const int trip = 4;
-    cudaGraphConditionalHandle h;
+    cudaGraphConditionalHandle h, hif;
     IBM_TRY(cond_handle(c, &h));
-    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, q, h);
+    IBM_TRY(cond_handle(c, &hif));
+    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, q, c->opts.helm_check_first, h);
     CondScope sc;
     IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
-    for (int t = 0; t < trip; ++t) {
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 0);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, c->type, rhs, hinv, u, alpha, 1);
+    {
+        // one sweep per trip; the residual test (an IF node) on the same
+        // sweep counts as the host-driven solve
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 0);
+        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 1);
         if (c->ng > 0) {
             ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
         }
+        ++c->nlaunch, k_helm_tick<<<1, 1, 0, c->s>>>(H, q, c->opts.helm_maxit, hif);
+        IBM_LAUNCHED(c);
+        CondScope si;
+        IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hif, &si));
+        ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, make_bc(c), q, u, alpha,
+                                                                     c->part);
+        IBM_LAUNCHED(c);
+        IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
+        if (c->ng > 0) {
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
+            IBM_LAUNCHED(c);
+        }
+        IBM_TRY(cond_close(c, &si));
+        ++c->nlaunch, k_helm_decide<<<1, 1, 0, c->s>>>(H, q, c->scal, c->ng > 0, c->opts.helm_rtol, u_scale(c),
+                                                     c->opts.helm_maxit, h);
+        IBM_LAUNCHED(c);
     }
-    ++c->nlaunch, k_helm_resid<<<c->nred, RED_THREADS, 0, c->s>>>(c->g, c->type, rhs, make_bc(c), q, u, alpha, c->part);
-    IBM_LAUNCHED(c);
-    IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
-    if (c->ng > 0) {
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
-        ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
-    }
-    ++c->nlaunch, k_helm_decide<<<1, 1, 0, c->s>>>(H, q, c->scal, c->ng > 0, c->opts.helm_rtol, u_scale(c),
-                                                 c->opts.helm_maxit, trip, h);
-    IBM_LAUNCHED(c);
     IBM_TRY(cond_close(c, &sc));
     return IBM_OK;
 }
@@ -903,7 +971,7 @@ static ibm_status ghost_refresh_dev(Ctx *c) {
     const int trip = 4;
     cudaGraphConditionalHandle h;
     IBM_TRY(cond_handle(c, &h));
-    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, -1, h);
+    ++c->nlaunch, k_hc_reset<<<1, 1, 0, c->s>>>(H, -1, 0, h);
     CondScope sc;
     IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
     for (int t = 0; t < trip; ++t) {

@@ -48,7 +48,8 @@ class ibm_solver_opts(Structure):
                 ("outer", c_int), ("band_sweeps", c_int), ("band_omega", c_double),
                 ("mixed_inner_rtol", c_double), ("mg_interp", c_int), ("tile_x", c_int), ("graph", c_int),
                 ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
-                ("smooth_omega", c_double), ("reorth_eta", c_double)]
+                ("smooth_omega", c_double), ("reorth_eta", c_double),
+                ("helm_check_first", c_int)]
 
 
 class ibm_table_info(Structure):
