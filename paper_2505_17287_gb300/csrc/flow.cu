@@ -207,6 +207,18 @@ __global__ void k_scaled_copy(int n, const double *__restrict__ src, double a, d
     if (t < n) dst[t] = a * src[t];
 }
 
+// Poisson initial guess: from the third step on the linear extrapolation
+// 2 phi^n - phi^(n-1) (phi changes smoothly between steps; against phi^n
+// alone it saves about a tenth of the iterations), else phi^n; phi^n is kept
+// for the next step
+__global__ void k_phi_guess(int64_t n, double *__restrict__ p, double *__restrict__ pp, int extrap) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double t = p[c];
+        if (extrap) p[c] = 2.0 * t - pp[c];
+        pp[c] = t;
+    }
+}
+
 // Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
 __global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
                           const double *__restrict__ hinv, double *__restrict__ u, int col) {
@@ -777,6 +789,8 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     double *braw = c->rhs[0];
     ++c->nlaunch, k_divergence<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
     IBM_LAUNCHED(c);
+    ++c->nlaunch, k_phi_guess<<<c->nelem, 256, 0, c->s>>>(c->N, c->p, c->p_prev, c->nstep >= 2 ? 1 : 0);
+    IBM_LAUNCHED(c);
     IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
     ibm_solve_stats ps{};
     ibm_status s = poisson_solve(c, braw, c->p, c->opts.rtol, c->opts.max_outer, &ps);
@@ -1008,6 +1022,8 @@ static ibm_status flow_step_capture(Ctx *c) {
     double *braw = c->rhs[0];
     ++c->nlaunch, k_divergence<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, Fs, 1.0 / dt, braw);
     IBM_LAUNCHED(c);
+    ++c->nlaunch, k_phi_guess<<<c->nelem, 256, 0, c->s>>>(c->N, c->p, c->p_prev, c->nstep >= 2 ? 1 : 0);
+    IBM_LAUNCHED(c);
     IBM_TRY(poisson_solve_dev(c, braw, c->p, c->opts.rtol, c->opts.max_outer));
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
@@ -1039,6 +1055,7 @@ static uint64_t graph_key(Ctx *c) {
     const unsigned char *g = (const unsigned char *)&c->mg_gen;
     for (size_t i = 0; i < sizeof(c->mg_gen); ++i) h = (h ^ g[i]) * 1099511628211ull;
     h = (h ^ (c->have_nold ? 1u : 2u)) * 1099511628211ull;
+    h = (h ^ (c->nstep >= 2 ? 3u : 4u)) * 1099511628211ull;   // extrapolated Poisson guess
     return h | 1ull;
 }
 
@@ -1130,15 +1147,23 @@ ibm_status flow_step_graph(Ctx *c) {
 // capture the graphs of the next step and of both buffer parities of the
 // steps after it, without running anything
 ibm_status flow_graph_prepare(Ctx *c) {
+    // the next four steps' states (start, buffer parity, extrapolated guess)
+    // cover every state of the steps after them
     const bool h0 = c->have_nold;
+    const int64_t n0 = c->nstep;
     int slot = 0;
-    ibm_status st = graph_for_state(c, &slot);
-    c->have_nold = true;
-    if (st == IBM_OK) st = graph_for_state(c, &slot);
-    swap_nold(c);
-    if (st == IBM_OK) st = graph_for_state(c, &slot);
-    swap_nold(c);
+    ibm_status st = IBM_OK;
+    int swaps = 0;
+    for (int k = 0; k < 4 && st == IBM_OK; ++k) {
+        st = graph_for_state(c, &slot);
+        swap_nold(c);
+        ++swaps;
+        c->have_nold = true;
+        c->nstep += 1;
+    }
+    if (swaps % 2) swap_nold(c);
     c->have_nold = h0;
+    c->nstep = n0;
     return st;
 }
 

@@ -247,6 +247,20 @@ def test_checkpoint_restart_is_bitwise():
         x.close()
 
 
+def test_poisson_guess_keeps_the_previous_pressure():
+    """From the third step on the Poisson solve starts from 2 p^n - p^(n-1);
+    the context keeps p^(n-1) as field p_prev, which a checkpoint carries."""
+    case = synth.cylinder_case(96, 48, nseg=256, dt=0.02)
+    s = _solver(case)
+    s.step(2)
+    p2 = s.get("p")
+    out = s.step(1)
+    assert out["status"] == ibm.IBM_OK and out["rel_residual"] <= 1e-10
+    assert np.array_equal(s.get("p_prev"), p2)
+    assert not np.array_equal(s.get("p"), p2)
+    s.close()
+
+
 def test_error_paths():
     case = synth.cylinder_case(32, 16, nseg=64)
     s = ibm.Solver(case)
