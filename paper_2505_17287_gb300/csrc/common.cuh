@@ -68,6 +68,15 @@ struct FastDiv {
 };
 
 // device view of a grid level (coordinates and extents)
+// j and k of grid row `row` (= j + ny k) by the multiply-shift divider:
+// a 64-bit (or even 32-bit) integer division costs tens of instructions per
+// thread, a measurable share of the issue slots of a streaming stencil pass
+__device__ __forceinline__ void row_jk(uint32_t row, const FastDiv &fny, int ny, int &j, int &k) {
+    const uint32_t kk = fny.div(row);
+    k = (int)kk;
+    j = (int)(row - kk * (uint32_t)ny);
+}
+
 struct GridDev {
     int nx, ny, nz, ndim;
     int64_t n;            // nx*ny*nz

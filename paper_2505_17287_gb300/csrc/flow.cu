@@ -223,7 +223,8 @@ __global__ void k_phi_guess(int64_t n, double *__restrict__ p, double *__restric
 __global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
                           const double *__restrict__ hinv, double *__restrict__ u, int col) {
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, g.fny, g.ny, j, k);
     const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
     if (i >= g.nx) return;
     const int64_t c = row * g.nx + i;

@@ -691,7 +691,8 @@ template <typename T, bool FINE, bool OMEGA = false>
 __global__ void __launch_bounds__(512, 4)
     k_rbgs(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col, T w = T(1)) {
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
     const int i = 2 * (blockIdx.y * blockDim.x + threadIdx.x) + ((j + k + col) & 1);
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
@@ -706,12 +707,65 @@ __global__ void __launch_bounds__(512, 4)
     }
 }
 
+// diagonal sum of the open faces at a cell of the finest level (the d of
+// k_offdiag<T, true>, summed in the same order)
+template <typename T>
+__device__ __forceinline__ T fine_diag(const MGLevel<T> &L, unsigned msk, int i, int j, int k) {
+    const T ayz = L.wy[j] * L.wz[k], axz = L.wx[i] * L.wz[k], axy = L.wx[i] * L.wy[j];
+    T d = T(0);
+    if (msk & 1u) d += ayz * L.rhx[i];
+    if (msk & 2u) d += ayz * L.rhx[i + 1];
+    if (msk & 4u) d += axz * L.rhy[j];
+    if (msk & 8u) d += axz * L.rhy[j + 1];
+    if (msk & 16u) d += axy * L.rhz[k];
+    if (msk & 32u) d += axy * L.rhz[k + 1];
+    return d;
+}
+
+// The first colour pass of a level, from x = 0: the neighbour sum vanishes,
+// so x_c = f_c / D_c (times w) on the active cells of colour col, the same
+// value k_rbgs gives, without reading x or the face coefficients. Each
+// thread owns the pair of cells (2t, 2t + 1) of its row; with zero_rest it
+// writes 0 to the pair's other cell and to inactive cells, in place of
+// clearing x beforehand.
+template <typename T, bool FINE, bool OMEGA = false>
+__global__ void __launch_bounds__(512, 4)
+    k_rbgs_first(MGLevel<T> L, const T *__restrict__ f, T *__restrict__ x, int col, T w, int zero_rest) {
+    const int64_t row = blockIdx.x;
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
+    const int i0 = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+    if (i0 >= L.nx) return;
+    const int par = (j + k + col) & 1;
+    const int ic = i0 + par, io = i0 + 1 - par;   // the cell of colour col, the other
+    if (zero_rest && io < L.nx) x[row * L.nx + io] = T(0);
+    if (ic >= L.nx) return;
+    const int64_t c = row * L.nx + ic;
+    T v = T(0);
+    bool wr = zero_rest != 0;
+    if (FINE) {
+        const unsigned msk = L.omask[c];
+        if (msk & 0x80u) {
+            const T d = fine_diag<T>(L, msk, ic, j, k);
+            if (d > T(0)) {
+                v = OMEGA ? w * (f[c] / d) : f[c] / d;
+                wr = true;
+            }
+        }
+    } else if (active<T, false>(L, c)) {
+        v = OMEGA ? w * (f[c] * L.dinv[c]) : f[c] * L.dinv[c];
+        wr = true;
+    }
+    if (wr) x[c] = v;
+}
+
 // coarse f_C = sum over children of (f - K x); coarse x_C = 0
 template <typename T, bool FINE>
 __global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, MGLevel<T> C,
                                  int fx, int fy, int fz) {
     const int64_t row = blockIdx.x;
-    const int J = (int)(row % C.ny), K = (int)(row / C.ny);
+    int J, K;
+    row_jk((uint32_t)blockIdx.x, C.fny, C.ny, J, K);
     const int I = blockIdx.y * blockDim.x + threadIdx.x;
     if (I >= C.nx) return;
     T acc = T(0);
@@ -741,7 +795,8 @@ __global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ f, const T 
 template <typename T, bool FINE>
 __global__ void k_prolong(MGLevel<T> L, T *__restrict__ x, MGLevel<T> C, int fx, int fy, int fz) {
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
@@ -785,7 +840,8 @@ __device__ __forceinline__ int xfer_axis(const int *I, const int *J, const T *w,
 template <typename T, bool FINE>
 __global__ void k_pnorm(MGLevel<T> L, MGLevel<T> C, Xfer<T> X, T *__restrict__ pn) {
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
@@ -820,7 +876,8 @@ __global__ void __launch_bounds__(RX_THREADS)
                int cnx, int fx, int zcol, T *__restrict__ tA) {
     __shared__ T sg[2 * RX_THREADS + 2];
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
     const int I0 = blockIdx.y * RX_THREADS;
     const int lo = fx == 2 ? 2 * I0 - 1 : I0;
     const int cnt = fx == 2 ? 2 * RX_THREADS + 2 : RX_THREADS;
@@ -877,7 +934,8 @@ __global__ void __launch_bounds__(RX_THREADS)
 template <typename T>
 __global__ void k_restrict_yz(MGLevel<T> C, const T *__restrict__ tA, int fny, Xfer<T> X) {
     const int64_t row = blockIdx.x;
-    const int Jc = (int)(row % C.ny), Kc = (int)(row / C.ny);
+    int Jc, Kc;
+    row_jk((uint32_t)blockIdx.x, C.fny, C.ny, Jc, Kc);
     const int Ic = blockIdx.y * blockDim.x + threadIdx.x;
     if (Ic >= C.nx) return;
     const int64_t cc = row * C.nx + Ic;
@@ -921,7 +979,8 @@ template <typename T>
 __global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restrict__ tB, int cny, Xfer<T> X,
                              const T *__restrict__ pn) {
     const int64_t row = blockIdx.x;
-    const int j = (int)(row % L.ny), k = (int)(row / L.ny);
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= L.nx) return;
     const int64_t c = row * L.nx + i;
@@ -1496,12 +1555,30 @@ ibm_status mg_build(Ctx *c) {
     return IBM_OK;
 }
 
+// first: 0 a colour pass; 1 the first pass of the level from x = 0; 2 the
+// same, also writing the zeros of x (no clearing before)
 template <typename T>
-static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col) {
+static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col, int first = 0) {
     MGLevel<T> &L = H.lv[l];
     const int bx = c->opts.tile_x;
     const dim3 grid = rows_grid(L.nx, L.ny, L.nz, 2, bx);
     const double w = c->opts.smooth_omega;
+    // (the first pass moves fewer bytes than a colour pass: timed apart, so
+    // that the finest-level id keeps to full passes)
+    const int kid = -1;
+    if (first) {
+        const int z = first == 2;
+        const bool fine = l == 0 && H.fine0;
+        if (w != 1.0) {
+            if (fine) KL(kid, (k_rbgs_first<T, true, true>), grid, bx, L, f, x, col, (T)w, z);
+            else KL(kid, (k_rbgs_first<T, false, true>), grid, bx, L, f, x, col, (T)w, z);
+        } else {
+            if (fine) KL(kid, (k_rbgs_first<T, true>), grid, bx, L, f, x, col, T(1), z);
+            else KL(kid, (k_rbgs_first<T, false>), grid, bx, L, f, x, col, T(1), z);
+        }
+        IBM_LAUNCHED(c);
+        return IBM_OK;
+    }
     if (w != 1.0) {
         if (l == 0 && H.fine0) KL(K_RBGS0, (k_rbgs<T, true, true>), grid, bx, L, f, x, col, (T)w);
         else KL(l == 0 ? K_RBGS0 : K_RBGS_C, (k_rbgs<T, false, true>), grid, bx, L, f, x, col, (T)w);
@@ -1521,12 +1598,14 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         IBM_LAUNCHED(c);
         return IBM_OK;
     }
-    IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
+    // x0 starts at zero: the first colour pass writes it whole (the coarse
+    // levels' x is cleared by the restriction)
+    if (nu1 < 1) IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
     for (int l = 0; l < L - 1; ++l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         for (int s = 0; s < nu1; ++s) {
-            IBM_TRY(rbgs(c, H, l, f, x, 0));
+            IBM_TRY(rbgs(c, H, l, f, x, 0, s == 0 ? (l == 0 ? 2 : 1) : 0));
             IBM_TRY(rbgs(c, H, l, f, x, 1));
         }
         MGLevel<T> &Lf = H.lv[l];
