@@ -477,7 +477,7 @@ def main():
     if not args.no_e2e:
         # end to end through the C ABI with pinned host buffers: every step
         # copies its input state host->device, steps, and reads u, v, w, p back
-        names_in = ["u", "v", "w", "p", "face_u", "face_v", "face_w", "nold_u", "nold_v", "nold_w"]
+        names_in = ["u", "v", "w", "p", "p_prev", "face_u", "face_v", "face_w", "nold_u", "nold_v", "nold_w"]
         names_out = ["u", "v", "w", "p"]
         st = s.get_state()
         host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in names_in}

@@ -78,8 +78,10 @@ ibm_status kt_flush(Ctx *c) {
 
 static void release_all(Ctx *c) {
     if (c->s) cudaStreamSynchronize(c->s);
-    if (c->mg64.vgraph) cudaGraphExecDestroy(c->mg64.vgraph);
-    if (c->mg32.vgraph) cudaGraphExecDestroy(c->mg32.vgraph);
+    for (int i = 0; i < MGHier<double>::NVG; ++i) {
+        if (c->mg64.vgraph[i]) cudaGraphExecDestroy(c->mg64.vgraph[i]);
+        if (c->mg32.vgraph[i]) cudaGraphExecDestroy(c->mg32.vgraph[i]);
+    }
     for (int i = 0; i < Ctx::NSGRAPH; ++i)
         if (c->sgraph[i]) cudaGraphExecDestroy(c->sgraph[i]);
     for (int i = 0; i < 8; ++i)

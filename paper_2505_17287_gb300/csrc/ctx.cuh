@@ -18,9 +18,12 @@ struct MGHier {
     // coarse interpolation weights of each cell (trilinear transfer)
     std::vector<T *> res, pn;
     bool built = false;
-    // the V-cycle z = M^{-1} r on (pr -> pz) captured as a CUDA graph, with
-    // the settings it was captured for and its kernel count
-    cudaGraphExec_t vgraph = nullptr;
+    // the V-cycle z = M^{-1} r (pr -> an output buffer) captured as CUDA
+    // graphs, one per output buffer (pz, or a Krylov vector written in
+    // place), with the settings they were captured for and the kernel count
+    static constexpr int NVG = 18;
+    cudaGraphExec_t vgraph[NVG] = {};
+    const void *vgraph_out[NVG] = {};
     uint64_t vgraph_key = 0;
     int64_t vgraph_kernels = 0;
 };

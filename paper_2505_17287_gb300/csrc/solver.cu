@@ -1665,34 +1665,51 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
 // settings), then replayed with a single launch. Its buffers are fixed, so
 // the graph stays valid for the life of the hierarchy.
 template <typename T>
-static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H) {
+static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H, T *out) {
     const ibm_solver_opts &o = c->opts;
     const uint64_t key = ((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
                            (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 2 + (uint64_t)o.mg_interp + 1;
-    if (!H.vgraph || H.vgraph_key != key) {
-        if (H.vgraph) {
-            IBM_CUDA(c, cudaStreamSynchronize(c->s));
-            cudaGraphExecDestroy(H.vgraph);
-            H.vgraph = nullptr;
+    auto drop_all = [&]() -> ibm_status {
+        IBM_CUDA(c, cudaStreamSynchronize(c->s));
+        for (int i = 0; i < MGHier<T>::NVG; ++i) {
+            if (H.vgraph[i]) cudaGraphExecDestroy(H.vgraph[i]);
+            H.vgraph[i] = nullptr;
+            H.vgraph_out[i] = nullptr;
+        }
+        return IBM_OK;
+    };
+    if (H.vgraph_key != key) {
+        IBM_TRY(drop_all());
+        H.vgraph_key = key;
+    }
+    int slot = -1;
+    for (int i = 0; i < MGHier<T>::NVG && slot < 0; ++i)
+        if (H.vgraph[i] && H.vgraph_out[i] == out) slot = i;
+    if (slot < 0) {
+        for (int i = 0; i < MGHier<T>::NVG && slot < 0; ++i)
+            if (!H.vgraph[i]) slot = i;
+        if (slot < 0) {
+            IBM_TRY(drop_all());
+            slot = 0;
         }
         const int64_t n0 = c->nlaunch;
         IBM_CUDA(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-        const ibm_status st = vcycle(c, H, H.pr, H.pz);
+        const ibm_status st = vcycle(c, H, H.pr, out);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->s, &g);
         IBM_TRY(st);
         if (e != cudaSuccess) return c->fail(IBM_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
-        const cudaError_t e2 = cudaGraphInstantiate(&H.vgraph, g, 0);
+        const cudaError_t e2 = cudaGraphInstantiate(&H.vgraph[slot], g, 0);
         cudaGraphDestroy(g);
         if (e2 != cudaSuccess) {
-            H.vgraph = nullptr;
+            H.vgraph[slot] = nullptr;
             return c->fail(IBM_ERR_CUDA, std::string("V-cycle graph instantiation: ") + cudaGetErrorString(e2));
         }
-        H.vgraph_key = key;
+        H.vgraph_out[slot] = out;
         H.vgraph_kernels = c->nlaunch - n0;
         c->nlaunch = n0;   // counted when the graph runs
     }
-    IBM_CUDA(c, cudaGraphLaunch(H.vgraph, c->s));
+    IBM_CUDA(c, cudaGraphLaunch(H.vgraph[slot], c->s));
     c->nlaunch += H.vgraph_kernels;
     return IBM_OK;
 }
@@ -1814,17 +1831,23 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
         xin = xo;
     } else if (c->opts.inner_iters == 1 && c->opts.outer == IBM_OUTER_FGMRES) {
         // one CG step is alpha times one V-cycle; FGMRES is invariant to
-        // that scalar, so the V-cycle output is used directly
+        // that scalar, so the V-cycle output is used directly. On large
+        // grids it is written straight into z: the V-cycle leaves every cell
+        // outside the active (FLUID) set at zero, so the copy below would be
+        // the identity (small grids keep one buffer and one graph)
+        T *xo = c->N >= (int64_t)1 << 20 ? z : H.pz;
         // (the legacy default stream cannot be captured: launched directly there)
         if (c->opts.graph == 1 && !c->kt.on && !c->capturing && c->s != nullptr && c->s != cudaStreamLegacy)
-            IBM_TRY(vcycle_graph(c, H));
-        else IBM_TRY(vcycle(c, H, H.pr, H.pz));
-        xin = H.pz;
+            IBM_TRY(vcycle_graph(c, H, xo));
+        else IBM_TRY(vcycle(c, H, H.pr, xo));
+        xin = xo;
     } else {
         IBM_TRY(pcg(c, H, c->opts.inner_iters));
     }
-    KL(-1, k_pre_out<T>, c->nred_wide, RED_THREADS, c->N, c->type, xin, z);
-    IBM_LAUNCHED(c);
+    if (xin != z) {
+        KL(-1, k_pre_out<T>, c->nred_wide, RED_THREADS, c->N, c->type, xin, z);
+        IBM_LAUNCHED(c);
+    }
     const OpT<T> o = op_of<T>(c);
     if (c->ng > 0) {
         KL(-1, k_pre_ghost<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o.wp, c->type, v, z);
