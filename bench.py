@@ -40,9 +40,9 @@ METRIC = "Mcell-steps/s per GB300, mixed vs FP64 at 1e-10 residual; serve p50/p9
 UNIT = "Mcell-steps/s"
 
 # DRAM traffic of one finest-level FP64 colour pass on the 384x256x256 wing,
-# from an ncu capture of the 256x192x192 case (513.0 MB per launch) scaled by
+# from an ncu capture of the 256x192x192 case (512.9 MB per launch) scaled by
 # the cell count; valid for the kernel as captured
-RBGS64_TRAFFIC_BYTES = 513.0e6 * 25165824 / 9437184
+RBGS64_TRAFFIC_BYTES = 512.93e6 * 25165824 / 9437184
 
 # algorithmic bytes per cell of one launch of the timed kernels
 # (FP64 s = 8, FP32 s = 4, cell type 1 byte); see the design notes
@@ -477,7 +477,7 @@ def main():
     if not args.no_e2e:
         # end to end through the C ABI with pinned host buffers: every step
         # copies its input state host->device, steps, and reads u, v, w, p back
-        names_in = ["u", "v", "w", "p", "p_prev", "face_u", "face_v", "face_w", "nold_u", "nold_v", "nold_w"]
+        names_in = ["u", "v", "w", "p", "p_prev", "p_prev2", "face_u", "face_v", "face_w", "nold_u", "nold_v", "nold_w"]
         names_out = ["u", "v", "w", "p"]
         st = s.get_state()
         host_in = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in names_in}

@@ -196,9 +196,12 @@ enum {
     IBM_FIELD_USTAR_U = 11, IBM_FIELD_USTAR_V = 12, IBM_FIELD_USTAR_W = 13, /* last predictor */
     IBM_FIELD_RHS = 14,                                   /* last Poisson right-hand side, N */
     IBM_FIELD_STEP = 15,                                  /* int64 step counter, 1 value */
-    IBM_FIELD_P_PREV = 16                                 /* pressure of the step before, N: from the
-                                                             third step on, the Poisson initial guess
-                                                             is 2 P - P_PREV (part of a checkpoint) */
+    IBM_FIELD_P_PREV = 16,                                /* pressure of the step before, N */
+    IBM_FIELD_P_PREV2 = 17                                /* pressure two steps before, N. The Poisson
+                                                             initial guess is P on the first two steps,
+                                                             2 P - P_PREV on the third, then
+                                                             3 P - 3 P_PREV + P_PREV2 (both are part
+                                                             of a checkpoint) */
 };
 
 /* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,

@@ -454,15 +454,17 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     }
     c->p = (double *)dev_alloc(c, nb);
     c->p_prev = (double *)dev_alloc(c, nb);
+    c->p_prev2 = (double *)dev_alloc(c, nb);
     c->b = (double *)dev_alloc(c, nb);
     c->w = (double *)dev_alloc(c, nb);
     c->rr = (double *)dev_alloc(c, nb);
     c->part = (double *)dev_alloc(c, sizeof(double) * RED_BLOCKS_MAX * 40);
     c->scal = (double *)dev_alloc(c, sizeof(double) * 64);
-    if (!c->p || !c->p_prev || !c->b || !c->w || !c->rr || !c->part || !c->scal)
+    if (!c->p || !c->p_prev || !c->p_prev2 || !c->b || !c->w || !c->rr || !c->part || !c->scal)
         return c->fail(IBM_ERR_OOM, "solver vector allocation failed");
     IBM_CUDA(c, cudaMemsetAsync(c->p, 0, nb, c->s));
     IBM_CUDA(c, cudaMemsetAsync(c->p_prev, 0, nb, c->s));
+    IBM_CUDA(c, cudaMemsetAsync(c->p_prev2, 0, nb, c->s));
     IBM_CUDA(c, cudaMemsetAsync(c->scal, 0, sizeof(double) * 64, c->s));
     IBM_TRY(build_levels(c));
     IBM_CUDA(c, cudaStreamSynchronize(c->s));
@@ -740,6 +742,7 @@ static ibm_status field_ptr(Ctx *c, int field, void **p, size_t *bytes) {
         *p = c->ustar[field - IBM_FIELD_USTAR_U]; *bytes = nb; return IBM_OK;
     case IBM_FIELD_RHS: *p = c->b; *bytes = nb; return IBM_OK;
     case IBM_FIELD_P_PREV: *p = c->p_prev; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_P_PREV2: *p = c->p_prev2; *bytes = nb; return IBM_OK;
     default: return c->fail(IBM_ERR_ARG, "unknown field id");
     }
 }

@@ -165,6 +165,23 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
+// block sum of FP32 per-thread partials: summed in FP32 within each warp,
+// then in FP64 across the warps (fixed order; valid in thread 0). On GB300 a
+// warp-wide FP64 instruction takes the FP64 pipe for many cycles, and the
+// FP64 shuffle tree cost the FP32 streaming kernels a third of their time
+template <int NT>
+__device__ __forceinline__ double block_sum(float v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NT / 32; ++q) t += sh[q];
+    __syncthreads();
+    return t;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;

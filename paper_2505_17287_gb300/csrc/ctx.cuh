@@ -100,7 +100,7 @@ struct Ctx {
 
     // flow state
     double *u[3] = {nullptr, nullptr, nullptr}, *F[3] = {nullptr, nullptr, nullptr};
-    double *p_prev = nullptr;   // pressure of the step before (Poisson initial guess)
+    double *p_prev = nullptr, *p_prev2 = nullptr;   // pressures of the two steps before (Poisson guess)
     double *p = nullptr, *Nold[3] = {nullptr, nullptr, nullptr}, *Nnew[3] = {nullptr, nullptr, nullptr};
     double *ustar[3] = {nullptr, nullptr, nullptr}, *rhs[3] = {nullptr, nullptr, nullptr};
     double *b = nullptr, *gtmp = nullptr;
@@ -170,7 +170,7 @@ struct Ctx {
     ibm_step_stats pend{};
     int pend_graph = 0;
     ibm_status pend_status = IBM_OK;
-    static constexpr int NSGRAPH = 4;   // first step, second step, then two buffer parities
+    static constexpr int NSGRAPH = 6;   // first three steps, then two buffer parities, one spare
     cudaGraphExec_t sgraph[NSGRAPH] = {nullptr};
     uint64_t sgraph_key[NSGRAPH] = {0};
     const double *sgraph_nold[NSGRAPH] = {nullptr};

@@ -272,7 +272,7 @@ void ibm_server::worker(Slot *sl) {
 extern "C" size_t ibm_case_bytes(int ndim, int nx, int ny, int nz, int precision, int64_t nelems_total) {
     const double n = (double)nx * ny * (ndim == 3 ? nz : 1);
     const double coarse = ndim == 3 ? 8.0 / 7.0 : 4.0 / 3.0;
-    double per_cell = 208.0;                  // FP64 fields, faces and step vectors
+    double per_cell = 216.0;                  // FP64 fields, faces and step vectors
     per_cell += 3 * 8 * coarse;               // open areas during the hierarchy build
     if (precision == IBM_MIXED)
         per_cell += 33 * 4 + 60 * coarse + 48;  // FP32 basis, FP32 hierarchy, FP32 operator

@@ -197,7 +197,7 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
         if constexpr (sizeof(T) == 8) acc += o.vol[c] * v;
         else acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
     }
-    const double tot = block_sum<RED_THREADS>((double)acc, sh);
+    const double tot = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(RED_THREADS)
                 if (u4get(t4, e) != GHOST) y[c + e] = out[e];
         }
     }
-    const double tot = block_sum<RED_THREADS>((double)acc, sh);
+    const double tot = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__rest
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-        const double t = block_sum<RED_THREADS>((double)acc[q], sh);
+        const double t = block_sum<RED_THREADS>(acc[q], sh);
         if (threadIdx.x == 0) part[(size_t)q * gridDim.x + blockIdx.x] = t;
     }
 }
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(int64_t n, T *__restrict__
         w[c] = a;
         ww += (A)a * (A)a;
     }
-    const double t = block_sum<RED_THREADS>((double)ww, sh);
+    const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -508,28 +508,30 @@ __global__ void k_add_scaled(int64_t n, const uint8_t *__restrict__ type, double
     GRID_STRIDE(c, n) if (type[c] != DEAD) phi[c] += a * ((double)d[c] - m);
 }
 
-// FLUID volume-weighted sum of an FP32 vector
-__global__ void k_fluid_volsum32(GridDev g, const uint8_t *__restrict__ type, const float *__restrict__ x,
-                                 double *__restrict__ part) {
+// FLUID volume-weighted sum of an FP32 vector (FP32 widths and per-thread
+// partials, FP64 across warps and blocks)
+__global__ void k_fluid_volsum32(GridDev g, OpT<float> o, const uint8_t *__restrict__ type,
+                                 const float *__restrict__ x, double *__restrict__ part) {
     __shared__ double sh[32];
-    double acc = 0.0;
+    float acc = 0.f;
     GRID_STRIDE(c, g.n) {
         if (type[c] != FLUID) continue;
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        acc += (g.dx[i] * g.dy[j] * g.dz[k]) * (double)x[c];
+        acc += (o.dx[i] * o.dy[j] * o.dz[k]) * x[c];
     }
-    acc = block_sum<RED_THREADS>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double t = block_sum<RED_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// (FP32 vectors: per-thread FP32 partials, FP64 across warps and blocks)
 template <typename T>
 __global__ void k_dotT(int64_t n, const T *__restrict__ a, const T *__restrict__ b, double *__restrict__ part) {
     __shared__ double sh[32];
-    double acc = 0.0;
-    GRID_STRIDE(c, n) acc += (double)a[c] * (double)b[c];
-    acc = block_sum<RED_THREADS>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    typename Acc<T>::type acc = 0;
+    GRID_STRIDE(c, n) acc += a[c] * b[c];
+    const double t = block_sum<RED_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // ---------------------------------------------------------------------------
@@ -2084,7 +2086,7 @@ static ibm_status mixed_refinement(Ctx *c, double *phi, double bnorm, double rto
                     refinements, rel, target, o, irel, (int)s);
         steps += o;
         inner += in;
-        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
+        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, op_of<float>(c), c->type, c->d32, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
         KL(-1, k_add_scaled, c->nred_wide, RED_THREADS, n, c->type, phi, c->d32, rn, c->scal + S_MEAN);
         IBM_LAUNCHED(c);
@@ -2294,7 +2296,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth_dev(int64_t n, T *__restri
         w[c] = a;
         ww += (A)a * (A)a;
     }
-    const double t = block_sum<RED_THREADS>((double)ww, sh);
+    const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -2595,7 +2597,7 @@ static ibm_status mixed_dev(Ctx *c, double *phi, DevFG *R, DevFG *F) {
         IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hi, &si));
         IBM_TRY(fgmres_dev_cycle<float>(c, K, c->d32, F));
         IBM_TRY(cond_close(c, &si));
-        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, c->type, c->d32, c->part);
+        KL(-1, k_fluid_volsum32, c->nred, RED_THREADS, c->g, op_of<float>(c), c->type, c->d32, c->part);
         IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, c->scal + S_MEAN));
         KL(-1, k_add_scaled_dev, c->nred_wide, RED_THREADS, n, c->type, phi, c->d32, R, c->scal + S_MEAN);
         KL(-1, k_ref_after, 1, 1, R, F);

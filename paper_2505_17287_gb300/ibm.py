@@ -28,7 +28,7 @@ IBM_FP64, IBM_MIXED = 0, 1
 IBM_OUTER_BICGSTAB, IBM_OUTER_FGMRES = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "face_u": 4, "face_v": 5, "face_w": 6, "nold_u": 7, "nold_v": 8,
           "nold_w": 9, "type": 10, "ustar_u": 11, "ustar_v": 12, "ustar_w": 13, "rhs": 14, "step": 15,
-          "p_prev": 16}
+          "p_prev": 16, "p_prev2": 17}
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
 FREE_FN = CFUNCTYPE(None, c_void_p, c_void_p)
@@ -421,7 +421,7 @@ class Solver:
         return ibm_set_field(self.ctx, FIELDS[name], a.ctypes.data, 0, a.nbytes)
 
     def state_names(self):
-        names = ["u", "v", "p", "p_prev", "face_u", "face_v", "nold_u", "nold_v"]
+        names = ["u", "v", "p", "p_prev", "p_prev2", "face_u", "face_v", "nold_u", "nold_v"]
         if self.ndim == 3:
             names += ["w", "face_w", "nold_w"]
         return names + ["step"]
