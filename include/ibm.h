@@ -198,8 +198,8 @@ enum {
     IBM_FIELD_STEP = 15,                                  /* int64 step counter, 1 value */
     IBM_FIELD_P_PREV = 16,                                /* pressure of the step before, N */
     IBM_FIELD_P_PREV2 = 17                                /* pressure two steps before, N. The Poisson
-                                                             initial guess is P on the first two steps,
-                                                             2 P - P_PREV on the third, then
+                                                             initial guess is P on the first three
+                                                             steps, 2 P - P_PREV on the fourth, then
                                                              3 P - 3 P_PREV + P_PREV2 (both are part
                                                              of a checkpoint) */
 };

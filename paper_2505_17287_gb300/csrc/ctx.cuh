@@ -170,7 +170,7 @@ struct Ctx {
     ibm_step_stats pend{};
     int pend_graph = 0;
     ibm_status pend_status = IBM_OK;
-    static constexpr int NSGRAPH = 6;   // first three steps, then two buffer parities, one spare
+    static constexpr int NSGRAPH = 6;   // first four steps, then two buffer parities
     cudaGraphExec_t sgraph[NSGRAPH] = {nullptr};
     uint64_t sgraph_key[NSGRAPH] = {0};
     const double *sgraph_nold[NSGRAPH] = {nullptr};

@@ -223,9 +223,12 @@ __global__ void k_phi_guess(int64_t n, double *__restrict__ p, double *__restric
     }
 }
 
-// order of the Poisson guess of the step about to run: phi^0, the zero start,
-// is never extrapolated from, so linear on the third step, quadratic after
-static int phi_order(const Ctx *c) { return c->nstep >= 3 ? 2 : (c->nstep == 2 ? 1 : 0); }
+// order of the Poisson guess of the step about to run. Neither phi^0 (the
+// zero start) nor phi^1 (the impulsive first step, far from the pressures
+// that follow: extrapolating from it cost the third step of a 208M-cell case
+// ~30% more iterations) is extrapolated from: linear on the fourth step,
+// quadratic from the fifth
+static int phi_order(const Ctx *c) { return c->nstep >= 4 ? 2 : (c->nstep == 3 ? 1 : 0); }
 
 // Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
 __global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
@@ -1156,14 +1159,14 @@ ibm_status flow_step_graph(Ctx *c) {
 // capture the graphs of the next step and of both buffer parities of the
 // steps after it, without running anything
 ibm_status flow_graph_prepare(Ctx *c) {
-    // the next five steps' states (start, buffer parity, order of the
+    // the next six steps' states (start, buffer parity, order of the
     // Poisson guess) cover every state of the steps after them
     const bool h0 = c->have_nold;
     const int64_t n0 = c->nstep;
     int slot = 0;
     ibm_status st = IBM_OK;
     int swaps = 0;
-    for (int k = 0; k < 5 && st == IBM_OK; ++k) {
+    for (int k = 0; k < 6 && st == IBM_OK; ++k) {
         st = graph_for_state(c, &slot);
         swap_nold(c);
         ++swaps;

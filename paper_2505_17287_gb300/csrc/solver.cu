@@ -479,6 +479,13 @@ __device__ __forceinline__ void scale_f32(int64_t n, float *__restrict__ dst, co
         dst[c] = a * src[c];
 }
 
+// grid of the multi-dot: each block ends with one FP64 tree sum per column,
+// which on GB300's FP64 pipe costs about as much as a few hundred elements, so
+// the FP64 kernel takes half the usual blocks (each thread streams twice the
+// elements)
+template <typename T>
+static unsigned mdot_blocks(const Ctx *c) { return sizeof(T) == 8 ? (unsigned)((c->nred + 1) / 2) : (unsigned)c->nred; }
+
 template <typename T, typename S>
 __global__ void k_scale(int64_t n, T *__restrict__ dst, const S *__restrict__ src, double a) {
     if constexpr (sizeof(T) == 4 && sizeof(S) == 4) scale_f32(n, dst, src, (float)a);
@@ -621,6 +628,12 @@ __global__ void k_bicg_xr(int64_t n, double *__restrict__ x, const double *__res
 // multigrid on the staircase operator, precision T
 // ---------------------------------------------------------------------------
 
+// quotient for the FP32 finest-level smoother (CUDA's approximate division
+// intrinsic; the operands are positive sums of face coefficients, far from
+// its 2^126 limit); FP64 keeps the correctly rounded division
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
 // v > 0 for the non-negative tables pn and dinv: an integer test of the bit
 // pattern for FP64 (an FP64 compare occupies GB300's slow FP64 pipe; -0 and
 // +0 both read as not positive)
@@ -703,7 +716,12 @@ __global__ void __launch_bounds__(512, 4)
     // the stored-coefficient levels accumulate onto f (one FP64 add fewer)
     const T s = FINE ? f[c] + k_offdiag<T, FINE>(L, x, c, i, j, k, d) : k_offdiag<T, FINE>(L, x, c, i, j, k, d, f[c]);
     if (FINE) {
-        if (d > T(0)) x[c] = OMEGA ? x[c] + w * (s / d - x[c]) : s / d;
+        // (FP32 only: the approximate quotient, two instructions instead of
+        // the correctly rounded division's sequence, in an issue-bound pass)
+        if (d > T(0)) {
+            const T q = fast_div(s, d);
+            x[c] = OMEGA ? x[c] + w * (q - x[c]) : q;
+        }
     } else {
         x[c] = OMEGA ? x[c] + w * (s * L.dinv[c] - x[c]) : s * L.dinv[c];
     }
@@ -750,7 +768,7 @@ __global__ void __launch_bounds__(512, 4)
         if (msk & 0x80u) {
             const T d = fine_diag<T>(L, msk, ic, j, k);
             if (d > T(0)) {
-                v = OMEGA ? w * (f[c] / d) : f[c] / d;
+                v = OMEGA ? w * fast_div(f[c], d) : fast_div(f[c], d);
                 wr = true;
             }
         }
@@ -1930,9 +1948,9 @@ static ibm_status fgmres(Ctx *c, Krylov<T> K, T *x, const T *b, double bnorm, do
             double hcol[17] = {0};
             double wbefore2 = 0.0, wafter2 = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
-                   K.w, vp, c->part);
-                IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
+                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], mdot_blocks<T>(c), RED_THREADS,
+                   n, K.w, vp, c->part);
+                IBM_TRY(finalize(c, c->part, mdot_blocks<T>(c), j + 1, 1.0, c->scal + S_MD));
                 IBM_TRY(sync_scalars(c, S_MD + j + 1));
                 Coef h{};
                 double h2 = 0.0;
@@ -2520,9 +2538,9 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
             KL(-1, (k_scale_dev<T, T>), c->nred_wide, RED_THREADS, n, K.V[j], j == 0 ? K.r : K.w, &F->scale);
             IBM_TRY(precond<T>(c, *K.H, K.V[j], K.Z[j]));
             IBM_TRY(apply_PA<T>(c, K.Z[j], nullptr, T(1), K.w));
-            KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w, vp,
-               c->part);
-            IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
+            KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], mdot_blocks<T>(c), RED_THREADS, n,
+               K.w, vp, c->part);
+            IBM_TRY(finalize(c, c->part, mdot_blocks<T>(c), j + 1, 1.0, c->scal + S_MD));
             KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
                vp, c->scal + S_MD, c->part);
             IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
@@ -2533,9 +2551,9 @@ static ibm_status fgmres_dev_cycle(Ctx *c, Krylov<T> K, T *x, DevFG *F) {
             CondScope sr;
             IBM_TRY(cond_open(c, cudaGraphCondTypeIf, hr, &sr));
             {
-                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n, K.w,
-                   vp, c->part);
-                IBM_TRY(finalize(c, c->part, c->nred, j + 1, 1.0, c->scal + S_MD));
+                KL(K_MDOT, mdot_table<T>(std::make_integer_sequence<int, 17>())[j], mdot_blocks<T>(c), RED_THREADS,
+                   n, K.w, vp, c->part);
+                IBM_TRY(finalize(c, c->part, mdot_blocks<T>(c), j + 1, 1.0, c->scal + S_MD));
                 KL(K_ORTH, orth_dev_table<T>(std::make_integer_sequence<int, 17>())[j], c->nred, RED_THREADS, n,
                    K.w, vp, c->scal + S_MD, c->part);
                 IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0, c->scal + S_TMP));
