@@ -261,6 +261,24 @@ def test_poisson_guess_keeps_the_previous_pressure():
     s.close()
 
 
+def test_helmholtz_test_schedule():
+    """The residual test schedule decides only when a converged Helmholtz solve
+    stops: a test after every sweep finds the smallest sweep count, a later
+    first test takes at least as many sweeps, and both meet the tolerance."""
+    case = synth.cylinder_case(96, 48, nseg=256, dt=0.02)
+    out = {}
+    for first in (1, 6):
+        s = _solver(case, helm_check_first=first)
+        r = s.step(3)
+        assert r["status"] == ibm.IBM_OK
+        out[first] = (r["helm_sweeps"], s.get("u"), s.get("v"))
+        s.close()
+    assert out[6][0] >= out[1][0]
+    for k in (1, 2):
+        a, b = out[1][k], out[6][k]
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+
+
 def test_error_paths():
     case = synth.cylinder_case(32, 16, nseg=64)
     s = ibm.Solver(case)
