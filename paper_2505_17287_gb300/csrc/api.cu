@@ -426,9 +426,17 @@ static ibm_status create_impl(Ctx *c, const ibm_grid_desc *d) {
     };
     double *rdx = upload(c, recip(c->hdx)), *rdy = upload(c, recip(c->hdy)), *rdz = upload(c, recip(c->hdz));
     if (!rdx || !rdy || !rdz) return c->fail(IBM_ERR_OOM, "grid allocation failed");
+    // 1 / centre spacing; entry 0 (no spacing below the first centre) is 0
+    auto recip_h = [](const std::vector<double> &h) {
+        std::vector<double> r(h.size(), 0.0);
+        for (size_t i = 1; i < h.size(); ++i) r[i] = 1.0 / h[i];
+        return r;
+    };
+    double *rhx = upload(c, recip_h(c->hhx)), *rhy = upload(c, recip_h(c->hhy)), *rhz = upload(c, recip_h(c->hhz));
+    if (!rhx || !rhy || !rhz) return c->fail(IBM_ERR_OOM, "grid allocation failed");
     c->g = GridDev{c->nx, c->ny, c->nz, c->ndim, c->N, c->xf, c->yf, c->zf, c->xc, c->yc, c->zc,
                    c->dx, c->dy, c->dz, c->hx, c->hy, c->hz, cxm, cxp, cxs, cym, cyp, cys, czm, czp, czs,
-                   FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny), rdx, rdy, rdz};
+                   FastDiv((uint32_t)c->nx), FastDiv((uint32_t)c->ny), rdx, rdy, rdz, rhx, rhy, rhz};
     const size_t nb = sizeof(double) * c->N;
     c->vol_c = (double *)dev_alloc(c, nb);
     c->dg_c = (double *)dev_alloc(c, nb);

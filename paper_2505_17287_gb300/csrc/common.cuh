@@ -90,6 +90,7 @@ struct GridDev {
     const double *cxm, *cxp, *cxs, *cym, *cyp, *cys, *czm, *czp, *czs;
     FastDiv fnx, fny;     // division by nx and ny (cell index < 2^32)
     const double *rdx, *rdy, *rdz;  // 1 / cell widths
+    const double *rhx, *rhy, *rhz;  // 1 / centre spacing h (index 0 unused, 0)
 };
 
 // cell (i, j, k) of a linear index below 2^32

@@ -58,6 +58,10 @@ struct CFields3 {
     const double *p[3];
 };
 
+// one of three values by a runtime index, by selection
+template <typename P>
+__device__ __forceinline__ P pick3(int q, P a, P b, P c) { return q == 0 ? a : (q == 1 ? b : c); }
+
 // Convective term N^n, explicit viscous term and the AB2 + CN right-hand side
 // on FLUID cells; other cells get rhs = 0 and N = 0. Per axis the face area
 // over the volume is 1/width, and the viscous face coefficients are the
@@ -69,7 +73,9 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) {
-            for (int q = 0; q < ncomp; ++q) { Nnew.p[q][c] = 0.0; rhs.p[q][c] = 0.0; }
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q < ncomp) { Nnew.p[q][c] = 0.0; rhs.p[q][c] = 0.0; }
             continue;
         }
         int i, j, k;
@@ -98,27 +104,41 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
         // factored form takes a third of the FP64 operations per component);
         // at a wall u_lo (u_hi) is 2 v - u_c for a Dirichlet value v and u_c
         // otherwise (zero gradient)
+        // (the axis loops are unrolled to their bound of 3, so that these
+        // small arrays stay in registers: indexed by a loop counter they went
+        // to local memory; the component loop stays rolled, which keeps the
+        // registers of one component live at a time)
         double fl[3], fh[3], dF = 0.0;
-        for (int a = 0; a < g.ndim; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a >= g.ndim) break;
             fl[a] = hrw[a] * Flo[a];
             fh[a] = hrw[a] * Fhi[a];
             dF += fh[a] - fl[a];
         }
         const double c15 = 1.5 * dt, c05 = 0.5 * dt;
+#pragma unroll 1
         for (int q = 0; q < ncomp; ++q) {
-            const double *uq = u.p[q];
+            // per-component pointers and wall data by selection (indexing the
+            // parameter arrays with q would copy them to local memory)
+            const double *uq = pick3(q, u.p[0], u.p[1], u.p[2]);
+            const double *noq = pick3(q, Nold.p[0], Nold.p[1], Nold.p[2]);
+            double *nnq = pick3(q, Nnew.p[0], Nnew.p[1], Nnew.p[2]);
+            double *rq = pick3(q, rhs.p[0], rhs.p[1], rhs.p[2]);
             const double uc = uq[c];
             // lap = off - D uc with off the neighbour (and Dirichlet wall)
             // terms and D the diagonal; src is the wall values' share of the
             // implicit half of Crank-Nicolson
             double N = dF * uc, off = 0.0, D = dint, src = 0.0;
-            for (int a = 0; a < g.ndim; ++a) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= g.ndim) break;
                 double ulo, uhi;
                 if (idx[a] > 0) {
                     ulo = uq[c - st[a]];
                     off += cm[a] * ulo;
-                } else if (bc.dir[q][2 * a]) {
-                    const double v = bc.val[q][2 * a], w2 = 2.0 * rw[a] * rw[a];
+                } else if (pick3(q, bc.dir[0][2 * a], bc.dir[1][2 * a], bc.dir[2][2 * a])) {
+                    const double v = pick3(q, bc.val[0][2 * a], bc.val[1][2 * a], bc.val[2][2 * a]), w2 = 2.0 * rw[a] * rw[a];
                     ulo = 2.0 * v - uc;
                     off += w2 * v;
                     D += w2;
@@ -129,8 +149,8 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
                 if (idx[a] < nn[a] - 1) {
                     uhi = uq[c + st[a]];
                     off += cp[a] * uhi;
-                } else if (bc.dir[q][2 * a + 1]) {
-                    const double v = bc.val[q][2 * a + 1], w2 = 2.0 * rw[a] * rw[a];
+                } else if (pick3(q, bc.dir[0][2 * a + 1], bc.dir[1][2 * a + 1], bc.dir[2][2 * a + 1])) {
+                    const double v = pick3(q, bc.val[0][2 * a + 1], bc.val[1][2 * a + 1], bc.val[2][2 * a + 1]), w2 = 2.0 * rw[a] * rw[a];
                     uhi = 2.0 * v - uc;
                     off += w2 * v;
                     D += w2;
@@ -140,9 +160,9 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
                 }
                 N += fh[a] * uhi - fl[a] * ulo;
             }
-            const double No = first ? N : Nold.p[q][c];
-            Nnew.p[q][c] = N;
-            rhs.p[q][c] = (uc - c15 * N + c05 * No) + alpha * ((off - D * uc) + src);
+            const double No = first ? N : noq[c];
+            nnq[c] = N;
+            rq[c] = (uc - c15 * N + c05 * No) + alpha * ((off - D * uc) + src);
         }
     }
 }
@@ -330,14 +350,14 @@ __global__ void k_max_final(const double *__restrict__ part, int n, double *__re
 
 // face velocities of axis a from cell values (interior and outer faces)
 __global__ void k_faces(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ ua, int a,
-                        BCInfo bc, double *__restrict__ Fa) {
+                        BCInfo bc, double *__restrict__ Fa, FastDiv fdx, FastDiv fdy) {
     const int nfx = g.nx + (a == 0), nfy = g.ny + (a == 1), nfz = g.nz + (a == 2);
     const int64_t nf = (int64_t)nfx * nfy * nfz;
     const int64_t st = a == 0 ? 1 : (a == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny);
     const int nax = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = f / nfx;
-        const int fi = (int)(f - t * nfx), fj = (int)(t % nfy), fk = (int)(t / nfy);
+        const uint32_t t = fdx.div((uint32_t)f), fkk = fdy.div(t);
+        const int fi = (int)((uint32_t)f - t * (uint32_t)nfx), fj = (int)(t - fkk * (uint32_t)nfy), fk = (int)fkk;
         const int fa = a == 0 ? fi : (a == 1 ? fj : fk);
         // cell on the high side (index fa along a) and on the low side (fa-1)
         const int ci = fi, cj = fj, ck = fk;
@@ -444,32 +464,35 @@ __global__ void k_divergence(GridDev g, const uint8_t *__restrict__ type, CField
         if (type[c] != FLUID) { out[c] = 0.0; continue; }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        const double vol = g.dx[i] * g.dy[j] * g.dz[k];
-        double d = g.dy[j] * g.dz[k] * (F.p[0][fx_lo(g, i, j, k) + 1] - F.p[0][fx_lo(g, i, j, k)]);
-        d += g.dx[i] * g.dz[k] * (F.p[1][fy_lo(g, i, j, k) + g.nx] - F.p[1][fy_lo(g, i, j, k)]);
+        // (face area x flux difference) / volume = flux difference / width, per
+        // axis: stored reciprocal widths, no FP64 division
+        double d = (F.p[0][fx_lo(g, i, j, k) + 1] - F.p[0][fx_lo(g, i, j, k)]) * g.rdx[i];
+        d += (F.p[1][fy_lo(g, i, j, k) + g.nx] - F.p[1][fy_lo(g, i, j, k)]) * g.rdy[j];
         if (g.ndim == 3)
-            d += g.dx[i] * g.dy[j] * (F.p[2][fz_lo(g, i, j, k) + (int64_t)g.nx * g.ny] - F.p[2][fz_lo(g, i, j, k)]);
-        out[c] = (d / vol) * inv_dt;
+            d += (F.p[2][fz_lo(g, i, j, k) + (int64_t)g.nx * g.ny] - F.p[2][fz_lo(g, i, j, k)]) * g.rdz[k];
+        out[c] = d * inv_dt;
     }
 }
 
 // projection of the interior faces of axis a that have a FLUID side
+// (fdx, fdy: multiply-shift dividers by the face counts along x and y; the
+// gradient multiplies by the stored reciprocal centre spacing)
 __global__ void k_project_faces(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ phi, int a,
-                                double dt, double *__restrict__ Fa) {
+                                double dt, double *__restrict__ Fa, FastDiv fdx, FastDiv fdy) {
     const int nfx = g.nx + (a == 0), nfy = g.ny + (a == 1), nfz = g.nz + (a == 2);
     const int64_t nf = (int64_t)nfx * nfy * nfz;
     const int64_t st = a == 0 ? 1 : (a == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny);
     const int nax = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
-    const double *hc = a == 0 ? g.hx : (a == 1 ? g.hy : g.hz);
+    const double *rh = a == 0 ? g.rhx : (a == 1 ? g.rhy : g.rhz);
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = f / nfx;
-        const int fi = (int)(f - t * nfx), fj = (int)(t % nfy), fk = (int)(t / nfy);
-        const int fa = a == 0 ? fi : (a == 1 ? fj : fk);
+        const uint32_t t = fdx.div((uint32_t)f), fk = fdy.div(t);
+        const int fi = (int)((uint32_t)f - t * (uint32_t)nfx), fj = (int)(t - fk * (uint32_t)nfy);
+        const int fa = a == 0 ? fi : (a == 1 ? fj : (int)fk);
         if (fa == 0 || fa == nax) continue;
         const int64_t cR = (int64_t)fi + (int64_t)g.nx * (fj + (int64_t)g.ny * fk);
         const int64_t cL = cR - st;
         if (type[cL] != FLUID && type[cR] != FLUID) continue;
-        Fa[f] -= dt * (phi[cR] - phi[cL]) / hc[fa];
+        Fa[f] -= dt * (phi[cR] - phi[cL]) * rh[fa];
     }
 }
 
@@ -480,22 +503,24 @@ __global__ void k_project_cells(GridDev g, const uint8_t *__restrict__ type, con
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t != FLUID) {
-            for (int a = 0; a < g.ndim; ++a) u.p[a][c] = us.p[a][c];
+            u.p[0][c] = us.p[0][c];
+            u.p[1][c] = us.p[1][c];
+            if (g.ndim == 3) u.p[2][c] = us.p[2][c];
             continue;
         }
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
         const double pc = phi[c];
         double glo, ghi;
-        glo = i > 0 ? (pc - phi[c - 1]) / g.hx[i] : 0.0;
-        ghi = i < g.nx - 1 ? (phi[c + 1] - pc) / g.hx[i + 1] : 0.0;
+        glo = i > 0 ? (pc - phi[c - 1]) * g.rhx[i] : 0.0;
+        ghi = i < g.nx - 1 ? (phi[c + 1] - pc) * g.rhx[i + 1] : 0.0;
         u.p[0][c] = us.p[0][c] - dt * (0.5 * (glo + ghi));
-        glo = j > 0 ? (pc - phi[c - sy]) / g.hy[j] : 0.0;
-        ghi = j < g.ny - 1 ? (phi[c + sy] - pc) / g.hy[j + 1] : 0.0;
+        glo = j > 0 ? (pc - phi[c - sy]) * g.rhy[j] : 0.0;
+        ghi = j < g.ny - 1 ? (phi[c + sy] - pc) * g.rhy[j + 1] : 0.0;
         u.p[1][c] = us.p[1][c] - dt * (0.5 * (glo + ghi));
         if (g.ndim == 3) {
-            glo = k > 0 ? (pc - phi[c - sz]) / g.hz[k] : 0.0;
-            ghi = k < g.nz - 1 ? (phi[c + sz] - pc) / g.hz[k + 1] : 0.0;
+            glo = k > 0 ? (pc - phi[c - sz]) * g.rhz[k] : 0.0;
+            ghi = k < g.nz - 1 ? (phi[c + sz] - pc) * g.rhz[k + 1] : 0.0;
             u.p[2][c] = us.p[2][c] - dt * (0.5 * (glo + ghi));
         }
     }
@@ -544,7 +569,8 @@ static ibm_status faces_from(Ctx *c, double *const *ucell) {
     for (int a = 0; a < c->ndim; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
-        ++c->nlaunch, k_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, ucell[a], a, bc, c->F[a]);
+        ++c->nlaunch, k_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, ucell[a], a, bc, c->F[a], FastDiv((uint32_t)(c->nx + (a == 0))),
+                                                  FastDiv((uint32_t)(c->ny + (a == 1))));
         IBM_LAUNCHED(c);
     }
     CFields3 F{{c->F[0], c->F[1], c->F[2]}};
@@ -812,7 +838,9 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
-        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
+        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a],
+                                                          FastDiv((uint32_t)(c->nx + (a == 0))),
+                                                          FastDiv((uint32_t)(c->ny + (a == 1))));
     }
     IBM_LAUNCHED(c);
     CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
@@ -1040,7 +1068,9 @@ static ibm_status flow_step_capture(Ctx *c) {
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
-        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a]);
+        ++c->nlaunch, k_project_faces<<<nb, 256, 0, c->s>>>(c->g, c->type, c->p, a, dt, c->F[a],
+                                                          FastDiv((uint32_t)(c->nx + (a == 0))),
+                                                          FastDiv((uint32_t)(c->ny + (a == 1))));
     }
     CFields3 us{{c->ustar[0], c->ustar[1], nc == 3 ? c->ustar[2] : c->ustar[1]}};
     Fields3 un{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
