@@ -146,6 +146,11 @@ typedef struct {
                            needing n sweeps takes O(log n) tests. Each test costs
                            about one and a half sweeps in FP64; default 6, the count
                            the 3D wing's components need at helm_rtol 1e-12 */
+    double helm_omega;  /* Helmholtz red-black relaxation factor: 0 = automatic,
+                           2 / (1 + sqrt(1 - rho^2)) with rho the grid's bound on the
+                           Jacobi spectral radius (Young's optimum for a red-black
+                           ordered 7-point operator); 1 = Gauss-Seidel; otherwise the
+                           factor itself, in (0, 2) */
 } ibm_solver_opts;
 
 typedef struct {
@@ -209,7 +214,7 @@ enum {
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6. */
+   helm_check_first 6, helm_omega 1. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -123,6 +123,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->smooth_omega = 1.0;
     o->reorth_eta = 0.3;
     o->helm_check_first = 6;
+    o->helm_omega = 1.0;
     return IBM_OK;
 }
 
@@ -155,6 +156,10 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->helm_solver != 0 && o->helm_solver != 1) { why = "helm_solver must be 0 or 1"; return false; }
     if (!(o->reorth_eta >= 0.0 && o->reorth_eta <= 1.0)) { why = "reorth_eta must be in [0, 1]"; return false; }
     if (o->helm_check_first < 1) { why = "helm_check_first must be >= 1"; return false; }
+    if (!(o->helm_omega == 0.0 || (o->helm_omega > 0.0 && o->helm_omega < 2.0))) {
+        why = "helm_omega must be 0 (automatic) or in (0, 2)";
+        return false;
+    }
     if (!(o->smooth_omega > 0.0 && o->smooth_omega < 2.0)) { why = "smooth_omega must be in (0, 2)"; return false; }
     if (o->inner_iters > 1 && o->smooth_omega != 1.0) { why = "smooth_omega must be 1 when inner_iters > 1"; return false; }
     return true;

@@ -250,9 +250,11 @@ __global__ void k_phi_guess(int64_t n, double *__restrict__ p, double *__restric
 // quadratic from the fifth
 static int phi_order(const Ctx *c) { return c->nstep >= 4 ? 2 : (c->nstep == 3 ? 1 : 0); }
 
-// Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells
+// Helmholtz (I - alpha L0) u = rhs: one red-black colour on FLUID cells;
+// SOR: u += w (Gauss-Seidel value - u)
+template <bool SOR>
 __global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                          const double *__restrict__ hinv, double *__restrict__ u, int col) {
+                          const double *__restrict__ hinv, double *__restrict__ u, int col, double w) {
     const int64_t row = blockIdx.x;
     int j, k;
     row_jk((uint32_t)blockIdx.x, g.fny, g.ny, j, k);
@@ -260,7 +262,13 @@ __global__ void k_helm_rb(GridDev g, HelmCoef h, const uint8_t *__restrict__ typ
     if (i >= g.nx) return;
     const int64_t c = row * g.nx + i;
     if (type[c] != FLUID) return;
-    u[c] = visc_sum(g, h, u, c, i, j, k, rhs[c]) * hinv[c];
+    const double gs = visc_sum(g, h, u, c, i, j, k, rhs[c]) * hinv[c];
+    if (SOR) {
+        const double uc = u[c];
+        u[c] = uc + w * (gs - uc);
+    } else {
+        u[c] = gs;
+    }
 }
 
 // one damped-Jacobi sweep of the Helmholtz system: out = u + w (D^{-1}(rhs +
@@ -670,6 +678,37 @@ static ibm_status helm_prepare(Ctx *c) {
     return IBM_OK;
 }
 
+// bound on the spectral radius of the Jacobi iteration of H = I - alpha L:
+// alpha S / (1 + alpha S), S the largest diagonal of L, bounded per axis from
+// the 1D coefficients (a Dirichlet wall counting 2 / w^2)
+static double helm_rho(const Ctx *c) {
+    const double alpha = c->desc.dt / (2.0 * c->desc.Re);
+    auto axis_max = [](const std::vector<double> &w, const std::vector<double> &h) {
+        double m = 0.0;
+        const size_t n = w.size();
+        for (size_t i = 0; i < n; ++i) {
+            const double cm = i > 0 ? 1.0 / (h[i] * w[i]) : 2.0 / (w[i] * w[i]);
+            const double cp = i + 1 < n ? 1.0 / (h[i + 1] * w[i]) : 2.0 / (w[i] * w[i]);
+            m = fmax(m, cm + cp);
+        }
+        return m;
+    };
+    double S = axis_max(c->hdx, c->hhx) + axis_max(c->hdy, c->hhy);
+    if (c->ndim == 3) S += axis_max(c->hdz, c->hhz);
+    return alpha * S / (1.0 + alpha * S);
+}
+
+// relaxation factor of the red-black Helmholtz sweeps (opts.helm_omega; 0:
+// Young's optimum 2 / (1 + sqrt(1 - rho^2)) for the bound rho, which for a
+// red-black (consistently ordered) operator takes the error reduction per
+// sweep from rho^2 to about omega - 1)
+static double helm_omega(const Ctx *c) {
+    const double w = c->opts.helm_omega;
+    if (w != 0.0) return w;
+    const double r = helm_rho(c);
+    return 2.0 / (1.0 + sqrt(1.0 - r * r));
+}
+
 // Helmholtz by scheduled relaxation Jacobi: cycles of 8 sweeps with factors
 // 1/tau_k, tau_k the Chebyshev points of [1 - rho, 1 + rho] (the spectrum of
 // D^{-1} H for H = I - alpha L, rho = alpha S / (1 + alpha S) with S the
@@ -682,20 +721,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
         c->htmp = (double *)dev_alloc(c, sizeof(double) * c->N);
         if (!c->htmp) return c->fail(IBM_ERR_OOM, "Helmholtz buffer allocation failed");
     }
-    auto axis_max = [](const std::vector<double> &w, const std::vector<double> &h) {
-        // largest c_m + c_p + 2 / w^2 (a Dirichlet wall) of one axis
-        double m = 0.0;
-        const size_t n = w.size();
-        for (size_t i = 0; i < n; ++i) {
-            const double cm = i > 0 ? 1.0 / (h[i] * w[i]) : 2.0 / (w[i] * w[i]);
-            const double cp = i + 1 < n ? 1.0 / (h[i + 1] * w[i]) : 2.0 / (w[i] * w[i]);
-            m = fmax(m, cm + cp);
-        }
-        return m;
-    };
-    double S = axis_max(c->hdx, c->hhx) + axis_max(c->hdy, c->hhy);
-    if (c->ndim == 3) S += axis_max(c->hdz, c->hhz);
-    const double rho = alpha * S / (1.0 + alpha * S), pi = 3.14159265358979323846;
+    const double rho = helm_rho(c), pi = 3.14159265358979323846;
     const int M = 8;
     double w[M];
     const int order[M] = {0, 4, 2, 6, 1, 5, 3, 7};   // bit-reversed
@@ -746,6 +772,13 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
     return IBM_ERR_NOT_CONVERGED;
 }
 
+// one red-black colour pass of the Helmholtz sweeps (kernel launch)
+static void helm_rb(Ctx *c, const double *rhs, const double *hinv, double *u, int col) {
+    const double w = helm_omega(c);
+    if (w != 1.0) k_helm_rb<true><<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, col, w);
+    else k_helm_rb<false><<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, col, 1.0);
+}
+
 static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     const double alpha = c->desc.dt / (2.0 * c->desc.Re);
     IBM_TRY(helm_prepare(c));
@@ -760,10 +793,10 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
     Fields3 U{{u, u, u}};
     for (int it = 0; it < c->opts.helm_maxit; ++it) {
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 0);
+        ++c->nlaunch, helm_rb(c, rhs, hinv, u, 0);
         kt_end(c, K_HELM);
         kt_begin(c, K_HELM);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 1);
+        ++c->nlaunch, helm_rb(c, rhs, hinv, u, 1);
         kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
@@ -988,8 +1021,8 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
     {
         // one sweep per trip; the residual test (an IF node) on the same
         // sweep counts as the host-driven solve
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 0);
-        ++c->nlaunch, k_helm_rb<<<rb_grid(c), 128, 0, c->s>>>(c->g, helm_coef(c), c->type, rhs, hinv, u, 1);
+        ++c->nlaunch, helm_rb(c, rhs, hinv, u, 0);
+        ++c->nlaunch, helm_rb(c, rhs, hinv, u, 1);
         if (c->ng > 0) {
             ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
