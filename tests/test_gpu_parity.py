@@ -279,6 +279,22 @@ def test_helmholtz_test_schedule():
         assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
 
 
+@pytest.mark.parametrize("omega", [0.0, 1.05])
+def test_helmholtz_relaxation_factor(omega):
+    """Over-relaxed colour passes (a given factor, or 0 for the optimum of the
+    grid bound) converge to the Gauss-Seidel solution within the tolerances."""
+    case = synth.cylinder_case(96, 48, nseg=256, dt=0.02)
+    out = []
+    for w in (1.0, omega):
+        s = _solver(case, helm_omega=w)
+        r = s.step(3)
+        assert r["status"] == ibm.IBM_OK and r["rel_residual"] <= 1e-12
+        out.append((s.get("u"), s.get("v")))
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+
+
 def test_error_paths():
     case = synth.cylinder_case(32, 16, nseg=64)
     s = ibm.Solver(case)
