@@ -511,6 +511,13 @@ extern "C" ibm_status ibm_create_grid(const ibm_grid_desc *d, ibm_ctx **out) {
     if ((d->alloc == nullptr) != (d->free == nullptr)) { g_create_error = "alloc and free hooks must be given together"; return IBM_ERR_ARG; }
     const double ncell = (double)d->nx * d->ny * (d->ndim == 3 ? d->nz : 1);
     if (ncell >= 4294967296.0) { g_create_error = "grid too large (at most 2^32 - 1 cells)"; return IBM_ERR_ARG; }
+    {
+        // face arrays are indexed with 32-bit multiply-shift division too
+        const double nz = d->ndim == 3 ? d->nz : 1;
+        double nf = fmax((d->nx + 1.0) * d->ny * nz, d->nx * (d->ny + 1.0) * nz);
+        if (d->ndim == 3) nf = fmax(nf, (double)d->nx * d->ny * (nz + 1.0));
+        if (nf >= 4294967296.0) { g_create_error = "grid too large (at most 2^32 - 1 faces per axis)"; return IBM_ERR_ARG; }
+    }
     ibm_ctx *c = new (std::nothrow) ibm_ctx();
     if (!c) { g_create_error = "host allocation failed"; return IBM_ERR_OOM; }
     ibm_status s = create_impl(c, d);

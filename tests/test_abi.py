@@ -76,6 +76,16 @@ def test_create_rejects_bad_descriptor_without_gpu(lib):
     assert lib.ibm_create_grid(ctypes.byref(d), ctypes.byref(ctx)) == ibm.IBM_ERR_ARG
     assert ctx.value is None
     assert b"ndim" in lib.ibm_last_error(None)
+    # fewer than 2^32 cells but 2^32 or more x-faces (32-bit face indexing)
+    import numpy as np
+    n = 37837
+    xs, ys = np.linspace(0.0, 1.0, 4), np.linspace(0.0, 1.0, n + 1)
+    d = ibm.ibm_grid_desc()
+    d.ndim, d.nx, d.ny, d.nz, d.Re, d.dt = 3, 3, n, n, 100.0, 0.01
+    d.xf, d.yf, d.zf = xs.ctypes.data, ys.ctypes.data, ys.ctypes.data
+    assert 3 * n * n < 2 ** 32 <= 4 * n * n
+    assert lib.ibm_create_grid(ctypes.byref(d), ctypes.byref(ctx)) == ibm.IBM_ERR_ARG
+    assert b"faces" in lib.ibm_last_error(None)
     assert lib.ibm_destroy(None) == ibm.IBM_OK
     o = ibm.ibm_solver_opts()
     assert lib.ibm_default_opts(ctypes.byref(o)) == ibm.IBM_OK
