@@ -163,7 +163,6 @@ typedef struct {
     int outer_iters;         /* FGMRES iterations */
     int inner_iters;         /* MG-PCG iterations summed over preconditioner calls */
     double rel_residual;     /* final ||P(b - A phi)|| / ||P b||, in FP64 */
-    double lambda_est;       /* not used; 0 */
     double ms;               /* device time of the solve */
 } ibm_solve_stats;
 
@@ -320,18 +319,20 @@ ibm_status ibm_kernel_time(ibm_ctx *ctx, int kernel, double *ms_total, int64_t *
 /* Allocation-free residual check (no counterpart in the paper): returns in
    *rel_out (host or device pointer) the relative residual
    ||P(b - A phi)||_2 / ||P b||_2 of a pressure solution phi_dev for the
-   right-hand side rhs_dev (both device, N doubles; b = rhs with its
-   volume-weighted FLUID mean removed), the quantity ibm_poisson_solve reports
-   as rel_residual. For callers that may not allocate device memory (code
-   running during stream capture into a CUDA graph, where cudaMalloc is not
-   allowed, or frameworks that own all device memory): it calls no
-   cudaMalloc/cudaFree and keeps its partial sums in a 96 KiB file-scope
-   device array, held by every GPU that loads the library until exit.
-   Grids above 268,435,456 cells are rejected (IBM_ERR_ARG). The first call
-   on each device looks up that array's device address with that device
-   current, so make it before starting any stream capture. Calls share the
-   array: calls that overlap on the GPU (other streams or host threads)
-   race. IBM_ERR_STATE before ibm_classify_cells. */
+   right-hand side rhs_dev (both device memory, N doubles, else IBM_ERR_ARG;
+   b = rhs with its volume-weighted FLUID mean removed), the quantity
+   ibm_poisson_solve reports as rel_residual. For callers that cannot
+   allocate device memory: an application whose memory manager owns the whole
+   device and forbids libraries to allocate during its step, or a caller
+   running with the device already full. It calls no cudaMalloc/cudaFree and
+   keeps its partial sums in a 96 KiB file-scope device array, held by every
+   GPU that loads the library until exit. Grids above 268,435,456 cells are
+   rejected (IBM_ERR_ARG). The first call on each device looks up that
+   array's device address with that device current, so make it before
+   starting any stream capture. Calls share the array: calls that overlap on
+   the GPU (other streams or host threads) race. The call synchronises the
+   context's stream before it returns. IBM_ERR_STATE before
+   ibm_classify_cells. */
 ibm_status ibm_poisson_residual_noalloc(ibm_ctx *ctx, const double *rhs_dev, const double *phi_dev,
                                         double *rel_out);
 

@@ -44,6 +44,14 @@ FLUID, GHOST, DEAD = 0, 1, 2
 INFLOW, OUTFLOW, SLIP = 0, 1, 2
 DEFAULT_BC = (INFLOW, OUTFLOW, SLIP, SLIP, SLIP, SLIP)
 
+# Time scheme of Section 2.1 (reading: second-order Adams-Bashforth for the
+# convective term, Crank-Nicolson for the viscous term). AB2 holds the
+# weights of N^n and N^(n-1); CN_THETA is the implicit share of the viscous
+# operator (the explicit share is 1 - CN_THETA). Module constants so that a
+# pin can swap in another scheme and show that it fails.
+AB2 = (1.5, -0.5)
+CN_THETA = 0.5
+
 
 @dataclass
 class Grid:
@@ -435,6 +443,54 @@ def refresh_velocity_ghosts(g: Grid, typ, tabs, u, u_bi=0.0):
     return out
 
 
+def body_force(g: Grid, typ, tabs, u, p, Re):
+    """Force of the fluid on the immersed body (all bodies together), per
+    unit span in 2D (the grid's z extent is 1), for density 1.
+
+    The paper reports drag and lift coefficients (Section 3.2) but does not
+    say how the force is taken. Reading: the traction is integrated at the
+    body intercepts (BI) of the ghost cells,
+        F = sum_G dS_G ( -p_BI n_G + (1/Re) du/dn|_BI ),
+    with n_G the outward body normal at the BI, and
+      * p_BI = p_G: under the zero-gradient closure of the pressure ghost
+        row the image-point value equals the ghost value, and the BI value
+        is the mean of the two;
+      * du/dn|_BI = (u_IP - u_G) / |IP - GC| with u_IP = 2 u_BI - u_G and
+        u_BI = 0 (body at rest), i.e. -2 u_G / |IP - GC|; at a no-slip wall
+        of an incompressible flow the viscous traction is (1/Re) du/dn;
+      * dS_G, the surface area a ghost cell stands for, is the area of its
+        faces shared with FLUID cells projected onto n_G:
+        sum_faces A_f |n_G . e_f|.
+    Returns the force vector (3,)."""
+    gi = tabs["gidx"]
+    F = np.zeros(3)
+    if gi.size == 0:
+        return F
+    t = typ.ravel()
+    nx, ny, nz = g.nx, g.ny, g.nz
+    i, j, k = gi % nx, (gi // nx) % ny, gi // (nx * ny)
+    idx = [i, j, k]
+    n = [nx, ny, nz]
+    stride = [1, nx, nx * ny]
+    area = [g.h[1][j] * g.h[2][k], g.h[0][i] * g.h[2][k], g.h[0][i] * g.h[1][j]]
+    nrm = tabs["nrm"]
+    dS = np.zeros(gi.size)
+    for a in axes(g):
+        for side in (-1, 1):
+            has = (idx[a] > 0) if side < 0 else (idx[a] < n[a] - 1)
+            nb = np.where(has, gi + side * stride[a], gi)
+            fl = has & (t[nb] == FLUID)
+            dS += np.where(fl, area[a] * np.abs(nrm[:, a]), 0.0)
+    gc = np.stack([g.c[0][i], g.c[1][j], g.c[2][k]], 1)
+    span = np.linalg.norm(tabs["ip"][:, :g.ndim] - gc[:, :g.ndim], axis=1)
+    pg = p.ravel()[gi]
+    for a in axes(g):
+        ug = u[a].ravel()[gi]
+        dudn = -2.0 * ug / span
+        F[a] = float(np.sum(dS * (-pg * nrm[:, a] + dudn / Re)))
+    return F
+
+
 @dataclass
 class State:
     u: list           # ncomp cell arrays
@@ -458,14 +514,16 @@ def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 
     """One fractional step (rows P1-P4, S, C1). Returns the new State; with
     keep=True also a dict of the intermediate fields. `cache` (a dict)
     keeps matrix factorisations between steps of one run."""
-    alpha = dt / (2.0 * Re)
+    alpha = CN_THETA * dt / Re              # implicit viscous share
+    alpha_e = (1.0 - CN_THETA) * dt / Re    # explicit viscous share
     N = convection(g, typ, st.u, st.F, bc, u_inf)
     Nold = N if st.Nold is None else st.Nold
     ustar = []
     rhs_all = []
     for c in range(g.ncomp):
         Lu = laplacian(g, typ, st.u[c], c, bc, u_inf)
-        rhs = st.u[c] - dt * (1.5 * N[c] - 0.5 * Nold[c]) + alpha * Lu + alpha * bc_source(g, typ, c, bc, u_inf)
+        rhs = (st.u[c] - dt * (AB2[0] * N[c] + AB2[1] * Nold[c]) + alpha_e * Lu
+               + alpha * bc_source(g, typ, c, bc, u_inf))
         rhs = np.where(typ == FLUID, rhs, 0.0)
         lu = None if cache is None else cache.get(("helm", c, alpha))
         if lu is None:

@@ -1,11 +1,12 @@
-// Allocation-free Poisson residual: an entry point for callers that cannot
-// allocate device memory (for instance code running while a stream is being
-// captured into a CUDA graph, where cudaMalloc is not permitted, or host
-// frameworks that own all device memory and forbid allocations inside a
-// step). It evaluates the same quantity that ibm_poisson_solve reports as
+// Allocation-free Poisson residual, for callers that cannot allocate device
+// memory: a host application whose memory manager owns the whole device (a
+// framework's caching pool, or a fixed arena sized at start-up) and forbids
+// libraries to allocate while it runs a step, or a caller running with the
+// device already full, which must not fail for want of a few kilobytes of
+// partial sums. It evaluates the quantity that ibm_poisson_solve reports as
 // rel_residual, ||P(b - A phi)||_2 / ||P b||_2, and needs no buffer from the
 // caller besides its inputs and output: the per-block partial sums live in a
-// file-scope device array.
+// file-scope device array. It has no counterpart in the paper.
 //
 // The array g_noalloc_partials is 3 * NOALLOC_MAX_BLOCKS doubles (96 KiB).
 // Every GPU that loads the library holds it until the process exits. One
@@ -13,14 +14,15 @@
 // NOALLOC_MAX_BLOCKS * NOALLOC_CELLS_PER_BLOCK = 268,435,456 cells are
 // accepted; larger ones are rejected with IBM_ERR_ARG.
 //
-// All calls share the one array and each call overwrites it completely
-// before reading it, so nothing needs clearing between calls; two calls
-// that overlap on the GPU (different streams, or different host threads)
-// race on it. In host code the array's name is only a host-side stand-in for
-// the device symbol, so the device address is fetched with
+// All calls share the one array and each call overwrites every entry it
+// reads before reading it, so nothing needs clearing between calls; two
+// calls that overlap on the GPU (different streams, or different host
+// threads) race on it. In host code the array's name is only a host-side
+// stand-in for the device symbol, so the device address is fetched with
 // cudaGetSymbolAddress once per device, the first time the entry point runs
-// with that device current; that first call should therefore come before any
-// stream capture begins.
+// with that device current; that first call should therefore come before
+// any stream capture begins. The call ends by copying the ratio to rel_out
+// and waiting for the stream.
 #include "ctx.cuh"
 
 #include <math.h>
@@ -61,8 +63,7 @@ __device__ __forceinline__ double fluid_residual(const GridDev &g, const uint8_t
 // pass 1 (mode 0): columns sum vol*rhs, sum vol*(rhs - A phi) over FLUID
 // pass 2 (mode 1): columns sum (rhs - mu_b)^2, sum (r - mu_r)^2 over FLUID
 __global__ void k_noalloc_fluid(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
-                                const double *__restrict__ phi, int mode, double inv_vol,
-                                double *__restrict__ part) {
+                                const double *__restrict__ phi, int mode, double *__restrict__ part) {
     __shared__ double sh[32];
     const double mub = mode ? part[3 * NOALLOC_MAX_BLOCKS - 2] : 0.0;
     const double mur = mode ? part[3 * NOALLOC_MAX_BLOCKS - 1] : 0.0;
@@ -85,7 +86,6 @@ __global__ void k_noalloc_fluid(GridDev g, const uint8_t *__restrict__ type, con
             a1 += dr * dr;
         }
     }
-    (void)inv_vol;
     a0 = block_sum<NOALLOC_THREADS>(a0, sh);
     a1 = block_sum<NOALLOC_THREADS>(a1, sh);
     if (threadIdx.x == 0) {
@@ -159,6 +159,13 @@ extern "C" ibm_status ibm_poisson_residual_noalloc(ibm_ctx *c, const double *rhs
     if (!c) return IBM_ERR_ARG;
     if (!rhs_dev || !phi_dev || !rel_out) return c->fail(IBM_ERR_ARG, "rhs, phi and rel_out must not be NULL");
     if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called first");
+    // a host or stale pointer must not reach the kernels
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, rhs_dev) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+        cudaPointerGetAttributes(&at, phi_dev) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return c->fail(IBM_ERR_ARG, "rhs and phi must be device memory");
+    }
     const int64_t nblocks = (c->N + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK;
     if (nblocks > NOALLOC_MAX_BLOCKS)
         return c->fail(IBM_ERR_ARG, "grid has more than 268,435,456 cells, the scratch limit of "
@@ -166,11 +173,9 @@ extern "C" ibm_status ibm_poisson_residual_noalloc(ibm_ctx *c, const double *rhs
     double *part = nullptr;
     IBM_TRY(noalloc_scratch(c, &part));
     const double inv_vol = 1.0 / c->fluid_vol;
-    k_noalloc_fluid<<<(unsigned)nblocks, NOALLOC_THREADS, 0, c->s>>>(c->g, c->type, rhs_dev, phi_dev, 0, inv_vol,
-                                                                     part);
+    k_noalloc_fluid<<<(unsigned)nblocks, NOALLOC_THREADS, 0, c->s>>>(c->g, c->type, rhs_dev, phi_dev, 0, part);
     k_noalloc_final<<<1, NOALLOC_THREADS, 0, c->s>>>((int)nblocks, 0, inv_vol, part);
-    k_noalloc_fluid<<<(unsigned)nblocks, NOALLOC_THREADS, 0, c->s>>>(c->g, c->type, rhs_dev, phi_dev, 1, inv_vol,
-                                                                     part);
+    k_noalloc_fluid<<<(unsigned)nblocks, NOALLOC_THREADS, 0, c->s>>>(c->g, c->type, rhs_dev, phi_dev, 1, part);
     k_noalloc_ghost<<<1, NOALLOC_THREADS, 0, c->s>>>(c->gh, phi_dev, part);
     k_noalloc_final<<<1, NOALLOC_THREADS, 0, c->s>>>((int)nblocks, 1, inv_vol, part);
     IBM_LAUNCHED(c);

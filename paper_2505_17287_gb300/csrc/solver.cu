@@ -2754,7 +2754,6 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
         st->outer_iters = outer;
         st->inner_iters = inner;
         st->rel_residual = rel;
-        st->lambda_est = 0.0;
         st->ms = ms;
     }
     if (status == IBM_ERR_NOT_CONVERGED) c->fail(IBM_ERR_NOT_CONVERGED, "Poisson solve reached its iteration limit");

@@ -93,10 +93,12 @@ def _opts_kw(o):
     return {k: getattr(o, k) for k, _ in ibm.ibm_solver_opts._fields_}
 
 
-def run_graphs(cases, precision=ibm.IBM_MIXED, tuned=None):
+def run_graphs(cases, precision=ibm.IBM_MIXED, tuned=None, opts=None, fields=False):
     """All cases resident at once, each on its own stream; the step graphs
     are captured during setup (ibm_step_prepare), then every case's steps
-    are enqueued from this thread and run concurrently on the device."""
+    are enqueued from this thread and run concurrently on the device.
+    `opts` (dict) overrides solver options of every case; with fields=True
+    each result also holds the final u, v (w) and p under "fields"."""
     import torch
     from . import synth
     order = sorted(range(len(cases)), key=lambda i: -cases[i].ncells)
@@ -106,6 +108,7 @@ def run_graphs(cases, precision=ibm.IBM_MIXED, tuned=None):
         c = cases[i]
         s = ibm.Solver(c, precision=precision, stream=torch.cuda.Stream())
         kw = _opts_kw(tuned[size_class(c)][0]) if tuned and size_class(c) in tuned else {}
+        kw.update(opts or {})
         kw.update(precision=precision, graph=2)
         s.set_opts(**kw)
         for v, e in synth.case_bodies(c):
@@ -125,6 +128,10 @@ def run_graphs(cases, precision=ibm.IBM_MIXED, tuned=None):
     out = [res[i] for i in range(len(cases))]
     work = sum(cases[i].ncells * out[i]["steps"] for i in range(len(cases)))
     ok = all(r["status"] == ibm.IBM_OK for r in out)
+    if fields:
+        for i, s in solvers.items():
+            names = ("u", "v", "w", "p") if cases[i].ndim == 3 else ("u", "v", "p")
+            out[i]["fields"] = {k: s.get(k) for k in names}
     for s in solvers.values():
         s.close()
     return {"results": out, "ok": ok, "wall_s": wall, "setup_s": setup_s, "enqueue_s": enqueue_s,

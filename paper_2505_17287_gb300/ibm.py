@@ -59,7 +59,7 @@ class ibm_table_info(Structure):
 
 class ibm_solve_stats(Structure):
     _fields_ = [("outer_iters", c_int), ("inner_iters", c_int), ("rel_residual", c_double),
-                ("lambda_est", c_double), ("ms", c_double)]
+                ("ms", c_double)]
 
 
 class ibm_step_stats(Structure):

@@ -293,6 +293,28 @@ def cylinder_case(nx: int = 256, ny: int = 128, nseg: int = 512, Re: float = 100
                 meta={"nx": nx, "ny": ny, "nseg": nseg})
 
 
+def cylinder_clustered_case(h_min: float = 0.02, ratio: float = 1.02, Re: float = 100.0, cfl: float = 0.3,
+                            nsteps: int = 20, nseg: int = 1024) -> Case:
+    """2D cylinder (D = 1 at the origin) in [-15, 30] x [-15, 15] on a grid
+    clustered to the body: uniform spacing h_min over [-0.7, 1.5] x
+    [-0.7, 0.7] (the body and its near wake), growing by `ratio` per cell
+    outside. The shape of the paper's cylinder validation (Section 3.2.1) at
+    the resolution a shedding-frequency and drag check needs (h_min = D/50);
+    dt = cfl * h_min for a unit inflow."""
+    v, e = circle_polyline(nseg, 0.5)
+
+    def count(L, core):
+        lnr = math.log(ratio)
+        return core / h_min + sum(math.log1p(x * lnr / h_min) / lnr for x in L)
+
+    nx = int(round(count((14.3, 28.5), 2.2)))
+    ny = int(round(count((14.3, 14.3), 1.4)))
+    xf = stretched_faces(-15.0, 30.0, nx, -0.7, 1.5, ratio)
+    yf = stretched_faces(-15.0, 15.0, ny, -0.7, 0.7, ratio)
+    return Case("cylinder2d_clustered", 2, xf, yf, np.array([0.0, 1.0]), v, e, Re, cfl * h_min, nsteps,
+                meta={"h_min": h_min, "ratio": ratio, "nseg": nseg})
+
+
 def wing_case(nx: int = 384, ny: int = 256, nz: int = 256, Re: float = 1000.0,
               dt: float = 0.002, nsteps: int = 10, ratio: float = None,
               n_chord: int = 100, n_span: int = 50) -> Case:
@@ -325,6 +347,40 @@ def sphere_case(n: int = 32, radius: float = 0.3, Re: float = 200.0, dt: float =
     h = 2.0 / n
     return Case("sphere3d", 3, f.copy(), f.copy(), f.copy(), v, t, Re,
                 dt if dt is not None else 0.2 * h, nsteps)
+
+
+def taylor_green_case(n: int = 32, Re: float = 1.0, dt: float = 0.0025, nsteps: int = 20) -> Case:
+    """Decaying Taylor-Green vortex on the unit square, uniform n x n grid,
+    meant for free-slip (SLIP) walls on all four sides and u_inf = 0.
+
+    The solver wants a body, so this case carries a small closed polygon
+    far outside the domain: every cell is FLUID and there are no ghosts.
+    The initial fields come from `taylor_green_fields`."""
+    v, e = circle_polyline(16, 0.05, 5.0, 5.0)
+    f = uniform_faces(0.0, 1.0, n)
+    return Case("taylor_green2d", 2, f.copy(), f.copy(), np.array([0.0, 1.0]), v, e, Re, dt, nsteps,
+                u_inf=(0.0, 0.0, 0.0), meta={"n": n})
+
+
+def taylor_green_fields(case: Case, t: float = 0.0):
+    """The Taylor-Green vortex u = sin(pi x) cos(pi y) F, v = -cos(pi x)
+    sin(pi y) F, F = exp(-2 pi^2 t / Re), sampled at the cell centres (u, v)
+    and at the face centres (face_u on x-faces, face_v on y-faces), as
+    arrays shaped [1, ny, nx], [1, ny, nx + 1] and [1, ny + 1, nx]. Its
+    pressure is p = (cos(2 pi x) + cos(2 pi y)) F^2 / 4 (returned as p).
+    An exact solution of the incompressible Navier-Stokes equations with
+    free-slip walls on the unit square."""
+    xc, yc = 0.5 * (case.xf[:-1] + case.xf[1:]), 0.5 * (case.yf[:-1] + case.yf[1:])
+    F = math.exp(-2.0 * math.pi ** 2 * t / case.Re)
+    Yc, Xc = np.meshgrid(yc, xc, indexing="ij")
+    Yu, Xu = np.meshgrid(yc, case.xf, indexing="ij")
+    Yv, Xv = np.meshgrid(case.yf, xc, indexing="ij")
+    pi = math.pi
+    return dict(u=(np.sin(pi * Xc) * np.cos(pi * Yc) * F)[None],
+                v=(-np.cos(pi * Xc) * np.sin(pi * Yc) * F)[None],
+                face_u=(np.sin(pi * Xu) * np.cos(pi * Yu) * F)[None],
+                face_v=(-np.cos(pi * Xv) * np.sin(pi * Yv) * F)[None],
+                p=(0.25 * (np.cos(2 * pi * Xc) + np.cos(2 * pi * Yc)) * F * F)[None])
 
 
 def ensemble_2d(ncases: int = 64, seed: int = 250517287):
