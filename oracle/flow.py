@@ -25,8 +25,10 @@ Readings where the paper is silent (each listed in the design notes):
     is the one with A phi = b - lam * 1_fluid for the scalar lam that makes
     the system consistent, normalised to zero volume-weighted fluid mean.
 
-Every linear system here is solved by scipy's sparse direct LU: the
-solution is then the plain definition, reached by no iteration.
+Every linear system is solved by scipy's sparse direct LU by default: the
+solution is then the plain definition, reached by no iteration. For grids
+too large to factorise, solver="iter" reaches the same solutions by
+BiCGStab (the paper's Krylov method), pinned against the LU on small grids.
 
 Array layout: cell arrays are [nz, ny, nx] (x fastest); x-face arrays are
 [nz, ny, nx+1], y-face [nz, ny+1, nx], z-face [nz+1, ny, nx]. In 2D nz = 1,
@@ -419,6 +421,179 @@ def solve_poisson(g: Grid, typ, tabs, b, A=None, cache=None):
 
 
 # ---------------------------------------------------------------------------
+# Iterative solves, for grids too large for the sparse direct LU
+# ---------------------------------------------------------------------------
+#
+# The paper solves its linear systems with BiCGStab (Section 2.1). Here
+# BiCGStab is the oracle's second, independent route to the same discrete
+# solutions as the direct LU: it is checked against the LU on small grids
+# and carries the comparisons on grids of millions of cells. Its
+# preconditioner for the pressure is the exact inverse of the body-free
+# operator on the same tensor grid (fast diagonalisation by the 1D
+# generalised eigenproblems of each axis), a different algorithm from the
+# GPU path's multigrid.
+
+def bicgstab(apply_M, apply_K, b, x0, rtol, maxit, norm=np.linalg.norm):
+    """Right-preconditioned BiCGStab (van der Vorst, 1992): solves
+    M x = b, iterating on M K y = b with x = K y. Stops when
+    norm(b - M x) <= rtol * norm(b). Returns (x, iterations, relative
+    residual)."""
+    x = x0.copy()
+    r = b - apply_M(x)
+    bn = norm(b)
+    if bn == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    rel = norm(r) / bn
+    if rel <= rtol:
+        return x, 0, rel
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for it in range(1, maxit + 1):
+        rho = float(np.dot(rhat, r))
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = apply_K(p)
+        v = apply_M(ph)
+        alpha = rho / float(np.dot(rhat, v))
+        s_ = r - alpha * v
+        sh = apply_K(s_)
+        t = apply_M(sh)
+        tt = float(np.dot(t, t))
+        omega = float(np.dot(t, s_)) / tt if tt > 0.0 else 0.0
+        x = x + alpha * ph + omega * sh
+        r = s_ - omega * t
+        rho_old = rho
+        # the recursively updated r drifts from b - M x near the rounding
+        # floor: test (and restart from) the true residual
+        rel = norm(r) / bn
+        if rel <= rtol or it == maxit:
+            r = b - apply_M(x)
+            rel = norm(r) / bn
+            if rel <= rtol:
+                return x, it, rel
+            rhat = r.copy()
+            rho_old = alpha = omega = 1.0
+            v = np.zeros_like(b)
+            p = np.zeros_like(b)
+    return x, maxit, rel
+
+
+def _neumann_1d(g: Grid, a):
+    """1D cell-centred operator of axis a with zero-flux ends, as a dense
+    matrix K (K[i, i+1] = K[i+1, i] = 1/hc, rows summing to 0)."""
+    n = len(g.h[a])
+    K = np.zeros((n, n))
+    t = 1.0 / g.hc[a]
+    idx = np.arange(n - 1)
+    K[idx, idx + 1] = t
+    K[idx + 1, idx] = t
+    K[idx, idx] -= t
+    K[idx + 1, idx + 1] -= t
+    return K
+
+
+class SeparableInverse:
+    """Exact (pseudo-)inverse of the body-free pressure operator on the
+    tensor grid g, with zero-flux outer faces. vol * A = sum over axes of
+    K_a (x) D_b (x) D_c (K_a the 1D operator, D the cell widths); with the
+    generalised eigenpairs K_a V_a = D_a V_a M_a, V_a^T D_a V_a = I, the
+    operator is diagonal in the basis W = V_x (x) V_y (x) V_z:
+    A^+ r = W (M_x + M_y + M_z)^+ W^T (vol r), the zero eigenvalue (the
+    constants) left out."""
+
+    def __init__(self, g: Grid):
+        import scipy.linalg as sla
+        self.g = g
+        self.V = []
+        mus = []
+        for a in range(3):
+            if a < g.ndim:
+                mu, V = sla.eigh(_neumann_1d(g, a), np.diag(g.h[a]))
+            else:
+                mu, V = np.zeros(1), np.ones((1, 1)) / np.sqrt(g.h[a][0])
+            self.V.append(V)
+            mus.append(mu)
+        L = mus[0][None, None, :] + mus[1][None, :, None] + mus[2][:, None, None]
+        tol = 1e-12 * np.abs(L).max()
+        self.Linv = np.where(np.abs(L) > tol, 1.0 / np.where(np.abs(L) > tol, L, 1.0), 0.0)
+
+    def _along(self, t, M, a):
+        """out[.., i', ..] = sum_i t[.., i, ..] M[i, i'] over the index of
+        axis a (0 = x, the last array axis); every product is a contiguous
+        matrix product."""
+        nz, ny, nx = t.shape
+        if a == 0:
+            return (t.reshape(-1, nx) @ M).reshape(nz, ny, nx)
+        if a == 1:
+            return np.matmul(M.T, t)
+        return (M.T @ t.reshape(nz, -1)).reshape(nz, ny, nx)
+
+    def apply(self, r):
+        t = self.g.vol * r.reshape(self.g.shape)
+        for a in range(self.g.ndim):
+            t = self._along(t, self.V[a], a)          # W^T
+        t = t * self.Linv
+        for a in range(self.g.ndim):
+            t = self._along(t, self.V[a].T, a)        # W
+        return t
+
+
+def solve_poisson_iter(g: Grid, typ, tabs, b, A=None, rtol=1e-13, maxit=2000, sep=None):
+    """The Poisson solution of solve_poisson (A phi = b - lam 1_FLUID, zero
+    volume-weighted FLUID mean), reached by BiCGStab on P A phi = P b, with
+    P the projection that removes the volume-weighted FLUID mean of the
+    FLUID rows (its kernel is 1_FLUID, so P r = 0 means r = lam 1_FLUID).
+    DEAD cells are 0. Preconditioner: the body-free exact inverse on FLUID
+    rows, then each ghost row solved for its ghost value from the updated
+    neighbours (z_G = r_G + sum wp z_m), DEAD rows 0.
+    Returns (phi, lam, iterations, relative residual)."""
+    if A is None:
+        A = poisson_matrix(g, typ, tabs)
+    if sep is None:
+        sep = SeparableInverse(g)
+    t = typ.ravel()
+    fl, gh, dead = t == FLUID, t == GHOST, t == DEAD
+    v = np.where(fl, g.vol.ravel(), 0.0)
+    vsum = float(v.sum())
+    gi, sidx, wp = tabs["gidx"], tabs["sidx"], tabs["wp"]
+
+    def P(r):
+        r = np.where(dead, 0.0, r)
+        m = float(np.dot(v, r)) / vsum
+        return np.where(fl, r - m, r)
+
+    def M(x):
+        return P(A @ np.where(dead, 0.0, x))
+
+    def K(r):
+        z = sep.apply(np.where(fl, r, 0.0)).ravel()
+        z[dead] = 0.0
+        if gi.size:
+            z[gi] = r[gi] + np.sum(wp * z[sidx], axis=1)
+        return z
+
+    bb = P(b.ravel())
+    x, it, rel = bicgstab(M, K, bb, np.zeros(g.N), rtol, maxit)
+    phi = normalise(g, typ, x.reshape(g.shape))
+    r = (b.ravel() - A @ phi.ravel())
+    lam = float(np.dot(v, r)) / vsum
+    return phi, lam, it, rel
+
+
+def solve_helmholtz_iter(H, rhs, x0=None, rtol=1e-14, maxit=500):
+    """Crank-Nicolson velocity system H u = rhs (helmholtz_matrix) by
+    BiCGStab with the inverse diagonal as preconditioner. Returns (u,
+    iterations, relative residual)."""
+    d = H.diagonal()
+    dinv = 1.0 / d
+    b = rhs.ravel()
+    x0 = np.zeros_like(b) if x0 is None else x0.ravel()
+    return bicgstab(lambda x: H @ x, lambda r: dinv * r, b, x0, rtol, maxit)
+
+
+# ---------------------------------------------------------------------------
 # Ghost refresh and state
 # ---------------------------------------------------------------------------
 
@@ -510,10 +685,12 @@ def initial_state(g: Grid, typ, tabs, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
 
 
 def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0),
-         A=None, keep=False, cache=None):
+         A=None, keep=False, cache=None, solver="direct", rtol=1e-13, helm_rtol=1e-14):
     """One fractional step (rows P1-P4, S, C1). Returns the new State; with
     keep=True also a dict of the intermediate fields. `cache` (a dict)
-    keeps matrix factorisations between steps of one run."""
+    keeps matrix factorisations between steps of one run. solver="iter"
+    solves the Helmholtz and Poisson systems by BiCGStab (to helm_rtol and
+    rtol) instead of the direct LU, for grids too large to factorise."""
     alpha = CN_THETA * dt / Re              # implicit viscous share
     alpha_e = (1.0 - CN_THETA) * dt / Re    # explicit viscous share
     N = convection(g, typ, st.u, st.F, bc, u_inf)
@@ -525,12 +702,20 @@ def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 
         rhs = (st.u[c] - dt * (AB2[0] * N[c] + AB2[1] * Nold[c]) + alpha_e * Lu
                + alpha * bc_source(g, typ, c, bc, u_inf))
         rhs = np.where(typ == FLUID, rhs, 0.0)
-        lu = None if cache is None else cache.get(("helm", c, alpha))
-        if lu is None:
-            lu = spla.splu(helmholtz_matrix(g, typ, tabs, c, alpha, bc).tocsc())
-            if cache is not None:
-                cache[("helm", c, alpha)] = lu
-        x = lu.solve(rhs.ravel()).reshape(g.shape)
+        if solver == "iter":
+            H = None if cache is None else cache.get(("helmH", c, alpha))
+            if H is None:
+                H = helmholtz_matrix(g, typ, tabs, c, alpha, bc)
+                if cache is not None:
+                    cache[("helmH", c, alpha)] = H
+            x = solve_helmholtz_iter(H, rhs, st.u[c], helm_rtol)[0].reshape(g.shape)
+        else:
+            lu = None if cache is None else cache.get(("helm", c, alpha))
+            if lu is None:
+                lu = spla.splu(helmholtz_matrix(g, typ, tabs, c, alpha, bc).tocsc())
+                if cache is not None:
+                    cache[("helm", c, alpha)] = lu
+            x = lu.solve(rhs.ravel()).reshape(g.shape)
         ustar.append(x)
         rhs_all.append(rhs)
     Fs = face_velocity(g, typ, ustar, bc, u_inf)
@@ -538,7 +723,15 @@ def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 
     b = project_rhs(g, typ, braw)
     if A is None:
         A = poisson_matrix(g, typ, tabs)
-    phi, lam = solve_poisson(g, typ, tabs, b, A, cache)
+    if solver == "iter":
+        sep = None if cache is None else cache.get("sep")
+        if sep is None:
+            sep = SeparableInverse(g)
+            if cache is not None:
+                cache["sep"] = sep
+        phi, lam, _, _ = solve_poisson_iter(g, typ, tabs, b, A, rtol, sep=sep)
+    else:
+        phi, lam = solve_poisson(g, typ, tabs, b, A, cache)
     Fn, un = project(g, typ, ustar, Fs, phi, dt)
     un = refresh_velocity_ghosts(g, typ, tabs, un)
     new = State(un, Fn, phi, N, st.nstep + 1)
@@ -566,11 +759,13 @@ def project(g: Grid, typ, ustar, Fs, phi, dt):
     return Fn, un
 
 
-def run(g: Grid, typ, tabs, nsteps, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0), st=None):
+def run(g: Grid, typ, tabs, nsteps, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0), st=None, solver="direct",
+        rtol=1e-13, helm_rtol=1e-14):
     if st is None:
         st = initial_state(g, typ, tabs, bc, u_inf)
     A = poisson_matrix(g, typ, tabs)
     cache = {}
     for _ in range(nsteps):
-        st = step(g, typ, tabs, st, Re, dt, bc, u_inf, A, cache=cache)
+        st = step(g, typ, tabs, st, Re, dt, bc, u_inf, A, cache=cache, solver=solver, rtol=rtol,
+                  helm_rtol=helm_rtol)
     return st

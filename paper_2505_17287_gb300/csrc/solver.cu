@@ -137,8 +137,12 @@ ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_hos
 // Accumulator type of per-thread partial sums: FP64 for FP64 vectors; FP32
 // for FP32 vectors, whose cross-thread reductions are FP64 (per-element FP64
 // arithmetic would make the FP32 streaming kernels FP64-bound on GB300)
+// Dot products and volume sums accumulate in FP64 in both precisions (the
+// FP32 inner Krylov cycle included). FP32 vectors form leaves of four
+// products in FP32 (the lanes of one 16-byte load, or four consecutive
+// cells) and add each leaf to an FP64 per-thread partial: one FP64 add per
+// four cells, so the FP32 streaming kernels stay off the FP64 pipe's limit.
 template <typename T> struct Acc { typedef double type; };
-template <> struct Acc<float> { typedef float type; };
 
 // per-axis operator coefficients in precision T (the FP64 ones are the
 // GridDev arrays; FP32 copies serve the FP32 Krylov cycle of mixed mode)
@@ -195,7 +199,7 @@ __global__ void k_apply_A(GridDev g, OpT<T> o, const uint8_t *__restrict__ type,
         const T v = PLAIN ? A_row<T>(g, o, x, c, i, j, k) : sgn * A_row<T>(g, o, x, c, i, j, k) + (b ? b[c] : T(0));
         y[c] = v;
         if constexpr (sizeof(T) == 8) acc += o.vol[c] * v;
-        else acc += (o.dx[i] * o.dy[j] * o.dz[k]) * v;
+        else acc += (double)((o.dx[i] * o.dy[j] * o.dz[k]) * v);
     }
     const double tot = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(RED_THREADS)
     k_apply_A4(GridDev g, OpT<float> o, const uint8_t *__restrict__ type, const float *__restrict__ x,
                const float *__restrict__ b, float sgn, float *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
-    float acc = 0.f;
+    double acc = 0.0;
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     GRID_STRIDE(q, g.n / 4) {
         const int64_t c = 4 * q;
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         const float czm = g.ndim == 3 ? o.czm[k] : 0.f, czp = g.ndim == 3 ? o.czp[k] : 0.f;
         float out[4];
         bool ghost = false;
+        float leaf = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float xe = f4get(xc, e);
@@ -250,8 +255,9 @@ __global__ void __launch_bounds__(RED_THREADS)
             const uint8_t t = u4get(t4, e);
             ghost |= t == GHOST;
             out[e] = t == DEAD ? 0.f : v;
-            if (t == FLUID) acc += (f4get(dxv, e) * dyj * dzk) * v;
+            if (t == FLUID) leaf += (f4get(dxv, e) * dyj * dzk) * v;
         }
+        acc += (double)leaf;
         if (!ghost) {
             *reinterpret_cast<float4 *>(y + c) = make_float4(out[0], out[1], out[2], out[3]);
         } else {
@@ -396,14 +402,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n, const T *__rest
 #pragma unroll
         for (int q = 0; q < NC; ++q) b[q] = reinterpret_cast<const VT *>(V.p[q])[v];
 #pragma unroll
-        for (int q = 0; q < NC; ++q)
+        for (int q = 0; q < NC; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                T leaf = T(0);
 #pragma unroll
-            for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b[q], e);
+                for (int e = 0; e < W; ++e) leaf += vget(a, e) * vget(b[q], e);
+                acc[q] += (A)leaf;
+            } else {
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[q] += (A)vget(a, e) * (A)vget(b[q], e);
+            }
+        }
     }
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        const A a = (A)w[c];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) acc[q] += a * (A)V.p[q][c];
+        for (int q = 0; q < NC; ++q) acc[q] += (A)(w[c] * V.p[q][c]);
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
@@ -432,15 +445,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(int64_t n, T *__restrict__
 #pragma unroll
             for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - (T)h.v[q] * vget(b[q], e));
         reinterpret_cast<VT *>(w)[v] = a;
+        if constexpr (sizeof(T) == 4) {
+            T leaf = T(0);
 #pragma unroll
-        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+            for (int e = 0; e < W; ++e) leaf += vget(a, e) * vget(a, e);
+            ww += (A)leaf;
+        } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+        }
     }
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         T a = w[c];
 #pragma unroll
         for (int q = 0; q < NC; ++q) a -= (T)h.v[q] * V.p[q][c];
         w[c] = a;
-        ww += (A)a * (A)a;
+        ww += (A)(a * a);
     }
     const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -515,28 +535,42 @@ __global__ void k_add_scaled(int64_t n, const uint8_t *__restrict__ type, double
     GRID_STRIDE(c, n) if (type[c] != DEAD) phi[c] += a * ((double)d[c] - m);
 }
 
-// FLUID volume-weighted sum of an FP32 vector (FP32 widths and per-thread
-// partials, FP64 across warps and blocks)
+// FLUID volume-weighted sum of an FP32 vector: FP32 volumes and products,
+// leaves of four consecutive cells in FP32, FP64 across leaves, warps and
+// blocks
 __global__ void k_fluid_volsum32(GridDev g, OpT<float> o, const uint8_t *__restrict__ type,
                                  const float *__restrict__ x, double *__restrict__ part) {
     __shared__ double sh[32];
-    float acc = 0.f;
-    GRID_STRIDE(c, g.n) {
-        if (type[c] != FLUID) continue;
-        int i, j, k;
-        split3(g, (uint32_t)c, i, j, k);
-        acc += (o.dx[i] * o.dy[j] * o.dz[k]) * x[c];
+    double acc = 0.0;
+    GRID_STRIDE(q, (g.n + 3) / 4) {
+        float leaf = 0.f;
+        for (int64_t c = 4 * q; c < 4 * q + 4 && c < g.n; ++c) {
+            if (type[c] != FLUID) continue;
+            int i, j, k;
+            split3(g, (uint32_t)c, i, j, k);
+            leaf += (o.dx[i] * o.dy[j] * o.dz[k]) * x[c];
+        }
+        acc += (double)leaf;
     }
     const double t = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// (FP32 vectors: per-thread FP32 partials, FP64 across warps and blocks)
+// (FP32 vectors: leaves of four consecutive products in FP32, FP64
+// per-thread partials, FP64 across warps and blocks)
 template <typename T>
 __global__ void k_dotT(int64_t n, const T *__restrict__ a, const T *__restrict__ b, double *__restrict__ part) {
     __shared__ double sh[32];
-    typename Acc<T>::type acc = 0;
-    GRID_STRIDE(c, n) acc += a[c] * b[c];
+    double acc = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        GRID_STRIDE(q, (n + 3) / 4) {
+            T leaf = T(0);
+            for (int64_t c = 4 * q; c < 4 * q + 4 && c < n; ++c) leaf += a[c] * b[c];
+            acc += (double)leaf;
+        }
+    } else {
+        GRID_STRIDE(c, n) acc += a[c] * b[c];
+    }
     const double t = block_sum<RED_THREADS>(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -2304,15 +2338,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth_dev(int64_t n, T *__restri
 #pragma unroll
             for (int e = 0; e < W; ++e) vset(a, e, vget(a, e) - hv[q] * vget(b[q], e));
         reinterpret_cast<VT *>(w)[v] = a;
+        if constexpr (sizeof(T) == 4) {
+            T leaf = T(0);
 #pragma unroll
-        for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+            for (int e = 0; e < W; ++e) leaf += vget(a, e) * vget(a, e);
+            ww += (A)leaf;
+        } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e) ww += (A)vget(a, e) * (A)vget(a, e);
+        }
     }
     for (int64_t c = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         T a = w[c];
 #pragma unroll
         for (int q = 0; q < NC; ++q) a -= hv[q] * V.p[q][c];
         w[c] = a;
-        ww += (A)a * (A)a;
+        ww += (A)(a * a);
     }
     const double t = block_sum<RED_THREADS>(ww, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -2359,13 +2400,15 @@ __global__ void k_add_scaled_dev(int64_t n, const uint8_t *__restrict__ type, do
 __global__ void k_fg_setup(DevFG *F, const double *bn2, double rtol, int maxit) {
     const double bnorm = sqrt(*bn2);
     F->bnorm = bnorm;
-    F->zero = !(bnorm > 1e-300);
+    // a non-finite right-hand side is reported, not solved (phi is zeroed)
+    const bool bad = !isfinite(bnorm);
+    F->zero = bad || !(bnorm > 1e-300);
     F->rtol = rtol;
     F->maxit = maxit;
     F->outer = 0;
     F->cycles = 0;
     F->single = 0;
-    F->status = 0;
+    F->status = bad ? IBM_ERR_DIVERGED : 0;
     F->rel = 0.0;
     F->refinements = 0;
     F->stalls = 0;
@@ -2727,6 +2770,7 @@ ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, in
     double bn2;
     IBM_TRY(norm2<double>(c, c->b, &bn2));
     const double bnorm = sqrt(bn2);
+    if (!isfinite(bnorm)) return c->fail(IBM_ERR_DIVERGED, "Poisson right-hand side is not finite");
     int outer = 0, inner = 0;
     double rel = 0.0;
     ibm_status status = IBM_OK;

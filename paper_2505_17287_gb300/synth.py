@@ -315,6 +315,17 @@ def cylinder_clustered_case(h_min: float = 0.02, ratio: float = 1.02, Re: float 
                 meta={"h_min": h_min, "ratio": ratio, "nseg": nseg})
 
 
+def wake_bump(case: Case, amp: float = 0.3, x0: float = 1.5, y0: float = 0.3, width2: float = 0.5):
+    """A smooth off-axis bump amp * exp(-((x - x0)^2 + (y - y0)^2) / width2)
+    at the cell centres of a 2D case (shape [1, ny, nx]): added to the
+    initial cross-stream velocity behind a cylinder, it breaks the mirror
+    symmetry so that vortex shedding starts within tens of time units
+    instead of waiting for round-off to grow."""
+    xc, yc = 0.5 * (case.xf[:-1] + case.xf[1:]), 0.5 * (case.yf[:-1] + case.yf[1:])
+    Y, X = np.meshgrid(yc, xc, indexing="ij")
+    return (amp * np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / width2))[None]
+
+
 def wing_case(nx: int = 384, ny: int = 256, nz: int = 256, Re: float = 1000.0,
               dt: float = 0.002, nsteps: int = 10, ratio: float = None,
               n_chord: int = 100, n_span: int = 50) -> Case:
