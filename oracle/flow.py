@@ -314,7 +314,8 @@ def helmholtz_matrix(g: Grid, typ, tabs, comp, alpha, bc=DEFAULT_BC):
             rows.append(c[m])
             cols.append(nb[m])
             vals.append(-alpha * T[m] / vol[c[m]])
-            np.add.at(diag, c[m], alpha * T[m] / vol[c[m]])
+            # (each cell appears once per face direction: a plain add)
+            diag += np.bincount(c[m], weights=alpha * T[m] / vol[c[m]], minlength=g.N)
         for side in (0, 1):
             isd, _ = bc_dirichlet(bc, a, side, comp, (0.0, 0.0, 0.0))
             if not isd:
@@ -324,7 +325,7 @@ def helmholtz_matrix(g: Grid, typ, tabs, comp, alpha, bc=DEFAULT_BC):
             A = np.broadcast_to(g.area[a], g.face_shape(a))[_sl(a, 0, 1)].ravel()
             hh = 0.5 * g.h[a][0 if side == 0 else -1]
             m = t[ids] == FLUID
-            np.add.at(diag, ids[m], alpha * A[m] / (hh * vol[ids[m]]))
+            diag += np.bincount(ids[m], weights=alpha * A[m] / (hh * vol[ids[m]]), minlength=g.N)
     gi = tabs["gidx"]
     rows += [np.repeat(gi, 8)]
     cols += [tabs["sidx"].ravel()]
