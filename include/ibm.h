@@ -151,6 +151,12 @@ typedef struct {
                            Jacobi spectral radius (Young's optimum for a red-black
                            ordered 7-point operator); 1 = Gauss-Seidel; otherwise the
                            factor itself, in (0, 2) */
+    int fine_split;     /* 1: the finest FP32 multigrid level (mixed precision, nx a
+                           multiple of 8) keeps x, f and the open-face mask with the
+                           two red-black colours stored apart (each row's cells of one
+                           colour packed in x order), so a colour pass streams only the
+                           other colour's x and its own f; same arithmetic and results
+                           bit for bit as 0, the cell-ordered layout */
 } ibm_solver_opts;
 
 typedef struct {
@@ -213,7 +219,7 @@ enum {
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6, helm_omega 1. */
+   helm_check_first 6, helm_omega 1, fine_split 1. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

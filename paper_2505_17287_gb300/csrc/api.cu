@@ -124,6 +124,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->reorth_eta = 0.3;
     o->helm_check_first = 6;
     o->helm_omega = 1.0;
+    o->fine_split = 1;
     return IBM_OK;
 }
 
@@ -161,6 +162,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
         return false;
     }
     if (!(o->smooth_omega > 0.0 && o->smooth_omega < 2.0)) { why = "smooth_omega must be in (0, 2)"; return false; }
+    if (o->fine_split != 0 && o->fine_split != 1) { why = "fine_split must be 0 or 1"; return false; }
     if (o->inner_iters > 1 && o->smooth_omega != 1.0) { why = "smooth_omega must be 1 when inner_iters > 1"; return false; }
     return true;
 }

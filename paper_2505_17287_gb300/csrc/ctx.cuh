@@ -14,6 +14,17 @@ struct MGHier {
     T *wx = nullptr, *wy = nullptr, *wz = nullptr, *rhx = nullptr, *rhy = nullptr, *rhz = nullptr;
     // PCG vectors on level 0
     T *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
+    // level 0 in colour-split storage (fine variant, nx a multiple of 8):
+    // the cells of colour q ((i + j + k) & 1 == q) of each row packed in i
+    // order at h = i >> 1, row stride nx / 2; xs and fs are the V-cycle's
+    // level-0 x and f during a cycle, ms the open-face mask. The per-row
+    // metrics of the packed cells: swx[pc][h] = wx[2h + pc], srm[pc][h] =
+    // rhx[2h + pc], srp[pc][h] = rhx[2h + pc + 1] (pc the row's offset of the
+    // colour, (q + j + k) & 1)
+    bool split = false;
+    T *xs[2] = {nullptr, nullptr}, *fs[2] = {nullptr, nullptr};
+    uint8_t *ms[2] = {nullptr, nullptr};
+    T *swx[2] = {nullptr, nullptr}, *srm[2] = {nullptr, nullptr}, *srp[2] = {nullptr, nullptr};
     // per fine level: residual scratch (level >= 1) and 1 / sum of the active
     // coarse interpolation weights of each cell (trilinear transfer)
     std::vector<T *> res, pn;

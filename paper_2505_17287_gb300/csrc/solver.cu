@@ -813,6 +813,263 @@ __global__ void __launch_bounds__(512, 4)
     if (wr) x[c] = v;
 }
 
+// ---------------------------------------------------------------------------
+// Level 0 in colour-split storage (FP32 fine variant)
+// ---------------------------------------------------------------------------
+//
+// The cells of colour q of row (j, k) sit at packed index h = i >> 1 of row
+// j + ny k in array q (H = nx / 2 packed cells per row; nx a multiple of 8,
+// so a packed row is a whole number of 16-byte quads). The cell at packed h
+// has i = 2h + pc, pc = (q + j + k) & 1, and all six neighbours have the
+// other colour: x - 1 at packed h - 1 + pc and x + 1 at h + pc of the same
+// row, the y and z neighbours at h of the neighbouring rows. A colour pass
+// then reads the other colour's x once (s/2 per cell), its own f (s/2) and
+// mask byte (1/2) and writes its own x (s/2): the method's minimum, where
+// the cell-ordered pass moves whole 32-byte sectors of both colours.
+//
+// A thread updates one quad (four consecutive packed cells of one colour)
+// with 16-byte accesses: the other colour's quad of the same row and one
+// edge value give both x neighbours, one quad per y and z neighbour row.
+// Each cell evaluates the expression of k_offdiag<float, true> in its
+// order, so results equal the cell-ordered kernels bit for bit.
+
+template <typename T>
+struct SplitLv {
+    int nx, ny, nz, H;   // H = nx / 2
+    FastDiv fq, fny;     // division by the quads per packed row (H / 4) and by ny
+    int64_t nq;          // quads per colour
+    const T *wy, *wz, *rhy, *rhz;
+    const T *swx0, *swx1, *srm0, *srm1, *srp0, *srp1;   // per row offset pc (see MGHier)
+};
+
+template <typename T>
+static SplitLv<T> split_of(const MGHier<T> &H) {
+    const MGLevel<T> &L = H.lv[0];
+    SplitLv<T> s;
+    s.nx = L.nx;
+    s.ny = L.ny;
+    s.nz = L.nz;
+    s.H = L.nx / 2;
+    s.fq = FastDiv((uint32_t)(L.nx / 8));
+    s.fny = FastDiv((uint32_t)L.ny);
+    s.nq = L.n / 8;
+    s.wy = H.wy;
+    s.wz = H.wz;
+    s.rhy = H.rhy;
+    s.rhz = H.rhz;
+    s.swx0 = H.swx[0]; s.swx1 = H.swx[1];
+    s.srm0 = H.srm[0]; s.srm1 = H.srm[1];
+    s.srp0 = H.srp[0]; s.srp1 = H.srp[1];
+    return s;
+}
+
+__device__ __forceinline__ float f4at(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+// quad q of a colour: packed row, first packed index, (j, k)
+__device__ __forceinline__ void split_quad_pos(const SplitLv<float> &L, int64_t q, int64_t &base, int &h0, int &j,
+                                               int &k) {
+    const uint32_t row = L.fq.div((uint32_t)q);
+    h0 = 4 * (int)((uint32_t)q - row * (uint32_t)(L.H / 4));
+    row_jk(row, L.fny, L.ny, j, k);
+    base = (int64_t)row * L.H + h0;
+}
+
+// sum over the open faces of T_f x_nb and the face sum d for the four cells
+// of a quad (the order and operations of k_offdiag<float, true>)
+__device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const float *__restrict__ xo, int64_t base,
+                                              int h0, int j, int k, int pc, uchar4 m4, float4 O, float s[4],
+                                              float d[4]) {
+    const int64_t sy = L.H, sz = (int64_t)L.H * L.ny;
+    float xe = 0.f;   // x - 1 of cell 0 (pc = 0) or x + 1 of cell 3 (pc = 1)
+    if (pc == 0) {
+        if (h0 > 0) xe = xo[base - 1];
+    } else if (h0 + 4 < L.H) {
+        xe = xo[base + 4];
+    }
+    const float4 ym = j > 0 ? ld4(xo + base - sy) : O;
+    const float4 yp = j < L.ny - 1 ? ld4(xo + base + sy) : O;
+    float4 zm = O, zp = O;
+    if (L.nz > 1) {
+        if (k > 0) zm = ld4(xo + base - sz);
+        if (k < L.nz - 1) zp = ld4(xo + base + sz);
+    }
+    const float4 wx4 = ld4((pc ? L.swx1 : L.swx0) + h0);
+    const float4 rm4 = ld4((pc ? L.srm1 : L.srm0) + h0);
+    const float4 rp4 = ld4((pc ? L.srp1 : L.srp0) + h0);
+    const float wyj = L.wy[j], wzk = L.wz[k], ry0 = L.rhy[j], ry1 = L.rhy[j + 1], rz0 = L.rhz[k], rz1 = L.rhz[k + 1];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
+        const float xm = pc ? f4at(O, e) : (e == 0 ? xe : f4at(O, e - 1));
+        const float xp = pc ? (e == 3 ? xe : f4at(O, e + 1)) : f4at(O, e);
+        const float wxe = f4at(wx4, e);
+        const float ayz = wyj * wzk, axz = wxe * wzk, axy = wxe * wyj;
+        float dd = 0.f, ss = 0.f, t;
+        if (msk & 1u) { t = ayz * f4at(rm4, e); dd += t; ss += t * xm; }
+        if (msk & 2u) { t = ayz * f4at(rp4, e); dd += t; ss += t * xp; }
+        if (msk & 4u) { t = axz * ry0; dd += t; ss += t * f4at(ym, e); }
+        if (msk & 8u) { t = axz * ry1; dd += t; ss += t * f4at(yp, e); }
+        if (msk & 16u) { t = axy * rz0; dd += t; ss += t * f4at(zm, e); }
+        if (msk & 32u) { t = axy * rz1; dd += t; ss += t * f4at(zp, e); }
+        s[e] = ss;
+        d[e] = dd;
+    }
+}
+
+// One colour pass (colour col, other colour's x in xo) on level 0 in split
+// storage; cells that are not updated keep their value. With NAT the pass is
+// the last of the V-cycle: instead of xq it writes the cell-ordered output
+// xn (both colours: this colour's new values, the other colour's from xo).
+template <bool OMEGA, bool NAT>
+__global__ void __launch_bounds__(256)
+    k_rbgs_split(SplitLv<float> L, const float *__restrict__ fq, const uint8_t *__restrict__ mq,
+                 const float *__restrict__ xo, float *__restrict__ xq, int col, float w, float *__restrict__ xn) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= L.nq) return;
+    int64_t base;
+    int h0, j, k;
+    split_quad_pos(L, q, base, h0, j, k);
+    const int pc = (col + j + k) & 1;
+    const uchar4 m4 = *reinterpret_cast<const uchar4 *>(mq + base);
+    const unsigned any = (m4.x | m4.y | m4.z | m4.w) & 0x80u;
+    const float4 O = ld4(xo + base);
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    bool up[4] = {false, false, false, false};
+    if (any) {
+        float sv[4], dv[4];
+        split_offdiag(L, xo, base, h0, j, k, pc, m4, O, sv, dv);
+        const float4 f4 = ld4(fq + base);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
+            const float s = f4at(f4, e) + sv[e];
+            if ((msk & 0x80u) && dv[e] > 0.f) {
+                v[e] = fast_div(s, dv[e]);
+                up[e] = true;
+            }
+        }
+    }
+    const bool all = up[0] && up[1] && up[2] && up[3];
+    if (!NAT && !any) return;   // no active cell: nothing changes
+    if (OMEGA || !all) {
+        // the old values: the relaxation needs them, and cells not updated keep them
+        const float4 old = ld4(xq + base);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float o = f4at(old, e);
+            v[e] = up[e] ? (OMEGA ? o + w * (v[e] - o) : v[e]) : o;
+        }
+    }
+    if (NAT) {
+        // cell i = 2 h + pc of this colour, 2 h + 1 - pc of the other
+        float a[8];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a[2 * e + pc] = v[e];
+            a[2 * e + 1 - pc] = f4at(O, e);
+        }
+        float *dst = xn + base * 2;   // cell 2 h0 of the row (2 H = nx)
+        *reinterpret_cast<float4 *>(dst) = make_float4(a[0], a[1], a[2], a[3]);
+        *reinterpret_cast<float4 *>(dst + 4) = make_float4(a[4], a[5], a[6], a[7]);
+    } else {
+        *reinterpret_cast<float4 *>(xq + base) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// The first pass of a V-cycle on level 0 in split storage, from x = 0:
+// splits the cell-ordered right-hand side f0 into fs (both colours), writes
+// colour 0 as x = f / D (times w) on active cells with open faces and 0
+// elsewhere, and colour 1 as 0 (the values and zeros k_rbgs_first writes).
+template <bool OMEGA>
+__global__ void __launch_bounds__(256)
+    k_rbgs_first_split(SplitLv<float> L, const float *__restrict__ f0, const uint8_t *__restrict__ m0,
+                       float *__restrict__ fs0, float *__restrict__ fs1, float *__restrict__ xs0,
+                       float *__restrict__ xs1, float w) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= L.nq) return;
+    int64_t base;
+    int h0, j, k;
+    split_quad_pos(L, q, base, h0, j, k);
+    const int pc = (j + k) & 1;   // colour 0's offset in this row
+    const float *src = f0 + base * 2;   // cells 2 h0 .. 2 h0 + 7 of the row (2 base = row nx + 2 h0)
+    const float4 a = ld4(src), b = ld4(src + 4);
+    const float n8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    float c0[4], c1[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        c0[e] = n8[2 * e + pc];
+        c1[e] = n8[2 * e + 1 - pc];
+    }
+    *reinterpret_cast<float4 *>(fs0 + base) = make_float4(c0[0], c0[1], c0[2], c0[3]);
+    *reinterpret_cast<float4 *>(fs1 + base) = make_float4(c1[0], c1[1], c1[2], c1[3]);
+    const uchar4 m4 = *reinterpret_cast<const uchar4 *>(m0 + base);
+    const float4 wx4 = ld4((pc ? L.swx1 : L.swx0) + h0);
+    const float4 rm4 = ld4((pc ? L.srm1 : L.srm0) + h0);
+    const float4 rp4 = ld4((pc ? L.srp1 : L.srp0) + h0);
+    const float wyj = L.wy[j], wzk = L.wz[k], ry0 = L.rhy[j], ry1 = L.rhy[j + 1], rz0 = L.rhz[k], rz1 = L.rhz[k + 1];
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
+        v[e] = 0.f;
+        if (msk & 0x80u) {
+            // fine_diag's sum, in its order
+            const float wxe = f4at(wx4, e);
+            const float ayz = wyj * wzk, axz = wxe * wzk, axy = wxe * wyj;
+            float d = 0.f;
+            if (msk & 1u) d += ayz * f4at(rm4, e);
+            if (msk & 2u) d += ayz * f4at(rp4, e);
+            if (msk & 4u) d += axz * ry0;
+            if (msk & 8u) d += axz * ry1;
+            if (msk & 16u) d += axy * rz0;
+            if (msk & 32u) d += axy * rz1;
+            if (d > 0.f) v[e] = OMEGA ? w * fast_div(c0[e], d) : fast_div(c0[e], d);
+        }
+    }
+    *reinterpret_cast<float4 *>(xs0 + base) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(xs1 + base) = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// cell-ordered x from the two split colours (a V-cycle without post-smoothing)
+__global__ void k_split_merge(SplitLv<float> L, const float *__restrict__ xs0, const float *__restrict__ xs1,
+                              float *__restrict__ xn) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= L.nq) return;
+    int64_t base;
+    int h0, j, k;
+    split_quad_pos(L, q, base, h0, j, k);
+    const int pc = (j + k) & 1;
+    const float4 a = ld4(xs0 + base), b = ld4(xs1 + base);
+    float o[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        o[2 * e + pc] = f4at(a, e);
+        o[2 * e + 1 - pc] = f4at(b, e);
+    }
+    float *dst = xn + base * 2;
+    *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+}
+
+// per-colour copies of the level-0 open-face mask
+__global__ void k_split_mask(SplitLv<float> L, const uint8_t *__restrict__ m, uint8_t *__restrict__ m0,
+                             uint8_t *__restrict__ m1) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= L.nq) return;
+    int64_t base;
+    int h0, j, k;
+    split_quad_pos(L, q, base, h0, j, k);
+    const int pc = (j + k) & 1;
+    const uint8_t *src = m + base * 2;
+    uint8_t a[4], b[4];
+    for (int e = 0; e < 4; ++e) {
+        a[e] = src[2 * e + pc];
+        b[e] = src[2 * e + 1 - pc];
+    }
+    *reinterpret_cast<uchar4 *>(m0 + base) = make_uchar4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<uchar4 *>(m1 + base) = make_uchar4(b[0], b[1], b[2], b[3]);
+}
+
 // coarse f_C = sum over children of (f - K x); coarse x_C = 0
 template <typename T, bool FINE>
 __global__ void k_resid_restrict(MGLevel<T> L, const T *__restrict__ f, const T *__restrict__ x, MGLevel<T> C,
@@ -1060,6 +1317,93 @@ __global__ void k_prolong_yz(MGLevel<T> L, T *__restrict__ x, const T *__restric
         acc += wc[q3] * a2;
     }
     x[c] = xc + acc * p;
+}
+
+// k_resid_rx on level 0 in colour-split storage (x and f split; the mask and
+// pn cell-ordered): the same cells, values and order of evaluation
+__global__ void __launch_bounds__(RX_THREADS)
+    k_resid_rx_split(MGLevel<float> L, const float *__restrict__ fs0, const float *__restrict__ fs1,
+                     const float *__restrict__ xs0, const float *__restrict__ xs1, const float *__restrict__ pn,
+                     Xfer<float> X, int cnx, int fx, int zcol, float *__restrict__ tA) {
+    __shared__ float sg[2 * RX_THREADS + 2];
+    const int64_t row = blockIdx.x;
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
+    const int H = L.nx / 2;
+    const int64_t prow = row * H, sy = H, sz = (int64_t)H * L.ny;
+    const int I0 = blockIdx.y * RX_THREADS;
+    const int lo = fx == 2 ? 2 * I0 - 1 : I0;
+    const int cnt = fx == 2 ? 2 * RX_THREADS + 2 : RX_THREADS;
+    for (int t = threadIdx.x; t < cnt; t += RX_THREADS) {
+        const int i = lo + t;
+        float r = 0.f;
+        if (i >= 0 && i < L.nx) {
+            const int64_t c = row * L.nx + i;
+            const unsigned msk = L.omask[c];
+            const int col = (i + j + k) & 1;
+            const bool relaxed = col == zcol && (msk & 0x3fu) != 0;
+            const float p = pn[c];
+            if (!relaxed && p > 0.f) {
+                const float *xo = col ? xs0 : xs1;
+                const int64_t pb = prow + (i >> 1);
+                const float ayz = L.wy[j] * L.wz[k], axz = L.wx[i] * L.wz[k], axy = L.wx[i] * L.wy[j];
+                float d = 0.f, s = (col ? fs1 : fs0)[pb], tt;
+                if (msk & 1u) { tt = ayz * L.rhx[i]; d += tt; s += tt * xo[prow + ((i - 1) >> 1)]; }
+                if (msk & 2u) { tt = ayz * L.rhx[i + 1]; d += tt; s += tt * xo[prow + ((i + 1) >> 1)]; }
+                if (msk & 4u) { tt = axz * L.rhy[j]; d += tt; s += tt * xo[pb - sy]; }
+                if (msk & 8u) { tt = axz * L.rhy[j + 1]; d += tt; s += tt * xo[pb + sy]; }
+                if (msk & 16u) { tt = axy * L.rhz[k]; d += tt; s += tt * xo[pb - sz]; }
+                if (msk & 32u) { tt = axy * L.rhz[k + 1]; d += tt; s += tt * xo[pb + sz]; }
+                r = p * (s - d * (col ? xs1 : xs0)[pb]);
+            }
+        }
+        sg[t] = r;
+    }
+    __syncthreads();
+    const int I = I0 + threadIdx.x;
+    if (I < cnx) {
+        float acc = 0.f;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = X.Gx[4 * I + s];
+            if (i >= 0 && (unsigned)(i - lo) < (unsigned)cnt) acc += X.gwx[4 * I + s] * sg[i - lo];
+        }
+        tA[row * cnx + I] = acc;
+    }
+}
+
+// k_prolong_yz on level 0 in colour-split storage (x split, pn and tB
+// cell-ordered)
+__global__ void k_prolong_yz_split(MGLevel<float> L, float *__restrict__ xs0, float *__restrict__ xs1,
+                                   const float *__restrict__ tB, int cny, Xfer<float> X, const float *__restrict__ pn) {
+    const int64_t row = blockIdx.x;
+    int j, k;
+    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= L.nx) return;
+    const int64_t c = row * L.nx + i;
+    float *x = ((i + j + k) & 1) ? xs1 : xs0;
+    const int64_t pb = row * (L.nx / 2) + (i >> 1);
+    int ib[2], ic[2];
+    float wb[2], wc[2];
+    const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
+    const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
+    float tv[2][2];
+#pragma unroll
+    for (int q3 = 0; q3 < 2; ++q3)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+            tv[q3][q2] = tB[((int64_t)ic[q3 < nc ? q3 : 0] * cny + ib[q2 < nb ? q2 : 0]) * L.nx + i];
+    const float p = pn[c];
+    const float xc = x[pb];
+    if (!pos(p)) return;
+    float acc = 0.f;
+    for (int q3 = 0; q3 < nc; ++q3) {
+        float a2 = 0.f;
+        for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * tv[q3][q2];
+        acc += wc[q3] * a2;
+    }
+    x[pb] = xc + acc * p;
 }
 
 // coarsest level: red-black sweeps in one block, all data in shared memory.
@@ -1490,6 +1834,27 @@ static ibm_status build_hier(Ctx *c, MGHier<T> &H, bool fine0) {
         M.type = c->type;
         M.wx = H.wx; M.wy = H.wy; M.wz = H.wz;
         M.rhx = H.rhx; M.rhy = H.rhy; M.rhz = H.rhz;
+        // colour-split storage of level 0 (FP32, rows of whole 16-byte quads)
+        if (sizeof(T) == 4 && c->nx % 8 == 0 && L > 1) {
+            const size_t hn = (size_t)c->N / 2;
+            for (int q = 0; q < 2; ++q) {
+                H.xs[q] = (T *)dev_alloc(c, sizeof(T) * hn);
+                H.fs[q] = (T *)dev_alloc(c, sizeof(T) * hn);
+                H.ms[q] = (uint8_t *)dev_alloc(c, hn);
+                if (!H.xs[q] || !H.fs[q] || !H.ms[q]) return c->fail(IBM_ERR_OOM, "split level allocation failed");
+                std::vector<double> wx(c->nx / 2), rm(c->nx / 2), rp(c->nx / 2);
+                for (int h = 0; h < c->nx / 2; ++h) {
+                    wx[h] = c->hdx[2 * h + q];
+                    rm[h] = c->hhx[2 * h + q];
+                    rp[h] = c->hhx[2 * h + q + 1];
+                }
+                H.swx[q] = upload_as<T>(c, wx, false);
+                H.srm[q] = upload_as<T>(c, rm, true);
+                H.srp[q] = upload_as<T>(c, rp, true);
+                if (!H.swx[q] || !H.srm[q] || !H.srp[q]) return c->fail(IBM_ERR_OOM, "split metric allocation failed");
+            }
+            H.split = true;
+        }
     }
     H.res.assign(L, nullptr);
     H.pn.assign(L, nullptr);
@@ -1523,6 +1888,13 @@ static ibm_status fill_hier(Ctx *c, MGHier<T> &H, const std::vector<double *> &o
             KL(-1, k_open_mask, nblk(c->N), 256, c->g, c->type, H.omask);
             IBM_LAUNCHED(c);
             M.omask = H.omask;
+            if constexpr (sizeof(T) == 4) {
+                if (H.split) {
+                    const SplitLv<float> S = split_of(H);
+                    KL(-1, k_split_mask, (unsigned)((S.nq + 255) / 256), 256, S, H.omask, H.ms[0], H.ms[1]);
+                    IBM_LAUNCHED(c);
+                }
+            }
             continue;
         }
         KL(-1, k_level_coef<T>, nblk(M.n), 256, M.nx, M.ny, M.nz, ox[l], oy[l], oz[l], c->lhx[l], c->lhy[l],
@@ -1642,6 +2014,41 @@ static ibm_status rbgs(Ctx *c, MGHier<T> &H, int l, const T *f, T *x, int col, i
     return IBM_OK;
 }
 
+// level 0 of the FP32 hierarchy in colour-split storage for this cycle
+template <typename T>
+static bool split_on(const Ctx *c, const MGHier<T> &H) {
+    return sizeof(T) == 4 && H.split && c->opts.fine_split == 1 && c->opts.mg_interp == 1 && H.lv.size() > 1;
+}
+
+// split-storage passes of level 0: kind 0 a colour pass, 1 the first pass
+// from x = 0 (also splitting f0), 2 the last colour-0 pass writing the
+// cell-ordered output x0, 3 the merge of both colours into x0
+static ibm_status split_pass(Ctx *c, MGHier<float> &H, int kind, int col, const float *f0, float *x0) {
+    const SplitLv<float> S = split_of(H);
+    const unsigned nb = (unsigned)((S.nq + 255) / 256);
+    const double w = c->opts.smooth_omega;
+    const bool om = w != 1.0;
+    if (kind == 1) {
+        if (om) KL(-1, k_rbgs_first_split<true>, nb, 256, S, f0, H.ms[0], H.fs[0], H.fs[1], H.xs[0], H.xs[1], (float)w);
+        else KL(-1, k_rbgs_first_split<false>, nb, 256, S, f0, H.ms[0], H.fs[0], H.fs[1], H.xs[0], H.xs[1], 1.f);
+    } else if (kind == 3) {
+        KL(-1, k_split_merge, nb, 256, S, H.xs[0], H.xs[1], x0);
+    } else {
+        const float *fq = H.fs[col], *xo = H.xs[1 - col];
+        const uint8_t *mq = H.ms[col];
+        float *xq = H.xs[col];
+        if (kind == 2) {
+            if (om) KL(K_RBGS0, (k_rbgs_split<true, true>), nb, 256, S, fq, mq, xo, xq, col, (float)w, x0);
+            else KL(K_RBGS0, (k_rbgs_split<false, true>), nb, 256, S, fq, mq, xo, xq, col, 1.f, x0);
+        } else {
+            if (om) KL(K_RBGS0, (k_rbgs_split<true, false>), nb, 256, S, fq, mq, xo, xq, col, (float)w, nullptr);
+            else KL(K_RBGS0, (k_rbgs_split<false, false>), nb, 256, S, fq, mq, xo, xq, col, 1.f, nullptr);
+        }
+    }
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
 template <typename T>
 static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     const int L = (int)H.lv.size();
@@ -1655,12 +2062,24 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     // x0 starts at zero: the first colour pass writes it whole (the coarse
     // levels' x is cleared by the restriction)
     if (nu1 < 1) IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
+    const bool sp = split_on(c, H);
     for (int l = 0; l < L - 1; ++l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
-        for (int s = 0; s < nu1; ++s) {
-            IBM_TRY(rbgs(c, H, l, f, x, 0, s == 0 ? (l == 0 ? 2 : 1) : 0));
-            IBM_TRY(rbgs(c, H, l, f, x, 1));
+        if constexpr (sizeof(T) == 4) {
+            if (l == 0 && sp) {
+                for (int s = 0; s < nu1; ++s) {
+                    if (s == 0) IBM_TRY(split_pass(c, H, 1, 0, f0, x0));
+                    else IBM_TRY(split_pass(c, H, 0, 0, f0, x0));
+                    IBM_TRY(split_pass(c, H, 0, 1, f0, x0));
+                }
+            }
+        }
+        if (!(l == 0 && sp)) {
+            for (int s = 0; s < nu1; ++s) {
+                IBM_TRY(rbgs(c, H, l, f, x, 0, s == 0 ? (l == 0 ? 2 : 1) : 0));
+                IBM_TRY(rbgs(c, H, l, f, x, 1));
+            }
         }
         MGLevel<T> &Lf = H.lv[l];
         MGLevel<T> &Cl = H.lv[l + 1];
@@ -1673,7 +2092,16 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             const Xfer<T> X = xfer_of<T>(c, l + 1);
             const dim3 rgrid((unsigned)((int64_t)Lf.ny * Lf.nz), (unsigned)((Cl.nx + RX_THREADS - 1) / RX_THREADS));
             const int zcol = nu1 > 0 ? 1 : -1;   // each pre-smoothing sweep ends with colour 1
-            if (l == 0 && H.fine0)
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                if (l == 0 && sp) {
+                    KL(K_RESTRICT, k_resid_rx_split, rgrid, RX_THREADS, Lf, H.fs[0], H.fs[1], H.xs[0], H.xs[1],
+                       H.pn[l], X, Cl.nx, CG.fx, zcol, tA);
+                    done = true;
+                }
+            }
+            if (done) {
+            } else if (l == 0 && H.fine0)
                 KL(K_RESTRICT, (k_resid_rx<T, true>), rgrid, RX_THREADS, Lf, f, x, H.pn[l], X, Cl.nx, CG.fx, zcol, tA);
             else
                 KL(K_RESTRICT, (k_resid_rx<T, false>), rgrid, RX_THREADS, Lf, f, x, H.pn[l], X, Cl.nx, CG.fx, zcol,
@@ -1699,13 +2127,31 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             T *tB = l == 0 ? H.pq : H.res[l];
             const Xfer<T> X = xfer_of<T>(c, l + 1);
             KL(K_PROLONG, k_prolong_x<T>, rows_grid(Lf.nx, Cl.ny, Cl.nz, 1, bx), bx, Lf.nx, Cl, X, tB);
-            KL(K_PROLONG, k_prolong_yz<T>, grid, bx, Lf, x, tB, Cl.ny, X, H.pn[l]);
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                if (l == 0 && sp) {
+                    KL(K_PROLONG, k_prolong_yz_split, grid, bx, Lf, H.xs[0], H.xs[1], tB, Cl.ny, X, H.pn[l]);
+                    done = true;
+                }
+            }
+            if (!done) KL(K_PROLONG, k_prolong_yz<T>, grid, bx, Lf, x, tB, Cl.ny, X, H.pn[l]);
         } else if (l == 0 && H.fine0) {
             KL(K_PROLONG, (k_prolong<T, true>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
         } else {
             KL(K_PROLONG, (k_prolong<T, false>), grid, bx, Lf, x, H.lv[l + 1], CG.fx, CG.fy, CG.fz);
         }
         IBM_LAUNCHED(c);
+        if constexpr (sizeof(T) == 4) {
+            if (l == 0 && sp) {
+                // the last colour-0 pass writes the cell-ordered output x0
+                for (int s = 0; s < nu2; ++s) {
+                    IBM_TRY(split_pass(c, H, 0, 1, f0, x0));
+                    IBM_TRY(split_pass(c, H, s + 1 == nu2 ? 2 : 0, 0, f0, x0));
+                }
+                if (nu2 < 1) IBM_TRY(split_pass(c, H, 3, 0, f0, x0));
+                continue;
+            }
+        }
         for (int s = 0; s < nu2; ++s) {
             IBM_TRY(rbgs(c, H, l, f, x, 1));
             IBM_TRY(rbgs(c, H, l, f, x, 0));
@@ -1722,7 +2168,8 @@ template <typename T>
 static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H, T *out) {
     const ibm_solver_opts &o = c->opts;
     const uint64_t key = ((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
-                           (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 2 + (uint64_t)o.mg_interp + 1;
+                           (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 4 + (uint64_t)o.mg_interp * 2 +
+                         (uint64_t)o.fine_split + 1;
     auto drop_all = [&]() -> ibm_status {
         IBM_CUDA(c, cudaStreamSynchronize(c->s));
         for (int i = 0; i < MGHier<T>::NVG; ++i) {
