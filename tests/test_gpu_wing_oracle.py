@@ -37,14 +37,15 @@ def _oracle(size, nsteps):
     return _ORACLE[key]
 
 
-def _errors(size, nsteps, precision):
+def _errors(size, nsteps, precision, rtol=1e-13):
     case, g, T, st = _oracle(size, nsteps)
     s = ibm.Solver(case, precision=precision)
-    s.set_opts(**TIGHT, precision=precision)
+    opts = dict(TIGHT, rtol=rtol) if rtol != 1e-13 else TIGHT
+    s.set_opts(**opts, precision=precision)
     s.set_body(case.verts, case.elems)
     s.classify()
     r = s.step(nsteps)
-    assert r["status"] == ibm.IBM_OK and r["rel_residual"] <= 1e-13, r
+    assert r["status"] == ibm.IBM_OK and r["rel_residual"] <= rtol, r
     err = {}
     for q, n in enumerate(("u", "v", "w")):
         err[n] = float(np.abs(s.get(n) - st.u[q]).max() / max(1.0, np.abs(st.u[q]).max()))
@@ -71,3 +72,15 @@ def test_wing_25m_matches_iterative_oracle(precision):
     err = _errors((384, 256, 256), 2, precision)
     print("wing 384x256x256 vs FP64 oracle:", "mixed" if precision else "fp64", err)
     _check(err)
+
+
+@pytest.mark.slow
+def test_wing_25m_mixed_at_benchmark_tolerance():
+    """The mixed-precision path at the benchmark's 1e-10 residual against the
+    FP64 oracle (solved to 1e-13): the error the 201M-cell mixed
+    configuration carries, measured on its 1/8-size grid."""
+    err = _errors((384, 256, 256), 2, ibm.IBM_MIXED, rtol=1e-10)
+    print("wing 384x256x256 mixed at rtol 1e-10 vs FP64 oracle:", err)
+    for n in ("u", "v", "w"):
+        assert err[n] < 1e-6, err
+    assert err["p"] < 1e-5, err
