@@ -668,6 +668,13 @@ __global__ void k_bicg_xr(int64_t n, double *__restrict__ x, const double *__res
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
+// over-relaxed update o + w (q - o), rounded in a fixed way (no contraction
+// left to the compiler, so every kernel that relaxes a cell gives its bits)
+__device__ __forceinline__ float relax(float o, float q, float w) { return __fmaf_rn(w, __fsub_rn(q, o), o); }
+__device__ __forceinline__ double relax(double o, double q, double w) { return __fma_rn(w, __dsub_rn(q, o), o); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
 // v > 0 for the non-negative tables pn and dinv: an integer test of the bit
 // pattern for FP64 (an FP64 compare occupies GB300's slow FP64 pipe; -0 and
 // +0 both read as not positive)
@@ -754,10 +761,10 @@ __global__ void __launch_bounds__(512, 4)
         // the correctly rounded division's sequence, in an issue-bound pass)
         if (d > T(0)) {
             const T q = fast_div(s, d);
-            x[c] = OMEGA ? x[c] + w * (q - x[c]) : q;
+            x[c] = OMEGA ? relax(x[c], q, w) : q;
         }
     } else {
-        x[c] = OMEGA ? x[c] + w * (s * L.dinv[c] - x[c]) : s * L.dinv[c];
+        x[c] = OMEGA ? relax(x[c], s * L.dinv[c], w) : s * L.dinv[c];
     }
 }
 
@@ -802,7 +809,7 @@ __global__ void __launch_bounds__(512, 4)
         if (msk & 0x80u) {
             const T d = fine_diag<T>(L, msk, ic, j, k);
             if (d > T(0)) {
-                v = OMEGA ? w * fast_div(f[c], d) : fast_div(f[c], d);
+                v = OMEGA ? rmul(w, fast_div(f[c], d)) : fast_div(f[c], d);
                 wr = true;
             }
         }
@@ -957,7 +964,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float o = f4at(old, e);
-            v[e] = up[e] ? (OMEGA ? o + w * (v[e] - o) : v[e]) : o;
+            v[e] = up[e] ? (OMEGA ? relax(o, v[e], w) : v[e]) : o;
         }
     }
     if (NAT) {
@@ -1023,7 +1030,7 @@ __global__ void __launch_bounds__(256)
             if (msk & 8u) d += axz * ry1;
             if (msk & 16u) d += axy * rz0;
             if (msk & 32u) d += axy * rz1;
-            if (d > 0.f) v[e] = OMEGA ? w * fast_div(c0[e], d) : fast_div(c0[e], d);
+            if (d > 0.f) v[e] = OMEGA ? rmul(w, fast_div(c0[e], d)) : fast_div(c0[e], d);
         }
     }
     *reinterpret_cast<float4 *>(xs0 + base) = make_float4(v[0], v[1], v[2], v[3]);
