@@ -598,7 +598,14 @@ def solve_helmholtz_iter(H, rhs, x0=None, rtol=1e-14, maxit=500):
 # Ghost refresh and state
 # ---------------------------------------------------------------------------
 
-def refresh_velocity_ghosts(g: Grid, typ, tabs, u, u_bi=0.0):
+def ghost_bc_values(tabs, comp):
+    """Body velocity component at every ghost's body intercept: the body is
+    at rest unless a motion put "ubi" (ng x 3) into the tables."""
+    ubi = tabs.get("ubi")
+    return np.zeros(tabs["gidx"].size) if ubi is None else ubi[:, comp]
+
+
+def refresh_velocity_ghosts(g: Grid, typ, tabs, u):
     """Solve the Dirichlet ghost rows for the ghost values with the FLUID
     values fixed: u_G + sum_m wv_m u_m = (2 - bv) u_BI."""
     gi = tabs["gidx"]
@@ -607,11 +614,11 @@ def refresh_velocity_ghosts(g: Grid, typ, tabs, u, u_bi=0.0):
     pos = -np.ones(g.N, dtype=np.int64)
     pos[gi] = np.arange(gi.size)
     out = []
-    for c in u:
+    for comp, c in enumerate(u):
         flat = c.ravel().copy()
         sidx, wv = tabs["sidx"], tabs["wv"]
         isg = pos[sidx] >= 0
-        rhs = (2.0 - tabs["bv"]) * u_bi - np.sum(np.where(isg, 0.0, wv * flat[sidx]), axis=1)
+        rhs = (2.0 - tabs["bv"]) * ghost_bc_values(tabs, comp) - np.sum(np.where(isg, 0.0, wv * flat[sidx]), axis=1)
         r, cc = np.nonzero(isg & (wv != 0.0))
         G = sp.csr_matrix((wv[r, cc], (r, pos[sidx[r, cc]])), shape=(gi.size, gi.size)) + sp.identity(gi.size)
         flat[gi] = spla.spsolve(G.tocsc(), rhs)
@@ -667,6 +674,17 @@ def body_force(g: Grid, typ, tabs, u, p, Re):
     return F
 
 
+def body_velocity(motion, pts):
+    """Rigid body velocity U + Omega x (x - centre) at points pts (n x 3);
+    motion = (U, Omega, centre), each three numbers."""
+    U, w, c0 = (np.asarray(m, dtype=np.float64) for m in motion)
+    r = np.asarray(pts, dtype=np.float64) - c0
+    cr = np.stack([w[1] * r[:, 2] - w[2] * r[:, 1],
+                   w[2] * r[:, 0] - w[0] * r[:, 2],
+                   w[0] * r[:, 1] - w[1] * r[:, 0]], axis=1)
+    return U + cr
+
+
 @dataclass
 class State:
     u: list           # ncomp cell arrays
@@ -674,6 +692,63 @@ class State:
     p: np.ndarray
     Nold: list | None
     nstep: int = 0
+    fresh: np.ndarray | None = None   # cells that became FLUID at the last body move
+
+
+def interior_face_rule(g: Grid, typ, u, a):
+    """Interior face velocities of axis a by the predictor's face rule: the
+    mean of the two neighbours on faces with a FLUID side and no DEAD side,
+    0 elsewhere (the outer faces are left out)."""
+    L, R = typ[_sl(a, 0, -1)], typ[_sl(a, 1, None)]
+    ok = (L != DEAD) & (R != DEAD) & ((L == FLUID) | (R == FLUID))
+    return np.where(ok, 0.5 * (u[a][_sl(a, 0, -1)] + u[a][_sl(a, 1, None)]), 0.0)
+
+
+def move_state(g: Grid, typ_old, tabs, st, verts, elems, motion):
+    """The state after the body moved to `verts` (same elements) with the
+    rigid motion `motion` (Section 2.2, moving bodies; the paper moves the
+    body at the start of each step). `tabs` are the tables of the new
+    position; this function adds tabs["ubi"], the body velocity at every
+    ghost's body intercept. Then:
+      * fresh cells (FLUID now, not FLUID before) take the value of the
+        fresh-cell interpolation (geom.fresh_tables) with the body velocity
+        at their own body intercept; fresh corners are implicit unknowns,
+        so the fresh values solve one sparse system;
+      * DEAD cells are 0, and the ghost rows are solved with the body
+        velocity at their intercepts;
+      * interior faces next to a cell whose type changed take the face rule
+        from the new cell values; the other faces keep their values.
+    Returns the new State with its fresh mask (the next step takes the
+    Euler start at those cells)."""
+    from . import geom
+    typ = tabs["type"]
+    tabs["ubi"] = body_velocity(motion, tabs["bi"]) if tabs["gidx"].size else np.zeros((0, 3))
+    fresh = (typ == FLUID) & (typ_old != FLUID)
+    fidx = np.nonzero(fresh.ravel())[0]
+    ft = geom.fresh_tables(g.ndim, g.xf, g.yf, g.zf, typ, fidx, verts, elems)
+    ubf = body_velocity(motion, ft["bi"]) if fidx.size else np.zeros((0, 3))
+    u = [np.where(typ == DEAD, 0.0, c) for c in st.u]
+    if fidx.size:
+        pos = -np.ones(g.N, dtype=np.int64)
+        pos[fidx] = np.arange(fidx.size)
+        sidx, w = ft["sidx"], ft["w"]
+        isf = pos[sidx] >= 0
+        r, cc = np.nonzero(isf & (w != 0.0))
+        M = sp.identity(fidx.size) - sp.csr_matrix((w[r, cc], (r, pos[sidx[r, cc]])), shape=(fidx.size,) * 2)
+        lu = spla.splu(M.tocsc())
+        for comp in range(g.ncomp):
+            flat = u[comp].ravel().copy()
+            rhs = np.sum(np.where(isf, 0.0, w * flat[sidx]), axis=1) + ft["wb"] * ubf[:, comp]
+            flat[fidx] = lu.solve(rhs)
+            u[comp] = flat.reshape(g.shape)
+    u = refresh_velocity_ghosts(g, typ, tabs, u)
+    changed = typ != typ_old
+    F = [f.copy() for f in st.F]
+    for a in axes(g):
+        ch = changed[_sl(a, 0, -1)] | changed[_sl(a, 1, None)]
+        inner = F[a][_sl(a, 1, -1)]
+        F[a][_sl(a, 1, -1)] = np.where(ch, interior_face_rule(g, typ, u, a), inner)
+    return State(u, F, st.p, st.Nold, st.nstep, fresh), ft
 
 
 def initial_state(g: Grid, typ, tabs, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 0.0)):
@@ -696,6 +771,9 @@ def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 
     alpha_e = (1.0 - CN_THETA) * dt / Re    # explicit viscous share
     N = convection(g, typ, st.u, st.F, bc, u_inf)
     Nold = N if st.Nold is None else st.Nold
+    if st.fresh is not None:
+        # a fresh cell has no convective history: Euler start there
+        Nold = [np.where(st.fresh, N[c], Nold[c]) for c in range(g.ncomp)]
     ustar = []
     rhs_all = []
     for c in range(g.ncomp):
@@ -703,6 +781,11 @@ def step(g: Grid, typ, tabs, st: State, Re, dt, bc=DEFAULT_BC, u_inf=(1.0, 0.0, 
         rhs = (st.u[c] - dt * (AB2[0] * N[c] + AB2[1] * Nold[c]) + alpha_e * Lu
                + alpha * bc_source(g, typ, c, bc, u_inf))
         rhs = np.where(typ == FLUID, rhs, 0.0)
+        if tabs["gidx"].size:
+            # Dirichlet ghost rows: u_G + sum wv u_m = (2 - bv) u_BI
+            rf = rhs.ravel()
+            rf[tabs["gidx"]] = (2.0 - tabs["bv"]) * ghost_bc_values(tabs, c)
+            rhs = rf.reshape(g.shape)
         if solver == "iter":
             H = None if cache is None else cache.get(("helmH", c, alpha))
             if H is None:

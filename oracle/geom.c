@@ -443,3 +443,107 @@ void orc_ghost_tables(int ndim, int nx, int ny, int nz,
         }
     }
 }
+
+/*
+ * Fresh cells (Section 2.2: cells that were inside a moving body and are
+ * fluid now; their value comes from an interpolation that uses the body
+ * velocity at the body intercept). Reading fixed here: for a fresh cell FC
+ * with body intercept BI (closest surface point) and normal n = (FC - BI) /
+ * |FC - BI| (into the fluid), the trilinear basis is fitted on the lattice
+ * cell of centres that has FC as a corner and extends towards n along each
+ * axis (clamped into the grid); the row of the corner FC itself is the
+ * Dirichlet row b(x_BI), and the fit is evaluated at FC:
+ *     u_FC = sum_{m != FC} w_m u_m + wb u_BI.
+ * Other corners must be FLUID (fresh corners included, as implicit
+ * unknowns); a GHOST or DEAD corner, a near-singular system or an FC on the
+ * surface (|FC - BI| < 1e-9 h) gives kind 2: u_FC = u_BI (w = 0, wb = 1).
+ * Output per fresh cell: bi[3], kind, sidx[8] (the FC itself with weight 0
+ * in unused slots), w[8], wb.
+ */
+void orc_fresh_tables(int ndim, int nx, int ny, int nz,
+                      const double *xc, const double *yc, const double *zc,
+                      const double *dx, const double *dy, const double *dz,
+                      const uint8_t *type, int64_t nf, const int64_t *fidx,
+                      const double *verts, int64_t ne, const int32_t *elems,
+                      double *bi, uint8_t *kind, int64_t *sidx, double *w, double *wb)
+{
+    const int nc = ndim == 2 ? 4 : 8;
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    for (int64_t f = 0; f < nf; ++f) {
+        const int64_t c = fidx[f];
+        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / sz);
+        double p[3] = {xc[i], yc[j], ndim == 2 ? 0.0 : zc[k]};
+        double best = INFINITY, q[3] = {0, 0, 0};
+        for (int64_t e = 0; e < ne; ++e) {
+            double qq[3];
+            if (ndim == 2)
+                closest_on_seg(p, verts + 3 * (int64_t)elems[2 * e], verts + 3 * (int64_t)elems[2 * e + 1], qq);
+            else
+                closest_on_tri(p, verts + 3 * (int64_t)elems[3 * e], verts + 3 * (int64_t)elems[3 * e + 1],
+                               verts + 3 * (int64_t)elems[3 * e + 2], qq);
+            double dv[3] = {qq[0] - p[0], qq[1] - p[1], qq[2] - p[2]};
+            double dd = dot3(dv, dv);
+            if (dd < best) { best = dd; q[0] = qq[0]; q[1] = qq[1]; q[2] = qq[2]; }
+        }
+        for (int a = 0; a < 3; ++a) bi[3 * f + a] = q[a];
+        double dv[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+        double d = sqrt(dot3(dv, dv));
+        double hloc = dx[i] < dy[j] ? dx[i] : dy[j];
+        if (ndim == 3 && dz[k] < hloc) hloc = dz[k];
+        int kd = !(d >= 1e-9 * hloc) ? 2 : 1;
+        double n[3] = {0, 0, 0};
+        if (kd == 1) { n[0] = dv[0] / d; n[1] = dv[1] / d; n[2] = dv[2] / d; }
+        int i0 = n[0] >= 0.0 ? i : i - 1, j0 = n[1] >= 0.0 ? j : j - 1, k0 = 0;
+        if (i0 < 0) i0 = 0;
+        if (i0 > nx - 2) i0 = nx - 2;
+        if (j0 < 0) j0 = 0;
+        if (j0 > ny - 2) j0 = ny - 2;
+        if (ndim == 3) {
+            k0 = n[2] >= 0.0 ? k : k - 1;
+            if (k0 < 0) k0 = 0;
+            if (k0 > nz - 2) k0 = nz - 2;
+        }
+        int64_t cidx[8];
+        int self = -1;
+        for (int m = 0; m < nc; ++m) {
+            int di = m & 1, dj = (m >> 1) & 1, dk = (m >> 2) & 1;
+            cidx[m] = (int64_t)(i0 + di) * sx + (int64_t)(j0 + dj) * sy + (int64_t)(k0 + dk) * sz;
+            if (cidx[m] == c) self = m;
+            else if (type[cidx[m]] != FLUID) kd = 2;
+        }
+        double xw[8];
+        if (kd == 1) {
+            double hx = xc[i0 + 1] - xc[i0], hy = yc[j0 + 1] - yc[j0];
+            double hz = ndim == 3 ? zc[k0 + 1] - zc[k0] : 1.0;
+            double bxi = (q[0] - xc[i0]) / hx, bet = (q[1] - yc[j0]) / hy;
+            double bze = ndim == 3 ? (q[2] - zc[k0]) / hz : 0.0;
+            double bBI[8], bFC[8], M[64], r[8];
+            basis(ndim, bxi, bet, bze, bBI);
+            basis(ndim, (double)(self & 1), (double)((self >> 1) & 1), (double)((self >> 2) & 1), bFC);
+            for (int m = 0; m < nc; ++m) {
+                double row[8];
+                if (m == self) {
+                    for (int t = 0; t < nc; ++t) row[t] = bBI[t];
+                } else {
+                    basis(ndim, (double)(m & 1), (double)((m >> 1) & 1), (double)((m >> 2) & 1), row);
+                }
+                for (int t = 0; t < nc; ++t) M[t * nc + m] = row[t];
+            }
+            for (int t = 0; t < nc; ++t) r[t] = bFC[t];
+            if (lu_solve(nc, M, r, xw)) kd = 2;
+        }
+        kind[f] = (uint8_t)kd;
+        int64_t *SI = sidx + 8 * f;
+        double *W = w + 8 * f;
+        if (kd == 1) {
+            for (int m = 0; m < 8; ++m) {
+                if (m < nc && m != self) { SI[m] = cidx[m]; W[m] = xw[m]; }
+                else { SI[m] = c; W[m] = 0.0; }
+            }
+            wb[f] = xw[self];
+        } else {
+            for (int m = 0; m < 8; ++m) { SI[m] = c; W[m] = 0.0; }
+            wb[f] = 1.0;
+        }
+    }
+}

@@ -48,6 +48,7 @@ def lib():
         L.orc_classify.argtypes = [I, I, I, P, P, P]
         L.orc_classify.restype = I64
         L.orc_ghost_tables.argtypes = [I, I, I, I, P, P, P, P, P, P, P, I64, P, P, I64, P] + [P] * 12
+        L.orc_fresh_tables.argtypes = [I, I, I, I, P, P, P, P, P, P, P, I64, P, P, I64, P] + [P] * 5
         _lib = L
     return _lib
 
@@ -131,6 +132,28 @@ def ghost_tables(ndim, xf, yf, zf, typ, gidx, verts, elems):
                                *[_p(t[k]) for k in ("bi", "nrm", "ip", "dist", "base", "kind", "cmask",
                                                     "sidx", "wv", "wp", "bv", "bp")])
     t["gidx"] = gidx
+    return t
+
+
+def fresh_tables(ndim, xf, yf, zf, typ, fidx, verts, elems):
+    """Per-fresh-cell body intercept, kind, stencil and weights (geom.c,
+    orc_fresh_tables): u_FC = sum_m w_m u_m + wb u_BI."""
+    xf, yf, zf = (np.asarray(a, dtype=np.float64) for a in (xf, yf, zf))
+    nx, ny, nz = len(xf) - 1, len(yf) - 1, len(zf) - 1
+    xc, yc, zc = centres(xf), centres(yf), centres(zf)
+    dx, dy, dz = np.diff(xf), np.diff(yf), np.diff(zf)
+    typ = np.ascontiguousarray(typ, dtype=np.uint8).ravel()
+    fidx = np.ascontiguousarray(fidx, dtype=np.int64)
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    nf = fidx.size
+    t = dict(bi=np.zeros((nf, 3)), kind=np.zeros(nf, np.uint8), sidx=np.zeros((nf, 8), np.int64),
+             w=np.zeros((nf, 8)), wb=np.zeros(nf))
+    if nf:
+        lib().orc_fresh_tables(ndim, nx, ny, nz, _p(xc), _p(yc), _p(zc), _p(dx), _p(dy), _p(dz),
+                               _p(typ), nf, _p(fidx), _p(verts), elems.shape[0], _p(elems),
+                               *[_p(t[k]) for k in ("bi", "kind", "sidx", "w", "wb")])
+    t["fidx"] = fidx
     return t
 
 
