@@ -252,6 +252,37 @@ ibm_status ibm_set_body(ibm_ctx *ctx, const double *verts, int64_t nv,
    out may be NULL. IBM_ERR_STATE if no body was set. */
 ibm_status ibm_classify_cells(ibm_ctx *ctx, ibm_table_info *out);
 
+/* Move the bodies (Section 2.2, moving bodies: the body moves at the start
+   of a step; dead cells that become fluid, "fresh cells", take an
+   interpolation that uses the body velocity at their body intercept).
+   verts: host, nv x 3 doubles, the new positions of every vertex added by
+   ibm_set_body, in the same order (the elements are kept; copied). motion:
+   host, 9 doubles: the rigid velocity U (3), angular velocity Omega (3) and
+   rotation centre (3); the body velocity at a surface point x is
+   U + Omega x (x - centre). In 2D the vertices keep z = 0 and U_z, Omega_x,
+   Omega_y are 0. The call reclassifies the cells and rebuilds the ghost
+   tables and multigrid operators of the new position, keeps the flow state,
+   and then:
+     - fresh cells (FLUID now, not before): u = sum w_m u_m + wb u_BI from the
+       trilinear fit on the lattice cell of centres that has the fresh cell as
+       a corner and extends away from the body, the fresh cell's row replaced
+       by the Dirichlet row at its intercept; other fresh corners are solved
+       with it (Jacobi passes to ghost_tol); a ghost or dead corner gives
+       u = u_BI; the next step takes the Euler start of the convective term
+       at these cells;
+     - DEAD cells get u = 0; ghost rows use u_BI = the body velocity at their
+       intercept, in this call and in the steps after it (until the next
+       ibm_classify_cells, which puts the body at rest);
+     - interior face velocities next to a cell whose type changed take the
+       face rule (mean of the two cells with a FLUID side and no DEAD side,
+       else 0); the other faces keep theirs.
+   The pressure closure stays dp/dn = 0. Steps after a move are host-driven
+   (opts graph 2 falls back). out may be NULL. IBM_ERR_STATE before
+   ibm_classify_cells; IBM_ERR_ARG for another vertex count, non-finite
+   input, or 2D input off the plane. */
+ibm_status ibm_move_body(ibm_ctx *ctx, const double *verts, int64_t nv, const double *motion,
+                         ibm_table_info *out);
+
 /* Advance nsteps fractional steps (Section 2.1): convective term, AB2 + CN
    right-hand side, CN Helmholtz solve with Dirichlet ghost rows, face
    velocities and divergence, pressure Poisson solve (BiCGStab or FGMRES in

@@ -604,9 +604,9 @@ extern "C" ibm_status ibm_set_body(ibm_ctx *c, const double *verts, int64_t nv, 
     return IBM_OK;
 }
 
-extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
-    if (!c) return IBM_ERR_ARG;
-    if (c->ne == 0) return c->fail(IBM_ERR_STATE, "ibm_set_body must be called before ibm_classify_cells");
+// classification, ghost tables, FLUID volume and multigrid operators of the
+// current body position
+static ibm_status geometry_update(ibm_ctx *c) {
     IBM_TRY(geom_classify(c));
     c->wp32_n = -1;  // FP32 copies of the ghost weights are stale
     c->hinv_ok = false;
@@ -621,9 +621,63 @@ extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
         IBM_TRY(s);
     }
     c->fluid_vol = vol;
-    IBM_TRY(mg_build(c));
+    return mg_build(c);
+}
+
+extern "C" ibm_status ibm_classify_cells(ibm_ctx *c, ibm_table_info *out) {
+    if (!c) return IBM_ERR_ARG;
+    if (c->ne == 0) return c->fail(IBM_ERR_STATE, "ibm_set_body must be called before ibm_classify_cells");
+    c->moving = false;
+    c->fresh_pending = false;
+    IBM_TRY(geometry_update(c));
     IBM_TRY(flow_init(c));
     c->classified = true;
+    if (out) {
+        out->n_fluid = c->n_fluid;
+        out->n_ghost = c->ng;
+        out->n_dead = c->n_dead;
+        for (int q = 0; q < 3; ++q) out->n_kind[q] = c->n_kind[q];
+    }
+    return IBM_OK;
+}
+
+extern "C" ibm_status ibm_move_body(ibm_ctx *c, const double *verts, int64_t nv, const double *motion,
+                                    ibm_table_info *out) {
+    if (!c) return IBM_ERR_ARG;
+    if (!verts || !motion) return c->fail(IBM_ERR_ARG, "verts and motion must not be NULL");
+    if (!c->classified) return c->fail(IBM_ERR_STATE, "ibm_classify_cells must be called before ibm_move_body");
+    if (nv != c->nv) return c->fail(IBM_ERR_ARG, "ibm_move_body needs the vertex count of the bodies set");
+    for (int64_t q = 0; q < 3 * nv; ++q)
+        if (!isfinite(verts[q])) return c->fail(IBM_ERR_ARG, "vertex coordinates must be finite");
+    for (int q = 0; q < 9; ++q)
+        if (!isfinite(motion[q])) return c->fail(IBM_ERR_ARG, "motion must be finite");
+    if (c->ndim == 2) {
+        for (int64_t q = 0; q < nv; ++q)
+            if (verts[3 * q + 2] != 0.0) return c->fail(IBM_ERR_ARG, "2D vertices must have z = 0");
+        if (motion[2] != 0.0 || motion[3] != 0.0 || motion[4] != 0.0)
+            return c->fail(IBM_ERR_ARG, "2D motion: U_z, Omega_x and Omega_y must be 0");
+    }
+    if (!c->type_old) c->type_old = (uint8_t *)dev_alloc(c, (size_t)c->N);
+    if (!c->fresh) {
+        c->fresh = (uint8_t *)dev_alloc(c, (size_t)c->N);
+        if (c->fresh) IBM_CUDA(c, cudaMemsetAsync(c->fresh, 0, (size_t)c->N, c->s));
+    }
+    if (!c->type_old || !c->fresh) return c->fail(IBM_ERR_OOM, "moving-body allocation failed");
+    if (c->fresh_pending) {
+        // flags of a move with no step after it: those cells are FLUID
+        // already, so they are not fresh at this move
+        IBM_CUDA(c, cudaMemsetAsync(c->fresh, 0, (size_t)c->N, c->s));
+        c->fresh_pending = false;
+    }
+    std::copy(verts, verts + 3 * nv, c->verts.begin());
+    IBM_CUDA(c, cudaMemcpyAsync(c->d_verts, c->verts.data(), sizeof(double) * c->verts.size(), cudaMemcpyHostToDevice,
+                                c->s));
+    IBM_CUDA(c, cudaMemcpyAsync(c->type_old, c->type, (size_t)c->N, cudaMemcpyDeviceToDevice, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    IBM_TRY(geometry_update(c));
+    for (int q = 0; q < 9; ++q) c->motion[q] = motion[q];
+    c->moving = true;
+    IBM_TRY(flow_move(c));
     if (out) {
         out->n_fluid = c->n_fluid;
         out->n_ghost = c->ng;

@@ -124,6 +124,17 @@ struct Ctx {
     double *htmp = nullptr;   // second buffer of the Jacobi (SRJ) Helmholtz sweeps
     int64_t nstep = 0;
     bool have_nold = false;
+    // moving body (ibm_move_body): rigid motion (U, Omega, centre), the body
+    // velocity at every ghost's intercept (3 per ghost), the cell types
+    // before the last move and the per-cell flags of the fresh cells it
+    // made, which the next step's convective term reads (Euler start there)
+    bool moving = false;
+    double motion[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double *ubi = nullptr;
+    int64_t ubi_cap = 0;
+    uint8_t *type_old = nullptr, *fresh = nullptr;
+    bool fresh_pending = false;
+    int64_t n_fresh = 0;
 
     // reductions and scalars
     double *part = nullptr;      // partials: RED_BLOCKS * 32
@@ -222,6 +233,13 @@ ibm_status finalize(Ctx *c, const double *part, int nparts, int ncols, double sc
 
 // geom.cu
 ibm_status geom_classify(Ctx *c);
+// body velocity of the rigid motion c->motion at n points (3 per point)
+ibm_status geom_body_velocity(Ctx *c, int64_t n, const double *pts, double *out);
+// fresh-cell tables of the cells in fidx: body intercept, kind, stencil,
+// weights (u = sum w u_m + wb u_BI)
+ibm_status geom_fresh_tables(Ctx *c, int64_t nf, const int64_t *fidx, double *bi, uint8_t *kind, int64_t *sidx,
+                             double *w, double *wb);
+ibm_status compact_flags(Ctx *c, const uint8_t *flags, int64_t **out, int64_t *count);
 
 // flow.cu
 ibm_status flow_init(Ctx *c);
@@ -243,6 +261,8 @@ ibm_status cond_handle(Ctx *c, cudaGraphConditionalHandle *h);
 ibm_status cond_open(Ctx *c, cudaGraphConditionalNodeType type, cudaGraphConditionalHandle h, CondScope *sc);
 ibm_status cond_close(Ctx *c, CondScope *sc);
 ibm_status ghost_refresh_velocity(Ctx *c, int comp, int *iters);
+// the fields after a body move (fresh cells, dead cells, ghost rows, faces)
+ibm_status flow_move(Ctx *c);
 ibm_status div_stat(Ctx *c, double *out);
 
 }  // namespace ibm

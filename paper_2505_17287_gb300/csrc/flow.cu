@@ -68,8 +68,8 @@ __device__ __forceinline__ P pick3(int q, P a, P b, P c) { return q == 0 ? a : (
 // pressure operator's per-axis coefficients; a Dirichlet wall contributes
 // 2 (value - u_c) / width^2.
 __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const double *__restrict__ dg, CFields3 u,
-                           CFields3 F, CFields3 Nold, int first, Fields3 Nnew, Fields3 rhs, BCInfo bc, double dt,
-                           double alpha, int ncomp) {
+                           CFields3 F, CFields3 Nold, int first, const uint8_t *__restrict__ fresh, Fields3 Nnew,
+                           Fields3 rhs, BCInfo bc, double dt, double alpha, int ncomp) {
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
         if (type[c] != FLUID) {
@@ -160,7 +160,8 @@ __global__ void k_conv_rhs(GridDev g, const uint8_t *__restrict__ type, const do
                 }
                 N += fh[a] * uhi - fl[a] * ulo;
             }
-            const double No = first ? N : noq[c];
+            // Euler start on the first step, and at fresh cells (no history)
+            const double No = (first || (fresh && fresh[c])) ? N : noq[c];
             nnq[c] = N;
             rq[c] = (uc - c15 * N + c05 * No) + alpha * ((off - D * uc) + src);
         }
@@ -310,16 +311,17 @@ __global__ void k_helm_resid(GridDev g, HelmCoef h, const uint8_t *__restrict__ 
 }
 
 // Dirichlet ghost rows for up to three components at once:
-// tmp[q*ng + g] = (2 - bv) u_BI - sum_m wv_m u_m, u_BI = 0 (body at rest)
-__global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, double *__restrict__ tmp,
-                                 double *__restrict__ res, int want_res) {
+// tmp[q*ng + g] = (2 - bv) u_BI - sum_m wv_m u_m, with u_BI the body velocity
+// at the intercept (ubi, 3 per ghost; null: body at rest, u_BI = 0)
+__global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, const double *__restrict__ ubi,
+                                 double *__restrict__ tmp, double *__restrict__ res, int want_res) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     __shared__ double sh[32];
     double r2 = 0.0;
     if (q < gh.ng) {
         for (int cq = 0; cq < ncomp; ++cq) {
             const double *uu = u.p[cq];
-            double s = 0.0;
+            double s = ubi ? (2.0 - gh.bv[q]) * ubi[3 * q + cq] : 0.0;
             for (int m = 0; m < 8; ++m) s -= gh.wv[8 * q + m] * uu[gh.sidx[8 * q + m]];
             tmp[cq * gh.ng + q] = s;
             const double d = s - uu[gh.gidx[q]];
@@ -572,6 +574,9 @@ static inline dim3 rb_grid(const Ctx *c) {
     return dim3((unsigned)rows, (unsigned)((xs + 127) / 128), 1);
 }
 
+// body velocity at the ghosts' intercepts (null while the body is at rest)
+static const double *ghost_ubi(const Ctx *c) { return c->moving ? c->ubi : nullptr; }
+
 static ibm_status faces_from(Ctx *c, double *const *ucell) {
     const BCInfo bc = make_bc(c);
     for (int a = 0; a < c->ndim; ++a) {
@@ -605,7 +610,7 @@ static ibm_status ghost_refresh_all(Ctx *c, double *const *ucell, int *passes) {
     const int check_every = 4;
     for (int it = 0; it < c->opts.ghost_maxit; ++it) {
         const int want = ((it + 1) % check_every == 0) || it + 1 == c->opts.ghost_maxit;
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, want);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), c->gtmp, c->part, want);
         ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
         IBM_LAUNCHED(c);
         ++*passes;
@@ -739,7 +744,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
             kt_end(c, K_HELM);
             if (c->ng > 0) {
                 Fields3 T3{{t, t, t}};
-                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, c->gtmp, c->part, 0);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, ghost_ubi(c), c->gtmp, c->part, 0);
                 ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, c->gtmp);
             }
             IBM_LAUNCHED(c);
@@ -755,7 +760,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         double gmax = 0.0;
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
             ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
             IBM_LAUNCHED(c);
         }
@@ -800,7 +805,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
         kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
             IBM_LAUNCHED(c);
         }
@@ -813,7 +818,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
             double gmax = 0.0;
             if (c->ng > 0) {
                 // ghost-row residual: largest change a further Jacobi pass would make
-                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
                 ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
                 IBM_LAUNCHED(c);
             }
@@ -841,7 +846,7 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
     kt_begin(c, K_CONV);
-    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, Nn, R, make_bc(c), dt,
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, c->fresh_pending ? c->fresh : nullptr, Nn, R, make_bc(c), dt,
                                            alpha, nc);
     kt_end(c, K_CONV);
     IBM_LAUNCHED(c);
@@ -889,6 +894,11 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     }
     c->have_nold = true;
     c->nstep += 1;
+    if (c->fresh_pending) {
+        // the fresh cells of the last move took their Euler start
+        IBM_CUDA(c, cudaMemsetAsync(c->fresh, 0, (size_t)c->N, c->s));
+        c->fresh_pending = false;
+    }
     IBM_CUDA(c, cudaEventRecord(c->ev1, c->s));
     IBM_CUDA(c, cudaEventSynchronize(c->ev1));
     if (st) {
@@ -908,6 +918,154 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     }
     if (status == IBM_ERR_NOT_CONVERGED) c->fail(status, "a solve in the step reached its iteration limit");
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// moving body: the fields after a move (Section 2.2)
+// ---------------------------------------------------------------------------
+
+__global__ void k_fresh_flags(int64_t n, const uint8_t *__restrict__ type, const uint8_t *__restrict__ old,
+                              uint8_t *__restrict__ fresh) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        fresh[c] = (type[c] == FLUID && old[c] != FLUID) ? 1 : 0;
+}
+
+// fresh values, one Jacobi pass over the fresh rows (all components):
+// tmp = sum_m w_m u_m + wb u_BI; res: largest change
+__global__ void k_fresh_compute(int64_t nf, const int64_t *__restrict__ fidx, const int64_t *__restrict__ sidx,
+                                const double *__restrict__ w, const double *__restrict__ wb,
+                                const double *__restrict__ ub, Fields3 u, int ncomp, double *__restrict__ tmp,
+                                double *__restrict__ res) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ double sh[32];
+    double r = 0.0;
+    if (f < nf) {
+        for (int cq = 0; cq < ncomp; ++cq) {
+            const double *uu = u.p[cq];
+            double s = wb[f] * ub[3 * f + cq];
+            for (int m = 0; m < 8; ++m) s += w[8 * f + m] * uu[sidx[8 * f + m]];
+            tmp[cq * nf + f] = s;
+            r = fmax(r, fabs(s - uu[fidx[f]]));
+        }
+    }
+    r = warp_max(r);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) res[blockIdx.x] = t;
+    }
+}
+__global__ void k_fresh_scatter(int64_t nf, const int64_t *__restrict__ fidx, Fields3 u, int ncomp,
+                                const double *__restrict__ tmp) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    for (int cq = 0; cq < ncomp; ++cq) u.p[cq][fidx[f]] = tmp[cq * nf + f];
+}
+// start value of the fresh cells: the body velocity at their intercept
+__global__ void k_fresh_start(int64_t nf, const int64_t *__restrict__ fidx, const double *__restrict__ ub, Fields3 u,
+                              int ncomp) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    for (int cq = 0; cq < ncomp; ++cq) u.p[cq][fidx[f]] = ub[3 * f + cq];
+}
+
+__global__ void k_dead_zero(int64_t n, const uint8_t *__restrict__ type, Fields3 u, int ncomp) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        if (type[c] == DEAD)
+            for (int q = 0; q < ncomp; ++q) u.p[q][c] = 0.0;
+}
+
+// interior faces of axis a next to a cell whose type changed: the face rule
+// (mean of the two cells on faces with a FLUID side and no DEAD side, else 0)
+__global__ void k_faces_changed(GridDev g, const uint8_t *__restrict__ type, const uint8_t *__restrict__ old,
+                                const double *__restrict__ ua, int a, double *__restrict__ Fa) {
+    const int nfx = g.nx + (a == 0), nfy = g.ny + (a == 1);
+    const int64_t nf = (int64_t)nfx * nfy * (g.nz + (a == 2));
+    const int64_t st = a == 0 ? 1 : (a == 1 ? g.nx : (int64_t)g.nx * g.ny);
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = f / nfx;
+        const int i = (int)(f - t * nfx), j = (int)(t % nfy), k = (int)(t / nfy);
+        const int ia = a == 0 ? i : (a == 1 ? j : k);
+        const int na = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+        if (ia == 0 || ia == na) continue;   // outer faces keep their values
+        const int64_t cR = (int64_t)i + (int64_t)g.nx * (j + (int64_t)g.ny * k), cL = cR - st;
+        if (type[cL] == old[cL] && type[cR] == old[cR]) continue;
+        const uint8_t L = type[cL], R = type[cR];
+        const bool ok = L != DEAD && R != DEAD && (L == FLUID || R == FLUID);
+        Fa[f] = ok ? 0.5 * (ua[cL] + ua[cR]) : 0.0;
+    }
+}
+
+ibm_status flow_move(Ctx *c) {
+    const int nc = c->ndim;
+    Fields3 U{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
+    // body velocity at the ghosts' intercepts
+    if (c->ng > c->ubi_cap || !c->ubi) {
+        dev_free(c, c->ubi);
+        c->ubi_cap = c->ng > 0 ? c->ng : 1;
+        c->ubi = (double *)dev_alloc(c, sizeof(double) * 3 * c->ubi_cap);
+        if (!c->ubi) return c->fail(IBM_ERR_OOM, "body velocity allocation failed");
+    }
+    IBM_TRY(geom_body_velocity(c, c->ng, c->bi, c->ubi));
+    // fresh cells: FLUID now, not FLUID before the move
+    ++c->nlaunch, k_fresh_flags<<<c->nelem, 256, 0, c->s>>>(c->N, c->type, c->type_old, c->fresh);
+    IBM_LAUNCHED(c);
+    int64_t *fidx = nullptr, nf = 0;
+    IBM_TRY(compact_flags(c, c->fresh, &fidx, &nf));
+    c->n_fresh = nf;
+    if (nf > 0) {
+        double *fbi = (double *)dev_alloc(c, sizeof(double) * 3 * nf);
+        double *fub = (double *)dev_alloc(c, sizeof(double) * 3 * nf);
+        double *fw = (double *)dev_alloc(c, sizeof(double) * 8 * nf);
+        double *fwb = (double *)dev_alloc(c, sizeof(double) * nf);
+        double *ftmp = (double *)dev_alloc(c, sizeof(double) * 3 * nf);
+        int64_t *fs = (int64_t *)dev_alloc(c, sizeof(int64_t) * 8 * nf);
+        uint8_t *fk = (uint8_t *)dev_alloc(c, nf);
+        if (!fbi || !fub || !fw || !fwb || !ftmp || !fs || !fk) return c->fail(IBM_ERR_OOM, "fresh-cell allocation failed");
+        IBM_TRY(geom_fresh_tables(c, nf, fidx, fbi, fk, fs, fw, fwb));
+        IBM_TRY(geom_body_velocity(c, nf, fbi, fub));
+        const unsigned fb = (unsigned)((nf + 255) / 256);
+        ++c->nlaunch, k_fresh_start<<<fb, 256, 0, c->s>>>(nf, fidx, fub, U, nc);
+        IBM_LAUNCHED(c);
+        // fresh corners are implicit unknowns: Jacobi passes to ghost_tol
+        double scale = 1.0;
+        for (int a = 0; a < 3; ++a) scale = fmax(scale, fmax(fabs(c->desc.u_inf[a]), fabs(c->motion[a])));
+        bool done = false;
+        for (int it = 0; it < 4 * c->opts.ghost_maxit && !done; ++it) {
+            ++c->nlaunch, k_fresh_compute<<<fb, 256, 0, c->s>>>(nf, fidx, fs, fw, fwb, fub, U, nc, ftmp, c->part);
+            ++c->nlaunch, k_fresh_scatter<<<fb, 256, 0, c->s>>>(nf, fidx, U, nc, ftmp);
+            IBM_LAUNCHED(c);
+            if ((it + 1) % 4 == 0) {
+                ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)fb, c->scal + 40);
+                IBM_LAUNCHED(c);
+                IBM_TRY(sync_scalars(c, 41));
+                const double d = c->hscal[40];
+                if (!isfinite(d)) return c->fail(IBM_ERR_DIVERGED, "fresh-cell values are not finite");
+                done = d <= c->opts.ghost_tol * scale;
+            }
+        }
+        IBM_CUDA(c, cudaStreamSynchronize(c->s));
+        dev_free(c, fbi);
+        dev_free(c, fub);
+        dev_free(c, fw);
+        dev_free(c, fwb);
+        dev_free(c, ftmp);
+        dev_free(c, fs);
+        dev_free(c, fk);
+    }
+    dev_free(c, fidx);
+    ++c->nlaunch, k_dead_zero<<<c->nelem, 256, 0, c->s>>>(c->N, c->type, U, nc);
+    IBM_LAUNCHED(c);
+    int passes = 0;
+    IBM_TRY(ghost_refresh_all(c, c->u, &passes));
+    for (int a = 0; a < nc; ++a)
+        ++c->nlaunch, k_faces_changed<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->type_old, c->u[a], a, c->F[a]);
+    IBM_LAUNCHED(c);
+    c->fresh_pending = nf > 0;
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
 }
 
 // max |div U - mean| over FLUID cells of the current face field
@@ -1024,7 +1182,7 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
         ++c->nlaunch, helm_rb(c, rhs, hinv, u, 0);
         ++c->nlaunch, helm_rb(c, rhs, hinv, u, 1);
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
         }
         ++c->nlaunch, k_helm_tick<<<1, 1, 0, c->s>>>(H, q, c->opts.helm_maxit, hif);
@@ -1036,7 +1194,7 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
         IBM_LAUNCHED(c);
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
             ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
             IBM_LAUNCHED(c);
         }
@@ -1062,7 +1220,7 @@ static ibm_status ghost_refresh_dev(Ctx *c) {
     CondScope sc;
     IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
     for (int t = 0; t < trip; ++t) {
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp, c->part, t == trip - 1);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), c->gtmp, c->part, t == trip - 1);
         ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
     }
     ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
@@ -1083,7 +1241,7 @@ static ibm_status flow_step_capture(Ctx *c) {
     CFields3 No{{c->Nold[0], c->Nold[1], nc == 3 ? c->Nold[2] : c->Nold[1]}};
     Fields3 Nn{{c->Nnew[0], c->Nnew[1], nc == 3 ? c->Nnew[2] : c->Nnew[1]}};
     Fields3 R{{c->rhs[0], c->rhs[1], nc == 3 ? c->rhs[2] : c->rhs[1]}};
-    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, Nn, R,
+    ++c->nlaunch, k_conv_rhs<<<c->nelem, 256, 0, c->s>>>(c->g, c->type, c->dg_c, u, F, No, c->have_nold ? 0 : 1, c->fresh_pending ? c->fresh : nullptr, Nn, R,
                                                        make_bc(c), dt, alpha, nc);
     IBM_LAUNCHED(c);
     for (int q = 0; q < nc; ++q) {
@@ -1119,6 +1277,8 @@ ibm_status step_graph_eligible(Ctx *c) {
     const ibm_solver_opts &o = c->opts;
     if (o.graph != 2 || c->kt.on || c->s == nullptr || c->s == cudaStreamLegacy) return IBM_ERR_STATE;
     if (o.outer != IBM_OUTER_FGMRES || o.inner_iters != 1 || o.helm_solver != 0) return IBM_ERR_STATE;
+    // a moving body changes the tables every step: host-driven steps
+    if (c->moving) return IBM_ERR_STATE;
     return IBM_OK;
 }
 

@@ -561,6 +561,108 @@ __global__ void __launch_bounds__(64) k_ghost_tables(int ndim, int nx, int ny, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// moving bodies (Section 2.2): body velocity and fresh cells
+// ---------------------------------------------------------------------------
+
+struct Motion {
+    double U[3], w[3], c[3];
+};
+
+// U + Omega x (p - centre), the operations of the oracle's body_velocity
+__global__ void k_body_velocity(int64_t n, const double *__restrict__ pts, Motion m, double *__restrict__ out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const double r0 = pts[3 * g] - m.c[0], r1 = pts[3 * g + 1] - m.c[1], r2 = pts[3 * g + 2] - m.c[2];
+    out[3 * g + 0] = m.U[0] + (m.w[1] * r2 - m.w[2] * r1);
+    out[3 * g + 1] = m.U[1] + (m.w[2] * r0 - m.w[0] * r2);
+    out[3 * g + 2] = m.U[2] + (m.w[0] * r1 - m.w[1] * r0);
+}
+
+// Fresh cell (a FLUID cell that was not FLUID before the move): the
+// trilinear fit on the lattice cell of centres with the fresh cell FC as a
+// corner, extending towards n = (FC - BI) / |FC - BI| along each axis
+// (clamped into the grid), with FC's row replaced by the Dirichlet row at
+// the body intercept, evaluated at FC: u_FC = sum_{m != FC} w_m u_m + wb u_BI.
+// Other corners must be FLUID (fresh ones are implicit unknowns); a GHOST or
+// DEAD corner, a singular system or FC on the surface gives kind 2,
+// u_FC = u_BI. One thread per fresh cell; the operations of the oracle's
+// orc_fresh_tables in its order.
+__global__ void __launch_bounds__(64) k_fresh_tables(int ndim, int nx, int ny, int nz, const double *__restrict__ xc,
+                                                     const double *__restrict__ yc, const double *__restrict__ zc,
+                                                     const double *__restrict__ dx, const double *__restrict__ dy,
+                                                     const double *__restrict__ dz, const uint8_t *__restrict__ type,
+                                                     int64_t nf, const int64_t *__restrict__ fidx,
+                                                     const double *__restrict__ bi, uint8_t *__restrict__ kind,
+                                                     int64_t *__restrict__ sidx, double *__restrict__ w,
+                                                     double *__restrict__ wb) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int nc = ndim == 2 ? 4 : 8;
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    const int64_t c = fidx[f];
+    const int64_t tq = c / nx;
+    const int i = (int)(c - tq * nx), j = (int)(tq % ny), k = (int)(tq / ny);
+    const double p[3] = {xc[i], yc[j], ndim == 2 ? 0.0 : zc[k]};
+    const double q[3] = {bi[3 * f], bi[3 * f + 1], bi[3 * f + 2]};
+    const double dv[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    const double d = sqrt(dot3(dv, dv));
+    double hloc = dx[i] < dy[j] ? dx[i] : dy[j];
+    if (ndim == 3 && dz[k] < hloc) hloc = dz[k];
+    int kd = !(d >= 1e-9 * hloc) ? 2 : 1;
+    double n[3] = {0, 0, 0};
+    if (kd == 1) { n[0] = dv[0] / d; n[1] = dv[1] / d; n[2] = dv[2] / d; }
+    int i0 = n[0] >= 0.0 ? i : i - 1, j0 = n[1] >= 0.0 ? j : j - 1, k0 = 0;
+    i0 = i0 < 0 ? 0 : (i0 > nx - 2 ? nx - 2 : i0);
+    j0 = j0 < 0 ? 0 : (j0 > ny - 2 ? ny - 2 : j0);
+    if (ndim == 3) {
+        k0 = n[2] >= 0.0 ? k : k - 1;
+        k0 = k0 < 0 ? 0 : (k0 > nz - 2 ? nz - 2 : k0);
+    }
+    int64_t cidx[8];
+    int self = -1;
+    for (int m = 0; m < nc; ++m) {
+        const int di = m & 1, dj = (m >> 1) & 1, dk = (m >> 2) & 1;
+        cidx[m] = (int64_t)(i0 + di) * sx + (int64_t)(j0 + dj) * sy + (int64_t)(k0 + dk) * sz;
+        if (cidx[m] == c) self = m;
+        else if (type[cidx[m]] != FLUID) kd = 2;
+    }
+    double xw[8];
+    if (kd == 1) {
+        const double hx = xc[i0 + 1] - xc[i0], hy = yc[j0 + 1] - yc[j0];
+        const double hz = ndim == 3 ? zc[k0 + 1] - zc[k0] : 1.0;
+        const double bxi = (q[0] - xc[i0]) / hx, bet = (q[1] - yc[j0]) / hy;
+        const double bze = ndim == 3 ? (q[2] - zc[k0]) / hz : 0.0;
+        double bBI[8], bFC[8], M[64], r[8];
+        basis(ndim, bxi, bet, bze, bBI);
+        basis(ndim, (double)(self & 1), (double)((self >> 1) & 1), (double)((self >> 2) & 1), bFC);
+        for (int m = 0; m < nc; ++m) {
+            double row[8];
+            if (m == self) {
+                for (int t = 0; t < nc; ++t) row[t] = bBI[t];
+            } else {
+                basis(ndim, (double)(m & 1), (double)((m >> 1) & 1), (double)((m >> 2) & 1), row);
+            }
+            for (int t = 0; t < nc; ++t) M[t * nc + m] = row[t];
+        }
+        for (int t = 0; t < nc; ++t) r[t] = bFC[t];
+        if (lu_solve(nc, M, r, xw)) kd = 2;
+    }
+    kind[f] = (uint8_t)kd;
+    int64_t *SI = sidx + 8 * f;
+    double *W = w + 8 * f;
+    if (kd == 1) {
+        for (int m = 0; m < 8; ++m) {
+            if (m < nc && m != self) { SI[m] = cidx[m]; W[m] = xw[m]; }
+            else { SI[m] = c; W[m] = 0.0; }
+        }
+        wb[f] = xw[self];
+    } else {
+        for (int m = 0; m < 8; ++m) { SI[m] = c; W[m] = 0.0; }
+        wb[f] = 1.0;
+    }
+}
+
 __global__ void k_kind_counts(int64_t ng, const uint8_t *__restrict__ kind, unsigned long long *__restrict__ cnt) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g < ng) atomicAdd(&cnt[kind[g]], 1ull);
@@ -595,6 +697,32 @@ static ibm_status ensure_ghost_capacity(Ctx *c, int64_t ng) {
         !c->bp || !c->kind || !c->cmask || !c->gtmp)
         return c->fail(IBM_ERR_OOM, "ghost table allocation failed");
     c->ng_cap = cap;
+    return IBM_OK;
+}
+
+ibm_status geom_body_velocity(Ctx *c, int64_t n, const double *pts, double *out) {
+    if (n <= 0) return IBM_OK;
+    Motion m;
+    for (int a = 0; a < 3; ++a) {
+        m.U[a] = c->motion[a];
+        m.w[a] = c->motion[3 + a];
+        m.c[a] = c->motion[6 + a];
+    }
+    ++c->nlaunch, k_body_velocity<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(n, pts, m, out);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+ibm_status geom_fresh_tables(Ctx *c, int64_t nf, const int64_t *fidx, double *bi, uint8_t *kind, int64_t *sidx,
+                             double *w, double *wb) {
+    if (nf <= 0) return IBM_OK;
+    ++c->nlaunch, k_body_intercept<<<(unsigned)((nf + 127) / 128), 128, 0, c->s>>>(c->ndim, c->nx, c->ny, c->xc, c->yc, c->zc, nf,
+                                                                                  fidx, c->d_verts, c->ne, c->d_elems, bi);
+    IBM_LAUNCHED(c);
+    ++c->nlaunch, k_fresh_tables<<<(unsigned)((nf + 63) / 64), 64, 0, c->s>>>(c->ndim, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
+                                                                             c->dx, c->dy, c->dz, c->type, nf, fidx, bi,
+                                                                             kind, sidx, w, wb);
+    IBM_LAUNCHED(c);
     return IBM_OK;
 }
 

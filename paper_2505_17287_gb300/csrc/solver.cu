@@ -881,25 +881,34 @@ __device__ __forceinline__ void split_quad_pos(const SplitLv<float> &L, int64_t 
     base = (int64_t)row * L.H + h0;
 }
 
+// the other colour's values a quad needs: its own row's quad O and the edge
+// value xe (x - 1 of cell 0 for pc = 0, x + 1 of cell 3 for pc = 1), and the
+// quads of the y and z neighbour rows (O where there is no row: unused, the
+// mask has no open face there). All loads are issued together.
+struct QuadNb {
+    float4 O, ym, yp, zm, zp;
+    float xe;
+};
+
+__device__ __forceinline__ QuadNb split_loads(const SplitLv<float> &L, const float *__restrict__ xo, int64_t base,
+                                              int h0, int j, int k, int pc) {
+    const int64_t sy = L.H, sz = (int64_t)L.H * L.ny;
+    QuadNb q;
+    q.O = ld4(xo + base);
+    const int64_t ie = pc == 0 ? base - 1 : base + 4;
+    const bool he = pc == 0 ? h0 > 0 : h0 + 4 < L.H;
+    q.xe = he ? xo[ie] : 0.f;
+    q.ym = ld4(xo + (j > 0 ? base - sy : base));
+    q.yp = ld4(xo + (j < L.ny - 1 ? base + sy : base));
+    q.zm = ld4(xo + (L.nz > 1 && k > 0 ? base - sz : base));
+    q.zp = ld4(xo + (L.nz > 1 && k < L.nz - 1 ? base + sz : base));
+    return q;
+}
+
 // sum over the open faces of T_f x_nb and the face sum d for the four cells
 // of a quad (the order and operations of k_offdiag<float, true>)
-__device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const float *__restrict__ xo, int64_t base,
-                                              int h0, int j, int k, int pc, uchar4 m4, float4 O, float s[4],
-                                              float d[4]) {
-    const int64_t sy = L.H, sz = (int64_t)L.H * L.ny;
-    float xe = 0.f;   // x - 1 of cell 0 (pc = 0) or x + 1 of cell 3 (pc = 1)
-    if (pc == 0) {
-        if (h0 > 0) xe = xo[base - 1];
-    } else if (h0 + 4 < L.H) {
-        xe = xo[base + 4];
-    }
-    const float4 ym = j > 0 ? ld4(xo + base - sy) : O;
-    const float4 yp = j < L.ny - 1 ? ld4(xo + base + sy) : O;
-    float4 zm = O, zp = O;
-    if (L.nz > 1) {
-        if (k > 0) zm = ld4(xo + base - sz);
-        if (k < L.nz - 1) zp = ld4(xo + base + sz);
-    }
+__device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const QuadNb &N, int h0, int j, int k,
+                                              int pc, uchar4 m4, float s[4], float d[4]) {
     const float4 wx4 = ld4((pc ? L.swx1 : L.swx0) + h0);
     const float4 rm4 = ld4((pc ? L.srm1 : L.srm0) + h0);
     const float4 rp4 = ld4((pc ? L.srp1 : L.srp0) + h0);
@@ -907,17 +916,17 @@ __device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const flo
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
-        const float xm = pc ? f4at(O, e) : (e == 0 ? xe : f4at(O, e - 1));
-        const float xp = pc ? (e == 3 ? xe : f4at(O, e + 1)) : f4at(O, e);
+        const float xm = pc ? f4at(N.O, e) : (e == 0 ? N.xe : f4at(N.O, e - 1));
+        const float xp = pc ? (e == 3 ? N.xe : f4at(N.O, e + 1)) : f4at(N.O, e);
         const float wxe = f4at(wx4, e);
         const float ayz = wyj * wzk, axz = wxe * wzk, axy = wxe * wyj;
         float dd = 0.f, ss = 0.f, t;
         if (msk & 1u) { t = ayz * f4at(rm4, e); dd += t; ss += t * xm; }
         if (msk & 2u) { t = ayz * f4at(rp4, e); dd += t; ss += t * xp; }
-        if (msk & 4u) { t = axz * ry0; dd += t; ss += t * f4at(ym, e); }
-        if (msk & 8u) { t = axz * ry1; dd += t; ss += t * f4at(yp, e); }
-        if (msk & 16u) { t = axy * rz0; dd += t; ss += t * f4at(zm, e); }
-        if (msk & 32u) { t = axy * rz1; dd += t; ss += t * f4at(zp, e); }
+        if (msk & 4u) { t = axz * ry0; dd += t; ss += t * f4at(N.ym, e); }
+        if (msk & 8u) { t = axz * ry1; dd += t; ss += t * f4at(N.yp, e); }
+        if (msk & 16u) { t = axy * rz0; dd += t; ss += t * f4at(N.zm, e); }
+        if (msk & 32u) { t = axy * rz1; dd += t; ss += t * f4at(N.zp, e); }
         s[e] = ss;
         d[e] = dd;
     }
@@ -927,6 +936,8 @@ __device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const flo
 // storage; cells that are not updated keep their value. With NAT the pass is
 // the last of the V-cycle: instead of xq it writes the cell-ordered output
 // xn (both colours: this colour's new values, the other colour's from xo).
+// Every load of a quad is issued before the first use, so a thread waits
+// for memory once.
 template <bool OMEGA, bool NAT>
 __global__ void __launch_bounds__(256)
     k_rbgs_split(SplitLv<float> L, const float *__restrict__ fq, const uint8_t *__restrict__ mq,
@@ -938,29 +949,27 @@ __global__ void __launch_bounds__(256)
     split_quad_pos(L, q, base, h0, j, k);
     const int pc = (col + j + k) & 1;
     const uchar4 m4 = *reinterpret_cast<const uchar4 *>(mq + base);
+    const float4 f4 = ld4(fq + base);
+    const QuadNb N = split_loads(L, xo, base, h0, j, k, pc);
+    float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (OMEGA) old = ld4(xq + base);
     const unsigned any = (m4.x | m4.y | m4.z | m4.w) & 0x80u;
-    const float4 O = ld4(xo + base);
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    bool up[4] = {false, false, false, false};
-    if (any) {
-        float sv[4], dv[4];
-        split_offdiag(L, xo, base, h0, j, k, pc, m4, O, sv, dv);
-        const float4 f4 = ld4(fq + base);
+    if (!NAT && !any) return;   // no active cell: nothing changes
+    float sv[4], dv[4];
+    split_offdiag(L, N, h0, j, k, pc, m4, sv, dv);
+    float v[4];
+    bool up[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
-            const float s = f4at(f4, e) + sv[e];
-            if ((msk & 0x80u) && dv[e] > 0.f) {
-                v[e] = fast_div(s, dv[e]);
-                up[e] = true;
-            }
-        }
+    for (int e = 0; e < 4; ++e) {
+        const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
+        const float s = f4at(f4, e) + sv[e];
+        up[e] = (msk & 0x80u) && dv[e] > 0.f;
+        v[e] = up[e] ? fast_div(s, dv[e]) : 0.f;
     }
     const bool all = up[0] && up[1] && up[2] && up[3];
-    if (!NAT && !any) return;   // no active cell: nothing changes
     if (OMEGA || !all) {
         // the old values: the relaxation needs them, and cells not updated keep them
-        const float4 old = ld4(xq + base);
+        if (!OMEGA) old = ld4(xq + base);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float o = f4at(old, e);
@@ -973,7 +982,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             a[2 * e + pc] = v[e];
-            a[2 * e + 1 - pc] = f4at(O, e);
+            a[2 * e + 1 - pc] = f4at(N.O, e);
         }
         float *dst = xn + base * 2;   // cell 2 h0 of the row (2 H = nx)
         *reinterpret_cast<float4 *>(dst) = make_float4(a[0], a[1], a[2], a[3]);

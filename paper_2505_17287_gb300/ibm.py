@@ -102,7 +102,7 @@ class ibm_server_stats(Structure):
 
 EXPORTS = ["ibm_step_async", "ibm_step_wait", "ibm_step_prepare", "ibm_tune", "ibm_case_bytes", "ibm_server_create", "ibm_server_submit", "ibm_server_wait", "ibm_server_get_stats",
            "ibm_server_destroy",
-           "ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells",
+           "ibm_default_opts", "ibm_create_grid", "ibm_set_opts", "ibm_set_body", "ibm_classify_cells", "ibm_move_body",
            "ibm_step", "ibm_poisson_solve", "ibm_get_tables", "ibm_get_field", "ibm_set_field", "ibm_sizes",
            "ibm_kernel_timer", "ibm_kernel_time", "ibm_launch_count", "ibm_poisson_residual_noalloc",
            "ibm_destroy", "ibm_last_error"]
@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
     L.ibm_set_opts.argtypes = [P, POINTER(ibm_solver_opts)]
     L.ibm_set_body.argtypes = [P, P, c_int64, P, c_int64]
     L.ibm_classify_cells.argtypes = [P, POINTER(ibm_table_info)]
+    L.ibm_move_body.argtypes = [P, P, c_int64, P, POINTER(ibm_table_info)]
     L.ibm_step.argtypes = [P, c_int, POINTER(ibm_step_stats)]
     L.ibm_poisson_solve.argtypes = [P, P, P, c_double, c_int, POINTER(ibm_solve_stats)]
     L.ibm_get_tables.argtypes = [P, POINTER(ibm_tables_host)]
@@ -203,6 +204,16 @@ def ibm_set_body(ctx, verts: np.ndarray, elems: np.ndarray):
 def ibm_classify_cells(ctx):
     info = ibm_table_info()
     _check(load_library().ibm_classify_cells(ctx, byref(info)), ctx)
+    return info
+
+
+def ibm_move_body(ctx, verts: np.ndarray, motion):
+    """Move the bodies to verts (all vertices of every set body, same order)
+    with the rigid motion (U, Omega, centre); returns the new table info."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    m = np.ascontiguousarray(np.asarray(motion, dtype=np.float64).reshape(9))
+    info = ibm_table_info()
+    _check(load_library().ibm_move_body(ctx, _p(v), v.shape[0], _p(m), byref(info)), ctx)
     return info
 
 
@@ -347,6 +358,12 @@ class Solver:
 
     def classify(self):
         self.info = ibm_classify_cells(self.ctx)
+        return dict(n_fluid=self.info.n_fluid, n_ghost=self.info.n_ghost, n_dead=self.info.n_dead,
+                    n_kind=list(self.info.n_kind))
+
+    def move_body(self, verts, U=(0.0, 0.0, 0.0), omega=(0.0, 0.0, 0.0), centre=(0.0, 0.0, 0.0)):
+        """Move every set body to verts with the rigid velocity U + omega x (x - centre)."""
+        self.info = ibm_move_body(self.ctx, verts, tuple(U) + tuple(omega) + tuple(centre))
         return dict(n_fluid=self.info.n_fluid, n_ghost=self.info.n_ghost, n_dead=self.info.n_dead,
                     n_kind=list(self.info.n_kind))
 
