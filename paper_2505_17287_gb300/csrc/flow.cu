@@ -312,8 +312,9 @@ __global__ void k_helm_resid(GridDev g, HelmCoef h, const uint8_t *__restrict__ 
 
 // Dirichlet ghost rows for up to three components at once:
 // tmp[q*ng + g] = (2 - bv) u_BI - sum_m wv_m u_m, with u_BI the body velocity
-// at the intercept (ubi, 3 per ghost; null: body at rest, u_BI = 0)
-__global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, const double *__restrict__ ubi,
+// at the intercept (ubi, 3 per ghost; null: body at rest, u_BI = 0); the
+// fields u.p[0..ncomp) are velocity components comp0, comp0 + 1, ...
+__global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, const double *__restrict__ ubi, int comp0,
                                  double *__restrict__ tmp, double *__restrict__ res, int want_res) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     __shared__ double sh[32];
@@ -321,7 +322,8 @@ __global__ void k_vghost_compute(GhostDev gh, Fields3 u, int ncomp, const double
     if (q < gh.ng) {
         for (int cq = 0; cq < ncomp; ++cq) {
             const double *uu = u.p[cq];
-            double s = ubi ? (2.0 - gh.bv[q]) * ubi[3 * q + cq] : 0.0;
+            // (u.p[cq] is velocity component comp0 + cq)
+            double s = ubi ? (2.0 - gh.bv[q]) * ubi[3 * q + comp0 + cq] : 0.0;
             for (int m = 0; m < 8; ++m) s -= gh.wv[8 * q + m] * uu[gh.sidx[8 * q + m]];
             tmp[cq * gh.ng + q] = s;
             const double d = s - uu[gh.gidx[q]];
@@ -610,7 +612,7 @@ static ibm_status ghost_refresh_all(Ctx *c, double *const *ucell, int *passes) {
     const int check_every = 4;
     for (int it = 0; it < c->opts.ghost_maxit; ++it) {
         const int want = ((it + 1) % check_every == 0) || it + 1 == c->opts.ghost_maxit;
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), c->gtmp, c->part, want);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), 0, c->gtmp, c->part, want);
         ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
         IBM_LAUNCHED(c);
         ++*passes;
@@ -744,7 +746,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
             kt_end(c, K_HELM);
             if (c->ng > 0) {
                 Fields3 T3{{t, t, t}};
-                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, ghost_ubi(c), c->gtmp, c->part, 0);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, ghost_ubi(c), q, c->gtmp, c->part, 0);
                 ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, T3, 1, c->gtmp);
             }
             IBM_LAUNCHED(c);
@@ -760,7 +762,7 @@ static ibm_status helmholtz_srj(Ctx *c, int q, int *sweeps) {
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         double gmax = 0.0;
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), q, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
             ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
             IBM_LAUNCHED(c);
         }
@@ -805,7 +807,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
         kt_end(c, K_HELM);
         IBM_LAUNCHED(c);
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), q, c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
             IBM_LAUNCHED(c);
         }
@@ -818,7 +820,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
             double gmax = 0.0;
             if (c->ng > 0) {
                 // ghost-row residual: largest change a further Jacobi pass would make
-                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+                ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), q, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
                 ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
                 IBM_LAUNCHED(c);
             }
@@ -1182,7 +1184,7 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
         ++c->nlaunch, helm_rb(c, rhs, hinv, u, 0);
         ++c->nlaunch, helm_rb(c, rhs, hinv, u, 1);
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part, 0);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), q, c->gtmp, c->part, 0);
             ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, 1, c->gtmp);
         }
         ++c->nlaunch, k_helm_tick<<<1, 1, 0, c->s>>>(H, q, c->opts.helm_maxit, hif);
@@ -1194,7 +1196,7 @@ static ibm_status helmholtz_dev(Ctx *c, int q) {
         IBM_LAUNCHED(c);
         IBM_TRY(finalize(c, c->part, c->nred, 2, 1.0, c->scal + 48));
         if (c->ng > 0) {
-            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
+            ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, 1, ghost_ubi(c), q, c->gtmp, c->part + 2 * RED_BLOCKS_MAX, 1);
             ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part + 2 * RED_BLOCKS_MAX, (int)gb, c->scal + 50);
             IBM_LAUNCHED(c);
         }
@@ -1220,7 +1222,7 @@ static ibm_status ghost_refresh_dev(Ctx *c) {
     CondScope sc;
     IBM_TRY(cond_open(c, cudaGraphCondTypeWhile, h, &sc));
     for (int t = 0; t < trip; ++t) {
-        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), c->gtmp, c->part, t == trip - 1);
+        ++c->nlaunch, k_vghost_compute<<<gb, 256, 0, c->s>>>(c->gh, U, nc, ghost_ubi(c), 0, c->gtmp, c->part, t == trip - 1);
         ++c->nlaunch, k_vghost_scatter<<<gb, 256, 0, c->s>>>(c->gh, U, nc, c->gtmp);
     }
     ++c->nlaunch, k_max_final<<<1, 256, 0, c->s>>>(c->part, (int)gb, c->scal + 40);
