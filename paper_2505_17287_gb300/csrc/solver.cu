@@ -909,20 +909,21 @@ __device__ __forceinline__ QuadNb split_loads(const SplitLv<float> &L, const flo
 // of a quad (the order and operations of k_offdiag<float, true>)
 __device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const QuadNb &N, int h0, int j, int k,
                                               int pc, uchar4 m4, float s[4], float d[4]) {
-    const float4 wx4 = ld4((pc ? L.swx1 : L.swx0) + h0);
-    const float4 rm4 = ld4((pc ? L.srm1 : L.srm0) + h0);
-    const float4 rp4 = ld4((pc ? L.srp1 : L.srp0) + h0);
+    // the 1D metrics are small arrays (L1 hits), read per cell as needed so
+    // they hold no registers across the loop
+    const float *swx = (pc ? L.swx1 : L.swx0) + h0, *srm = (pc ? L.srm1 : L.srm0) + h0;
+    const float *srp = (pc ? L.srp1 : L.srp0) + h0;
     const float wyj = L.wy[j], wzk = L.wz[k], ry0 = L.rhy[j], ry1 = L.rhy[j + 1], rz0 = L.rhz[k], rz1 = L.rhz[k + 1];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const unsigned msk = e == 0 ? m4.x : e == 1 ? m4.y : e == 2 ? m4.z : m4.w;
         const float xm = pc ? f4at(N.O, e) : (e == 0 ? N.xe : f4at(N.O, e - 1));
         const float xp = pc ? (e == 3 ? N.xe : f4at(N.O, e + 1)) : f4at(N.O, e);
-        const float wxe = f4at(wx4, e);
+        const float wxe = swx[e];
         const float ayz = wyj * wzk, axz = wxe * wzk, axy = wxe * wyj;
         float dd = 0.f, ss = 0.f, t;
-        if (msk & 1u) { t = ayz * f4at(rm4, e); dd += t; ss += t * xm; }
-        if (msk & 2u) { t = ayz * f4at(rp4, e); dd += t; ss += t * xp; }
+        if (msk & 1u) { t = ayz * srm[e]; dd += t; ss += t * xm; }
+        if (msk & 2u) { t = ayz * srp[e]; dd += t; ss += t * xp; }
         if (msk & 4u) { t = axz * ry0; dd += t; ss += t * f4at(N.ym, e); }
         if (msk & 8u) { t = axz * ry1; dd += t; ss += t * f4at(N.yp, e); }
         if (msk & 16u) { t = axy * rz0; dd += t; ss += t * f4at(N.zm, e); }
@@ -939,7 +940,7 @@ __device__ __forceinline__ void split_offdiag(const SplitLv<float> &L, const Qua
 // Every load of a quad is issued before the first use, so a thread waits
 // for memory once.
 template <bool OMEGA, bool NAT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
     k_rbgs_split(SplitLv<float> L, const float *__restrict__ fq, const uint8_t *__restrict__ mq,
                  const float *__restrict__ xo, float *__restrict__ xq, int col, float w, float *__restrict__ xn) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
