@@ -1389,38 +1389,170 @@ __global__ void __launch_bounds__(RX_THREADS)
     }
 }
 
-// k_prolong_yz on level 0 in colour-split storage (x split, pn and tB
-// cell-ordered)
-__global__ void k_prolong_yz_split(MGLevel<float> L, float *__restrict__ xs0, float *__restrict__ xs1,
-                                   const float *__restrict__ tB, int cny, Xfer<float> X, const float *__restrict__ pn) {
-    const int64_t row = blockIdx.x;
+// k_resid_rx on level 0 in colour-split storage when x is coarsened by two
+// (nx a multiple of 8): one thread per four coarse x-cells I0 .. I0 + 3 of a
+// row. Coarse I gathers fine cells 2I - 1 .. 2I + 2, so the thread evaluates
+// pn r on the ten fine cells 2 I0 - 1 .. 2 I0 + 8 (the two outer ones also by
+// its neighbours) with 16-byte loads: the colour relaxed last (1) has zero
+// residual where it has an open face and p f where it has none; colour 0
+// takes the full stencil, in the order and operations of k_resid_rx. The
+// restriction then sums in the gather table's order, so the result equals
+// k_resid_rx bit for bit.
+__global__ void __launch_bounds__(256)
+    k_resid_rx_split4(MGLevel<float> L, SplitLv<float> S, const float *__restrict__ fs0, const float *__restrict__ fs1,
+                      const float *__restrict__ xs0, const float *__restrict__ xs1, const float *__restrict__ pn,
+                      Xfer<float> X, float *__restrict__ tA) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= S.nq) return;
+    const int H = S.H, nx = L.nx;
+    const uint32_t rw = S.fq.div((uint32_t)q);
+    const int I0 = 4 * (int)((uint32_t)q - rw * (uint32_t)(H / 4));   // packed quad h0 = I0 (H = coarse nx)
     int j, k;
-    row_jk((uint32_t)blockIdx.x, L.fny, L.ny, j, k);
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= L.nx) return;
-    const int64_t c = row * L.nx + i;
-    float *x = ((i + j + k) & 1) ? xs1 : xs0;
-    const int64_t pb = row * (L.nx / 2) + (i >> 1);
+    row_jk(rw, S.fny, S.ny, j, k);
+    const int64_t row = rw, base = row * H + I0, crow = row * nx;
+    const int pc0 = (j + k) & 1;             // colour 0 sits at i = 2 h + pc0
+    const int64_t sy = H, sz = (int64_t)H * L.ny;
+    const int i0 = 2 * I0 - 1;               // first fine cell of the window
+    // colour 0 of the window: packed I0 - pc0 .. I0 + 4 - pc0 = the quad at
+    // I0 and one edge cell he
+    const float4 x0q = ld4(xs0 + base), f0q = ld4(fs0 + base);
+    const int he = pc0 ? I0 - 1 : I0 + 4;
+    const bool heok = he >= 0 && he < H;
+    const int64_t be = row * H + (heok ? he : I0);
+    const float x0e = heok ? xs0[be] : 0.f, f0e = heok ? fs0[be] : 0.f;
+    // colour 1: packed I0 - 1 .. I0 + 4 of the row (x neighbours), and the
+    // y / z rows at the colour-0 cells' packed indices
+    const float4 c1q = ld4(xs1 + base);
+    const float c1m = I0 > 0 ? xs1[base - 1] : 0.f, c1p = I0 + 4 < H ? xs1[base + 4] : 0.f;
+    const float4 ymq = ld4(xs1 + (j > 0 ? base - sy : base)), ypq = ld4(xs1 + (j < L.ny - 1 ? base + sy : base));
+    const float yme = (j > 0 && heok) ? xs1[be - sy] : 0.f, ype = (j < L.ny - 1 && heok) ? xs1[be + sy] : 0.f;
+    float4 zmq = c1q, zpq = c1q;
+    float zme = 0.f, zpe = 0.f;
+    if (L.nz > 1) {
+        if (k > 0) {
+            zmq = ld4(xs1 + base - sz);
+            if (heok) zme = xs1[be - sz];
+        }
+        if (k < L.nz - 1) {
+            zpq = ld4(xs1 + base + sz);
+            if (heok) zpe = xs1[be + sz];
+        }
+    }
+    // cell-ordered pn and open-face mask of the window
+    const float4 pA = ld4(pn + crow + 2 * I0), pB = ld4(pn + crow + 2 * I0 + 4);
+    const float pm = I0 > 0 ? pn[crow + i0] : 0.f, pp = 2 * I0 + 8 < nx ? pn[crow + 2 * I0 + 8] : 0.f;
+    const uint2 mm = *reinterpret_cast<const uint2 *>(L.omask + crow + 2 * I0);
+    const unsigned mlo = I0 > 0 ? L.omask[crow + i0] : 0u, mhi = 2 * I0 + 8 < nx ? L.omask[crow + 2 * I0 + 8] : 0u;
+    const float wyj = L.wy[j], wzk = L.wz[k], ry0 = L.rhy[j], ry1 = L.rhy[j + 1], rz0 = L.rhz[k], rz1 = L.rhz[k + 1];
+    float r[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+        const int i = i0 + t;
+        const float p = t == 0 ? pm : (t == 9 ? pp : (t < 5 ? f4at(pA, t - 1) : f4at(pB, t - 5)));
+        const unsigned msk = t == 0 ? mlo : (t == 9 ? mhi : (((t < 5 ? mm.x : mm.y) >> (8 * ((t - 1) & 3))) & 0xffu));
+        float v = 0.f;
+        if (i >= 0 && i < nx && p > 0.f) {
+            if (((t + pc0 + 1) & 1) == 0) {
+                // colour 0, the e-th of the window's five (t = 2 e - pc0 + 1)
+                const int e = (t + pc0 - 1) >> 1;
+                const bool edge = pc0 ? e == 0 : e == 4;
+                const int qq = pc0 ? e - 1 : e;
+                const float xc = edge ? x0e : f4at(x0q, qq & 3), fc = edge ? f0e : f4at(f0q, qq & 3);
+                // x neighbours (colour 1) at packed I0 - 1 + e and I0 + e
+                const float xm = e == 0 ? c1m : f4at(c1q, (e - 1) & 3);
+                const float xp = e == 4 ? c1p : f4at(c1q, e & 3);
+                const float ym = edge ? yme : f4at(ymq, qq & 3), yp = edge ? ype : f4at(ypq, qq & 3);
+                const float zm = edge ? zme : f4at(zmq, qq & 3), zp = edge ? zpe : f4at(zpq, qq & 3);
+                const float ayz = wyj * wzk, axz = L.wx[i] * wzk, axy = L.wx[i] * wyj;
+                float d = 0.f, s = fc, tt;
+                if (msk & 1u) { tt = ayz * L.rhx[i]; d += tt; s += tt * xm; }
+                if (msk & 2u) { tt = ayz * L.rhx[i + 1]; d += tt; s += tt * xp; }
+                if (msk & 4u) { tt = axz * ry0; d += tt; s += tt * ym; }
+                if (msk & 8u) { tt = axz * ry1; d += tt; s += tt * yp; }
+                if (msk & 16u) { tt = axy * rz0; d += tt; s += tt * zm; }
+                if (msk & 32u) { tt = axy * rz1; d += tt; s += tt * zp; }
+                v = p * (s - d * xc);
+            } else if ((msk & 0x3fu) == 0) {
+                // colour 1 (relaxed last) without an open face: not updated by
+                // the smoother, r = p (f - 0 x)
+                const int64_t pb = row * H + (i >> 1);
+                const float d = 0.f;
+                v = p * (fs1[pb] - d * xs1[pb]);
+            }
+        }
+        r[t] = v;
+    }
+    // coarse I = I0 + u gathers the consecutive fine cells 2I - 1 .. 2I + 2
+    // (2I .. 2I + 2 at the row start): window positions 2u + s + sh
+    // (each coarse cell's four table entries in one 16-byte load apiece)
+    float out[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int I = I0 + u;
+        const int4 gi = *reinterpret_cast<const int4 *>(X.Gx + 4 * I);
+        const float4 gw = ld4(X.gwx + 4 * I);
+        const bool sh = gi.x != 2 * I - 1;
+        const int g4[4] = {gi.x, gi.y, gi.z, gi.w};
+        float acc = 0.f;
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+            if (g4[s2] < 0) continue;
+            const float rv = sh ? (2 * u + s2 + 1 <= 9 ? r[(2 * u + s2 + 1) > 9 ? 9 : (2 * u + s2 + 1)] : 0.f) : r[2 * u + s2];
+            acc += f4at(gw, s2) * rv;
+        }
+        out[u] = acc;
+    }
+    *reinterpret_cast<float4 *>(tA + base) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// k_prolong_yz on level 0 in colour-split storage, eight consecutive fine
+// cells (one quad of each colour) per thread: tB, pn and both colours' x in
+// 16-byte accesses; each cell gets the expression of k_prolong_yz (cells
+// with pn = 0 keep their value)
+__global__ void __launch_bounds__(256)
+    k_prolong_yz_split8(MGLevel<float> L, SplitLv<float> S, float *__restrict__ xs0, float *__restrict__ xs1,
+                        const float *__restrict__ tB, int cny, Xfer<float> X, const float *__restrict__ pn) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= S.nq) return;
+    int64_t base;
+    int h0, j, k;
+    split_quad_pos(S, q, base, h0, j, k);
+    const int pc0 = (j + k) & 1;
+    const int64_t nat = base * 2;   // cell 2 h0 of the row
     int ib[2], ic[2];
     float wb[2], wc[2];
     const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
     const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
-    float tv[2][2];
+    const int64_t off = 2 * (int64_t)h0;
+    float4 tv[2][2][2];
 #pragma unroll
     for (int q3 = 0; q3 < 2; ++q3)
 #pragma unroll
-        for (int q2 = 0; q2 < 2; ++q2)
-            tv[q3][q2] = tB[((int64_t)ic[q3 < nc ? q3 : 0] * cny + ib[q2 < nb ? q2 : 0]) * L.nx + i];
-    const float p = pn[c];
-    const float xc = x[pb];
-    if (!pos(p)) return;
-    float acc = 0.f;
-    for (int q3 = 0; q3 < nc; ++q3) {
-        float a2 = 0.f;
-        for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * tv[q3][q2];
-        acc += wc[q3] * a2;
+        for (int q2 = 0; q2 < 2; ++q2) {
+            const float *r = tB + ((int64_t)ic[q3 < nc ? q3 : 0] * cny + ib[q2 < nb ? q2 : 0]) * L.nx + off;
+            tv[q3][q2][0] = ld4(r);
+            tv[q3][q2][1] = ld4(r + 4);
+        }
+    const float4 pA = ld4(pn + nat), pB = ld4(pn + nat + 4);
+    const float4 a0 = ld4(xs0 + base), a1 = ld4(xs1 + base);
+    float o0[4] = {a0.x, a0.y, a0.z, a0.w}, o1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const float p = m < 4 ? f4at(pA, m) : f4at(pB, m - 4);
+        if (!pos(p)) continue;
+        float acc = 0.f;
+        for (int q3 = 0; q3 < nc; ++q3) {
+            float a2 = 0.f;
+            for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * f4at(tv[q3][q2][m >> 2], m & 3);
+            acc += wc[q3] * a2;
+        }
+        const bool c0 = ((m + pc0) & 1) == 0;
+        const int e = m >> 1;   // packed position of cell 2 h0 + m in its colour
+        if (c0) o0[e] = o0[e] + acc * p;
+        else o1[e] = o1[e] + acc * p;
     }
-    x[pb] = xc + acc * p;
+    *reinterpret_cast<float4 *>(xs0 + base) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+    *reinterpret_cast<float4 *>(xs1 + base) = make_float4(o1[0], o1[1], o1[2], o1[3]);
 }
 
 // coarsest level: red-black sweeps in one block, all data in shared memory.
@@ -2112,8 +2244,14 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             bool done = false;
             if constexpr (sizeof(T) == 4) {
                 if (l == 0 && sp) {
-                    KL(K_RESTRICT, k_resid_rx_split, rgrid, RX_THREADS, Lf, H.fs[0], H.fs[1], H.xs[0], H.xs[1],
-                       H.pn[l], X, Cl.nx, CG.fx, zcol, tA);
+                    if (CG.fx == 2 && zcol == 1) {
+                        const SplitLv<float> S = split_of(H);
+                        KL(K_RESTRICT, k_resid_rx_split4, (unsigned)((S.nq + 255) / 256), 256, Lf, S, H.fs[0],
+                           H.fs[1], H.xs[0], H.xs[1], H.pn[l], X, tA);
+                    } else {
+                        KL(K_RESTRICT, k_resid_rx_split, rgrid, RX_THREADS, Lf, H.fs[0], H.fs[1], H.xs[0], H.xs[1],
+                           H.pn[l], X, Cl.nx, CG.fx, zcol, tA);
+                    }
                     done = true;
                 }
             }
@@ -2147,7 +2285,9 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             bool done = false;
             if constexpr (sizeof(T) == 4) {
                 if (l == 0 && sp) {
-                    KL(K_PROLONG, k_prolong_yz_split, grid, bx, Lf, H.xs[0], H.xs[1], tB, Cl.ny, X, H.pn[l]);
+                    const SplitLv<float> S = split_of(H);
+                    KL(K_PROLONG, k_prolong_yz_split8, (unsigned)((S.nq + 255) / 256), 256, Lf, S, H.xs[0], H.xs[1], tB,
+                       Cl.ny, X, H.pn[l]);
                     done = true;
                 }
             }
