@@ -583,7 +583,12 @@ def main():
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    kname = ("k_rbgs<float, fine>" if mixed_main else "k_rbgs<double>") + " (finest level, one colour pass)"
+    # mixed precision with nx a multiple of 8: the finest FP32 level in
+    # colour-split storage (one colour pass streams the other colour's x)
+    split = mixed_main and N % 8 == 0 and int(args.size.split(",")[0]) % 8 == 0
+    kname = ("k_rbgs_split (finest FP32 level in colour-split storage" if split else
+             "k_rbgs<float, fine> (finest level" if mixed_main else "k_rbgs<double> (finest level") + \
+        ", one colour pass)"
     tpc = TRAFFIC_BYTES_PER_CELL.get((kname, sz))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

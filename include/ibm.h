@@ -101,8 +101,13 @@ typedef struct {
     int ghost_maxit;    /* velocity ghost refresh: Jacobi pass limit */
     int precision;      /* IBM_FP64 or IBM_MIXED */
     int outer;          /* IBM_OUTER_BICGSTAB or IBM_OUTER_FGMRES */
-    int band_sweeps;    /* damped Jacobi sweeps of the full operator near the body, per
-                           preconditioner call (0 = none) */
+    int band_sweeps;    /* damped Jacobi sweeps of the full ghost-cell operator on the
+                           near-body band (band_width), after the multigrid cycle of
+                           each preconditioner call, in its precision (0 = none).
+                           The cycle works on the staircase operator, whose faces
+                           between FLUID and GHOST cells are closed; these sweeps
+                           correct the preconditioned vector where the two
+                           operators differ */
     double band_omega;  /* their damping factor, in (0, 1] */
     double mixed_inner_rtol; /* IBM_MIXED with FGMRES: residual reduction asked of each
                            FP32 Krylov solve inside the FP64 defect correction */
@@ -157,6 +162,10 @@ typedef struct {
                            colour packed in x order), so a colour pass streams only the
                            other colour's x and its own f; same arithmetic and results
                            bit for bit as 0, the cell-ordered layout */
+    int band_width;     /* the near-body band of band_sweeps: the ghost cells and the
+                           FLUID cells within band_width faces of one, 1..4; read
+                           when the cells are classified (ibm_classify_cells,
+                           ibm_move_body) */
 } ibm_solver_opts;
 
 typedef struct {
@@ -217,9 +226,9 @@ enum {
 /* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
-   band_sweeps 0, band_omega 0.7, mixed_inner_rtol 1e-4, mg_interp 1,
+   band_sweeps 3, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6, helm_omega 1, fine_split 1. */
+   helm_check_first 6, helm_omega 1, fine_split 1, band_width 2. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -1762,31 +1762,67 @@ __global__ void k_pre_ghost(GhostDev gh, const T *__restrict__ wp, const uint8_t
     z[gi] = s;
 }
 
-// one damped Jacobi pass of the full operator on the band: tmp = new z
-__global__ void k_band_jacobi(GridDev g, GhostDev gh, int64_t nb, const int64_t *__restrict__ band,
-                              const int64_t *__restrict__ band_g, const double *__restrict__ v,
-                              const double *__restrict__ z, double omega, double *__restrict__ tmp) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nb) return;
+// one damped Jacobi pass of the full operator on the band, in precision T
+// (o: the operator of op_of<T>; the FP64 A_row reads its stored diagonal dg,
+// the FP32 one the per-axis sums): the new value of band cell q. z is read
+// through a plain pointer: the single-block form below writes it in place.
+template <typename T>
+__device__ __forceinline__ T band_value(const GridDev &g, const GhostDev &gh, const OpT<T> &o, const int64_t *band,
+                                        const int64_t *band_g, const T *v, const T *z, T omega, int64_t q) {
     const int64_t c = band[q];
     const int64_t gq = band_g[q];
-    double res, diag;
+    T res, diag;
     if (gq >= 0) {
-        double s = z[c];
-        for (int m = 0; m < 8; ++m) s -= gh.wp[8 * gq + m] * z[gh.sidx[8 * gq + m]];
+        T s = z[c];
+        for (int m = 0; m < 8; ++m) s -= o.wp[8 * gq + m] * z[gh.sidx[8 * gq + m]];
         res = v[c] - s;
-        diag = 1.0;
+        diag = T(1);
     } else {
         int i, j, k;
         split3(g, (uint32_t)c, i, j, k);
-        OpT<double> o{g.cxm, g.cxp, g.cxs, g.cym, g.cyp, g.cys, g.czm, g.czp, g.czs, g.dx, g.dy, g.dz, gh.wp};
-        res = v[c] - A_row<double>(g, o, z, c, i, j, k);
-        diag = -(g.cxs[i] + g.cys[j] + (g.ndim == 3 ? g.czs[k] : 0.0));
+        res = v[c] - A_row<T>(g, o, z, c, i, j, k);
+        if constexpr (sizeof(T) == 8) diag = -o.dg[c];
+        else diag = -(o.cxs[i] + o.cys[j] + (g.ndim == 3 ? o.czs[k] : T(0)));
     }
-    tmp[q] = z[c] + omega * res / diag;
+    return z[c] + omega * res / diag;
 }
-__global__ void k_band_scatter(int64_t nb, const int64_t *__restrict__ band, const double *__restrict__ tmp,
-                               double *__restrict__ z) {
+// tmp = the new band values (a pass over the whole band; k_band_scatter
+// then writes them into z)
+template <typename T>
+__global__ void k_band_jacobi(GridDev g, GhostDev gh, OpT<T> o, int64_t nb, const int64_t *__restrict__ band,
+                              const int64_t *__restrict__ band_g, const T *__restrict__ v, const T *__restrict__ z,
+                              T omega, T *__restrict__ tmp) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < nb) tmp[q] = band_value<T>(g, gh, o, band, band_g, v, z, omega, q);
+}
+// All sweeps in one block of BAND_BLOCK threads, for bands of at most
+// BAND_BLOCK * BAND_PER_THREAD cells: each sweep computes every new value
+// into registers, then (after a block barrier) writes them; the values
+// equal those of the two-kernel form.
+constexpr int BAND_BLOCK = 1024, BAND_PER_THREAD = 8;
+template <typename T>
+__global__ void __launch_bounds__(BAND_BLOCK)
+    k_band_block(GridDev g, GhostDev gh, OpT<T> o, int64_t nb, const int64_t *__restrict__ band,
+                 const int64_t *__restrict__ band_g, const T *__restrict__ v, T *z, T omega, int sweeps) {
+    T nv[BAND_PER_THREAD];
+    for (int s = 0; s < sweeps; ++s) {
+#pragma unroll
+        for (int u = 0; u < BAND_PER_THREAD; ++u) {
+            const int64_t q = threadIdx.x + (int64_t)u * BAND_BLOCK;
+            if (q < nb) nv[u] = band_value<T>(g, gh, o, band, band_g, v, z, omega, q);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < BAND_PER_THREAD; ++u) {
+            const int64_t q = threadIdx.x + (int64_t)u * BAND_BLOCK;
+            if (q < nb) z[band[q]] = nv[u];
+        }
+        __syncthreads();
+    }
+}
+template <typename T>
+__global__ void k_band_scatter(int64_t nb, const int64_t *__restrict__ band, const T *__restrict__ tmp,
+                               T *__restrict__ z) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q < nb) z[band[q]] = tmp[q];
 }
@@ -1872,7 +1908,7 @@ __global__ void k_level_diag(MGLevel<T> L) {
     }
 }
 
-// band: FLUID cells within two faces of a ghost cell, plus the ghosts
+// band: FLUID cells within band_width faces of a ghost cell, plus the ghosts
 __global__ void k_band_seed(int64_t n, const uint8_t *__restrict__ type, uint8_t *__restrict__ f) {
     GRID_STRIDE(c, n) f[c] = type[c] == GHOST;
 }
@@ -2103,8 +2139,10 @@ ibm_status mg_build(Ctx *c) {
     uint8_t *f0 = (uint8_t *)dev_alloc(c, c->N), *f1 = (uint8_t *)dev_alloc(c, c->N);
     if (!f0 || !f1) return c->fail(IBM_ERR_OOM, "band flag allocation failed");
     KL(-1, k_band_seed, nblk(c->N), 256, c->N, c->type, f0);
-    KL(-1, k_band_dilate, nblk(c->N), 256, c->g, c->type, f0, f1);
-    KL(-1, k_band_dilate, nblk(c->N), 256, c->g, c->type, f1, f0);
+    for (int d = 0; d < c->opts.band_width; ++d) {
+        KL(-1, k_band_dilate, nblk(c->N), 256, c->g, c->type, f0, f1);
+        std::swap(f0, f1);
+    }
     IBM_LAUNCHED(c);
     dev_free(c, c->band);
     dev_free(c, c->band_g);
@@ -2511,15 +2549,19 @@ static ibm_status precond(Ctx *c, MGHier<T> &H, const T *v, T *z) {
         KL(-1, k_pre_ghost<T>, (unsigned)((c->ng + 255) / 256), 256, c->gh, o.wp, c->type, v, z);
         IBM_LAUNCHED(c);
     }
-    if constexpr (sizeof(T) == sizeof(double)) {
-        if (c->nband > 0) {
-            const unsigned gb = (unsigned)((c->nband + 255) / 256);
-            for (int s = 0; s < c->opts.band_sweeps; ++s) {
-                KL(-1, k_band_jacobi, gb, 256, c->g, c->gh, c->nband, c->band, c->band_g, (const double *)v,
-                   (const double *)z, c->opts.band_omega, c->btmp);
-                KL(-1, k_band_scatter, gb, 256, c->nband, c->band, c->btmp, (double *)z);
-                IBM_LAUNCHED(c);
-            }
+    if (c->nband > 0 && c->opts.band_sweeps > 0 && c->nband <= (int64_t)BAND_BLOCK * BAND_PER_THREAD) {
+        KL(-1, k_band_block<T>, 1, BAND_BLOCK, c->g, c->gh, o, c->nband, c->band, c->band_g, v, z,
+           (T)c->opts.band_omega, c->opts.band_sweeps);
+        IBM_LAUNCHED(c);
+    } else if (c->nband > 0) {
+        // (btmp holds nband doubles: room for either precision)
+        const unsigned gb = (unsigned)((c->nband + 255) / 256);
+        T *tmp = reinterpret_cast<T *>(c->btmp);
+        for (int s = 0; s < c->opts.band_sweeps; ++s) {
+            KL(-1, k_band_jacobi<T>, gb, 256, c->g, c->gh, o, c->nband, c->band, c->band_g, v, (const T *)z,
+               (T)c->opts.band_omega, tmp);
+            KL(-1, k_band_scatter<T>, gb, 256, c->nband, c->band, (const T *)tmp, z);
+            IBM_LAUNCHED(c);
         }
     }
     return IBM_OK;

@@ -50,7 +50,8 @@ class ibm_solver_opts(Structure):
                 ("mixed_inner_rtol", c_double), ("mg_interp", c_int), ("tile_x", c_int), ("graph", c_int),
                 ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
                 ("smooth_omega", c_double), ("reorth_eta", c_double),
-                ("helm_check_first", c_int), ("helm_omega", c_double), ("fine_split", c_int)]
+                ("helm_check_first", c_int), ("helm_omega", c_double), ("fine_split", c_int),
+                ("band_width", c_int)]
 
 
 class ibm_table_info(Structure):

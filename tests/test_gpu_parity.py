@@ -70,14 +70,16 @@ def _poisson_case(name):
 
 
 @pytest.mark.parametrize("name", ["ellipse_ragged", "sphere_ragged"])
-@pytest.mark.parametrize("precision", [ibm.IBM_FP64, ibm.IBM_MIXED])
-def test_poisson_parity(name, precision):
+@pytest.mark.parametrize("precision,band", [(ibm.IBM_FP64, 0), (ibm.IBM_MIXED, 0), (ibm.IBM_FP64, 2)])
+def test_poisson_parity(name, precision, band):
+    """band > 0: damped Jacobi sweeps of the full operator on the cells near
+    the body after the V-cycle (FP64 preconditioner)."""
     import torch
     case, T, g = _poisson_case(name)
     rng = np.random.default_rng(7)
     b = flow.project_rhs(g, T["type"], rng.uniform(-1, 1, g.shape))
     phi_ref, _ = flow.solve_poisson(g, T["type"], T, b)
-    s = _solver(case, precision)
+    s = _solver(case, precision, band_sweeps=band)
     rhs = torch.from_numpy(rng.uniform(-1, 1, g.shape)).cuda()  # raw; FLUID mean removed inside
     rhs.copy_(torch.from_numpy(np.where(T["type"] == 0, b, 123.0)))  # non-FLUID rows must be ignored
     phi = torch.zeros(g.N, dtype=torch.float64, device="cuda")
