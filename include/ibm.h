@@ -166,6 +166,16 @@ typedef struct {
                            FLUID cells within band_width faces of one, 1..4; read
                            when the cells are classified (ibm_classify_cells,
                            ibm_move_body) */
+    int tail_cells;     /* multigrid levels below the finest with at most tail_cells
+                           cells run as one persistent launch per V-cycle (a
+                           cluster of up to 8 blocks walks their passes with
+                           hardware cluster barriers between them; same values as
+                           the per-level kernels, bit for bit); 0 = every level
+                           launched on its own, the default: on GB300 the
+                           per-level kernels replayed from CUDA graphs measured
+                           faster (2D 256x128 cylinder step 2.28 ms without the
+                           tail, 2.42-2.58 ms with it). Needs mg_interp 1 and
+                           three levels or more */
 } ibm_solver_opts;
 
 typedef struct {
@@ -228,7 +238,7 @@ enum {
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 3, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6, helm_omega 1, fine_split 1, band_width 2. */
+   helm_check_first 6, helm_omega 1, fine_split 1, band_width 2, tail_cells 0. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).
@@ -357,7 +367,8 @@ ibm_status ibm_launch_count(ibm_ctx *ctx, int64_t *count);
    level; 2 full ghost-cell pressure operator; 3 FGMRES multi-dot; 4 FGMRES
    orthogonalisation; 5 Helmholtz colour pass; 6 convective term and
    AB2/CN right-hand side; 7 red-black pass on coarse levels; 8 residual +
-   restriction; 9 prolongation; 10 every other kernel of the Poisson solver.
+   restriction; 9 prolongation; 10 every other kernel of the Poisson solver;
+   11 the persistent V-cycle tail (tail_cells).
    Recording adds host overhead per launch. */
 ibm_status ibm_kernel_timer(ibm_ctx *ctx, int enable);
 ibm_status ibm_kernel_time(ibm_ctx *ctx, int kernel, double *ms_total, int64_t *launches);

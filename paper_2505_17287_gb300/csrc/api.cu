@@ -126,6 +126,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->helm_omega = 1.0;
     o->fine_split = 1;
     o->band_width = 2;
+    o->tail_cells = 0;
     return IBM_OK;
 }
 
@@ -165,6 +166,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (!(o->smooth_omega > 0.0 && o->smooth_omega < 2.0)) { why = "smooth_omega must be in (0, 2)"; return false; }
     if (o->fine_split != 0 && o->fine_split != 1) { why = "fine_split must be 0 or 1"; return false; }
     if (o->band_width < 1 || o->band_width > 4) { why = "band_width must be in [1, 4]"; return false; }
+    if (o->tail_cells < 0) { why = "tail_cells must be >= 0"; return false; }
     if (o->inner_iters > 1 && o->smooth_omega != 1.0) { why = "smooth_omega must be 1 when inner_iters > 1"; return false; }
     return true;
 }

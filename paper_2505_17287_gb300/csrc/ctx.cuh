@@ -28,6 +28,9 @@ struct MGHier {
     // per fine level: residual scratch (level >= 1) and 1 / sum of the active
     // coarse interpolation weights of each cell (trilinear transfer)
     std::vector<T *> res, pn;
+    // per-level table of the persistent V-cycle tail (TailLv<T>[levels],
+    // device memory), null below three levels
+    void *tail = nullptr;
     bool built = false;
     // the V-cycle z = M^{-1} r (pr -> an output buffer) captured as CUDA
     // graphs, one per output buffer (pz, or a Krylov vector written in
@@ -59,7 +62,8 @@ enum KernelId {
     K_RESTRICT = 8,   // residual + restriction
     K_PROLONG = 9,    // prolongation + correction
     K_OTHER = 10,     // every other kernel of the Poisson solver
-    K_NKERNELS = 11
+    K_TAIL = 11,      // persistent V-cycle tail (the coarse levels in one launch)
+    K_NKERNELS = 12
 };
 
 // Records a CUDA event pair around every launch of the timed kernels on the

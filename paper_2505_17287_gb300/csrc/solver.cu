@@ -1644,6 +1644,216 @@ __global__ void __launch_bounds__(COARSE_MAX) k_coarse_solve(MGLevel<T> L, const
     coarse_solve_dev<T>(L, f, x, sweeps, S);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent V-cycle tail: the coarse levels in one launch
+// ---------------------------------------------------------------------------
+//
+// Below a few ten thousand cells the kernels of a level cannot fill the GPU,
+// and each still costs a launch (about twelve per level and V-cycle). The
+// tail runs the V-cycle from level l0 down to the coarsest level and back up
+// in one launch of a single thread-block cluster. Each phase of the cycle (a
+// colour pass, the residual-restriction along x, the restriction along y and
+// z, the coarsest solve, the two prolongation passes) is a list of
+// independent items (one cell, or one entry of a transfer row) that the
+// cluster's threads take in turn; consecutive phases are separated by the
+// cluster's hardware barrier (a block barrier for a one-block cluster), with
+// release/acquire ordering of the global-memory writes. Nothing spins. Every
+// item evaluates the expression of the per-level kernel it stands for, so
+// the cycle's values are those of the launched kernels.
+
+constexpr int TAIL_THREADS = 1024, TAIL_MAX_CTAS = 8;
+
+// the arrays of level l that the tail reads and writes (fixed for the life
+// of the hierarchy; the coarsest level uses L alone)
+template <typename T>
+struct TailLv {
+    MGLevel<T> L;
+    const T *pn;   // 1 / (active coarse weight sum) of the cells of l
+    T *tmp;        // transfer scratch between l and l + 1
+    Xfer<T> X;     // transfer tables between l and l + 1
+};
+
+__device__ __forceinline__ void tail_sync(int ncta) {
+    if (ncta == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+}
+
+// one colour pass (first: the first pass from x = 0, as k_rbgs_first with
+// the zeros already in place; else k_rbgs) of a coarse level
+template <typename T, bool OMEGA>
+__device__ __forceinline__ void tail_colour(const MGLevel<T> &L, int col, T w, bool first, int gt, int nt) {
+    const int np = (L.nx + 1) >> 1;
+    const int items = L.ny * L.nz * np;
+    for (int t = gt; t < items; t += nt) {
+        const int row = t / np;
+        int j, k;
+        row_jk((uint32_t)row, L.fny, L.ny, j, k);
+        const int i = 2 * (t - row * np) + ((j + k + col) & 1);
+        if (i >= L.nx) continue;
+        const int64_t c = (int64_t)row * L.nx + i;
+        if (!active<T, false>(L, c)) continue;
+        if (first) {
+            L.x[c] = OMEGA ? w * (L.f[c] * L.dinv[c]) : L.f[c] * L.dinv[c];
+        } else {
+            T d;
+            const T sm = k_offdiag<T, false>(L, L.x, c, i, j, k, d, L.f[c]);
+            L.x[c] = OMEGA ? relax(L.x[c], sm * L.dinv[c], w) : sm * L.dinv[c];
+        }
+    }
+}
+
+// the residual-restriction along x (k_resid_rx<T, false>): one item per
+// (fine row, coarse x index)
+template <typename T>
+__device__ __forceinline__ void tail_resid_rx(const TailLv<T> &A, int cnx, int zcol, int gt, int nt) {
+    const MGLevel<T> &L = A.L;
+    const int items = L.ny * L.nz * cnx;
+    for (int t = gt; t < items; t += nt) {
+        const int row = t / cnx, I = t - row * cnx;
+        int j, k;
+        row_jk((uint32_t)row, L.fny, L.ny, j, k);
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = A.X.Gx[4 * I + s];
+            if (i < 0) continue;
+            T v = T(0);
+            if (i < L.nx && !(zcol >= 0 && ((i + j + k) & 1) == zcol)) {
+                const int64_t c = (int64_t)row * L.nx + i;
+                const T p = A.pn[c];
+                if (pos(p)) {
+                    T d;
+                    const T sm = k_offdiag<T, false>(L, L.x, c, i, j, k, d, L.f[c]);
+                    v = p * (sm - d * L.x[c]);
+                }
+            }
+            acc += A.X.gwx[4 * I + s] * v;
+        }
+        A.tmp[(int64_t)row * cnx + I] = acc;
+    }
+}
+
+// the restriction along y and z into level C (k_restrict_yz)
+template <typename T>
+__device__ __forceinline__ void tail_restrict_yz(const MGLevel<T> &C, const T *tA, int fny, const Xfer<T> &X, int gt,
+                                                 int nt) {
+    const int items = C.ny * C.nz * C.nx;
+    for (int t = gt; t < items; t += nt) {
+        const int row = t / C.nx, Ic = t - row * C.nx;
+        int Jc, Kc;
+        row_jk((uint32_t)row, C.fny, C.ny, Jc, Kc);
+        const int64_t cc = (int64_t)row * C.nx + Ic;
+        C.x[cc] = T(0);
+        if (!pos(C.dinv[cc])) {
+            C.f[cc] = T(0);
+            continue;
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int s3 = 0; s3 < 4; ++s3) {
+            const int k = X.Gz[4 * Kc + s3];
+            if (k < 0) continue;
+            T a2 = T(0);
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) {
+                const int j = X.Gy[4 * Jc + s2];
+                if (j >= 0) a2 += X.gwy[4 * Jc + s2] * tA[((int64_t)k * fny + j) * C.nx + Ic];
+            }
+            acc += X.gwz[4 * Kc + s3] * a2;
+        }
+        C.f[cc] = acc;
+    }
+}
+
+// the prolongation along x from level C (k_prolong_x)
+template <typename T>
+__device__ __forceinline__ void tail_prolong_x(int fnx, const MGLevel<T> &C, const Xfer<T> &X, T *tB, int gt, int nt) {
+    const int items = C.ny * C.nz * fnx;
+    for (int t = gt; t < items; t += nt) {
+        const int row = t / fnx, i = t - row * fnx;
+        const T *xr = C.x + (int64_t)row * C.nx;
+        const int J2 = X.Jx[i];
+        T v = X.wx[i] * xr[X.Ix[i]];
+        if (J2 >= 0) v += X.vx[i] * xr[J2];
+        tB[(int64_t)row * fnx + i] = v;
+    }
+}
+
+// the prolongation along y and z and the correction of level l (k_prolong_yz)
+template <typename T>
+__device__ __forceinline__ void tail_prolong_yz(const TailLv<T> &A, int cny, int gt, int nt) {
+    const MGLevel<T> &L = A.L;
+    const Xfer<T> &X = A.X;
+    const int items = L.ny * L.nz * L.nx;
+    for (int t = gt; t < items; t += nt) {
+        const int row = t / L.nx, i = t - row * L.nx;
+        int j, k;
+        row_jk((uint32_t)row, L.fny, L.ny, j, k);
+        const int64_t c = (int64_t)row * L.nx + i;
+        int ib[2], ic[2];
+        T wb[2], wc[2];
+        const int nb = xfer_axis(X.Iy, X.Jy, X.wy, X.vy, j, ib, wb);
+        const int nc = xfer_axis(X.Iz, X.Jz, X.wz, X.vz, k, ic, wc);
+        const T p = A.pn[c];
+        if (!pos(p)) continue;
+        T acc = T(0);
+        for (int q3 = 0; q3 < nc; ++q3) {
+            T a2 = T(0);
+            for (int q2 = 0; q2 < nb; ++q2) a2 += wb[q2] * A.tmp[((int64_t)ic[q3] * cny + ib[q2]) * L.nx + i];
+            acc += wc[q3] * a2;
+        }
+        L.x[c] = L.x[c] + acc * p;
+    }
+}
+
+// The V-cycle from level l0 (its f and zeroed x written by the restriction
+// from l0 - 1) to the coarsest level nl - 1 and back, nu1 / nu2 sweeps per
+// level, cs sweep pairs on the coarsest level. One cluster of ncta blocks
+// (gridDim.x == ncta).
+template <typename T, bool OMEGA>
+__global__ void __launch_bounds__(TAIL_THREADS)
+    k_vtail(const TailLv<T> *__restrict__ A, int l0, int nl, int nu1, int nu2, int cs, T w, int ncta) {
+    __shared__ CoarseSmem<T> S;
+    const int gt = blockIdx.x * TAIL_THREADS + threadIdx.x, nt = ncta * TAIL_THREADS;
+    const int zcol = 1;   // each pre-smoothing sweep ends with colour 1
+    for (int l = l0; l < nl - 1; ++l) {
+        const TailLv<T> &F = A[l];
+        for (int s = 0; s < nu1; ++s) {
+            tail_colour<T, OMEGA>(F.L, 0, w, s == 0, gt, nt);
+            tail_sync(ncta);
+            tail_colour<T, OMEGA>(F.L, 1, w, false, gt, nt);
+            tail_sync(ncta);
+        }
+        const MGLevel<T> &C = A[l + 1].L;
+        tail_resid_rx<T>(F, C.nx, zcol, gt, nt);
+        tail_sync(ncta);
+        tail_restrict_yz<T>(C, F.tmp, F.L.ny, F.X, gt, nt);
+        tail_sync(ncta);
+    }
+    if (blockIdx.x == 0) {
+        const MGLevel<T> &C = A[nl - 1].L;
+        coarse_solve_dev<T>(C, C.f, C.x, cs, S);
+    }
+    tail_sync(ncta);
+    for (int l = nl - 2; l >= l0; --l) {
+        const TailLv<T> &F = A[l];
+        const MGLevel<T> &C = A[l + 1].L;
+        tail_prolong_x<T>(F.L.nx, C, F.X, F.tmp, gt, nt);
+        tail_sync(ncta);
+        tail_prolong_yz<T>(F, C.ny, gt, nt);
+        tail_sync(ncta);
+        for (int s = 0; s < nu2; ++s) {
+            tail_colour<T, OMEGA>(F.L, 1, w, false, gt, nt);
+            tail_sync(ncta);
+            tail_colour<T, OMEGA>(F.L, 0, w, false, gt, nt);
+            tail_sync(ncta);
+        }
+    }
+}
+
 // q = K p ; partial (p, q) in FP64
 template <typename T, bool FINE>
 __global__ void k_spmv_dot(MGLevel<T> L, const T *__restrict__ p, T *__restrict__ q, double *__restrict__ part) {
@@ -2056,6 +2266,22 @@ static ibm_status build_hier(Ctx *c, MGHier<T> &H, bool fine0) {
     H.pp = (T *)dev_alloc(c, b0);
     H.pq = (T *)dev_alloc(c, b0);
     if (!H.px || !H.pr || !H.pz || !H.pp || !H.pq) return c->fail(IBM_ERR_OOM, "PCG vector allocation failed");
+    // the persistent tail's per-level table (pointers fixed from here on)
+    if (L >= 3) {
+        std::vector<TailLv<T>> tl(L);
+        for (int l = 0; l < L; ++l) {
+            tl[l] = TailLv<T>{};
+            tl[l].L = H.lv[l];
+            if (l + 1 < L) {
+                tl[l].pn = H.pn[l];
+                tl[l].tmp = l > 0 ? H.res[l] : nullptr;
+                tl[l].X = xfer_of<T>(c, l + 1);
+            }
+        }
+        H.tail = dev_alloc(c, sizeof(TailLv<T>) * (size_t)L);
+        if (!H.tail) return c->fail(IBM_ERR_OOM, "tail table allocation failed");
+        IBM_CUDA(c, cudaMemcpy(H.tail, tl.data(), sizeof(TailLv<T>) * (size_t)L, cudaMemcpyHostToDevice));
+    }
     H.built = true;
     return IBM_OK;
 }
@@ -2236,6 +2462,52 @@ static ibm_status split_pass(Ctx *c, MGHier<float> &H, int kind, int col, const 
     return IBM_OK;
 }
 
+// First level of the persistent tail for this hierarchy and options (the
+// first level below 0 with at most tail_cells cells, if it leaves at least
+// one level to smooth above the coarsest), or -1; ncta: blocks of its cluster
+template <typename T>
+static int tail_level(const Ctx *c, const MGHier<T> &H, int *ncta) {
+    const int L = (int)H.lv.size();
+    if (c->opts.tail_cells <= 0 || c->opts.mg_interp != 1 || !H.tail || L < 3) return -1;
+    int l0 = 1;
+    while (l0 < L && H.lv[l0].n > c->opts.tail_cells) ++l0;
+    if (l0 > L - 2) return -1;
+    const int64_t per = 2 * (int64_t)TAIL_THREADS;
+    *ncta = (int)std::min<int64_t>(TAIL_MAX_CTAS, std::max<int64_t>(1, (H.lv[l0].n + per - 1) / per));
+    return l0;
+}
+
+template <typename T>
+static ibm_status launch_tail(Ctx *c, MGHier<T> &H, int l0, int ncta) {
+    const int L = (int)H.lv.size();
+    const TailLv<T> *A = reinterpret_cast<const TailLv<T> *>(H.tail);
+    const int nu1 = c->opts.nu1, nu2 = c->opts.nu2, cs = c->opts.coarse_sweeps;
+    const double w = c->opts.smooth_omega;
+    auto kern = w != 1.0 ? k_vtail<T, true> : k_vtail<T, false>;
+    kt_begin(c, K_TAIL);
+    ++c->nlaunch;
+    if (ncta == 1) {
+        kern<<<1, TAIL_THREADS, 0, c->s>>>(A, l0, L, nu1, nu2, cs, (T)w, 1);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)ncta, 1, 1);
+        cfg.blockDim = dim3(TAIL_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = c->s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)ncta;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        IBM_CUDA(c, cudaLaunchKernelEx(&cfg, kern, A, l0, L, nu1, nu2, cs, (T)w, ncta));
+    }
+    kt_end(c, K_TAIL);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
 template <typename T>
 static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     const int L = (int)H.lv.size();
@@ -2250,7 +2522,12 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     // levels' x is cleared by the restriction)
     if (nu1 < 1) IBM_CUDA(c, cudaMemsetAsync(x0, 0, sizeof(T) * (size_t)c->N, c->s));
     const bool sp = split_on(c, H);
-    for (int l = 0; l < L - 1; ++l) {
+    // levels lt .. L - 1 in one persistent launch (lt = L - 1: the coarsest
+    // solve alone)
+    int ncta = 1;
+    const int l0 = tail_level(c, H, &ncta);
+    const int lt = l0 > 0 ? l0 : L - 1;
+    for (int l = 0; l < lt; ++l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         if constexpr (sizeof(T) == 4) {
@@ -2307,9 +2584,13 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
         }
         IBM_LAUNCHED(c);
     }
-    KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
-    IBM_LAUNCHED(c);
-    for (int l = L - 2; l >= 0; --l) {
+    if (l0 > 0) {
+        IBM_TRY(launch_tail(c, H, l0, ncta));
+    } else {
+        KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[L - 1], H.lv[L - 1].f, H.lv[L - 1].x, cs);
+        IBM_LAUNCHED(c);
+    }
+    for (int l = lt - 1; l >= 0; --l) {
         const T *f = l == 0 ? f0 : H.lv[l].f;
         T *x = l == 0 ? x0 : H.lv[l].x;
         MGLevel<T> &Lf = H.lv[l];
@@ -2362,9 +2643,9 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
 template <typename T>
 static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H, T *out) {
     const ibm_solver_opts &o = c->opts;
-    const uint64_t key = ((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
+    const uint64_t key = (((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
                            (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 4 + (uint64_t)o.mg_interp * 2 +
-                         (uint64_t)o.fine_split + 1;
+                         (uint64_t)o.fine_split) * 1000003 + (uint64_t)o.tail_cells + 1;
     auto drop_all = [&]() -> ibm_status {
         IBM_CUDA(c, cudaStreamSynchronize(c->s));
         for (int i = 0; i < MGHier<T>::NVG; ++i) {

@@ -51,7 +51,7 @@ class ibm_solver_opts(Structure):
                 ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
                 ("smooth_omega", c_double), ("reorth_eta", c_double),
                 ("helm_check_first", c_int), ("helm_omega", c_double), ("fine_split", c_int),
-                ("band_width", c_int)]
+                ("band_width", c_int), ("tail_cells", c_int)]
 
 
 class ibm_table_info(Structure):
@@ -256,7 +256,7 @@ def ibm_launch_count(ctx):
 
 
 KERNEL_IDS = {"rbgs0": 0, "spmv0": 1, "apply_A": 2, "mdot": 3, "orth": 4, "helm": 5, "conv": 6,
-              "rbgs_coarse": 7, "restrict": 8, "prolong": 9, "other": 10}
+              "rbgs_coarse": 7, "restrict": 8, "prolong": 9, "other": 10, "tail": 11}
 
 
 def ibm_kernel_timer(ctx, enable: int):
