@@ -43,10 +43,13 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 METRIC = "Mcell-steps/s per GB300, mixed vs FP64 at 1e-10 residual; serve p50/p99 latency"
 UNIT = "Mcell-steps/s"
 
-# DRAM traffic per launch of the roofline kernel, from ncu captures of a
-# smaller case scaled by the cell count, keyed by (kernel, precision); valid
-# for the kernel as captured (None when the kernel changed since)
-TRAFFIC_BYTES_PER_CELL = {}
+# DRAM traffic per launch of the roofline kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch, per cell), keyed by (kernel, precision);
+# valid for the kernel as captured (removed when the kernel changes). The split
+# colour pass: a one-pass capture at 201,326,592 cells, 906.7 MB read and
+# 377.1 MB written per launch.
+SPLIT_PASS = "k_rbgs_split (finest FP32 level in colour-split storage, one colour pass)"
+TRAFFIC_BYTES_PER_CELL = {(SPLIT_PASS, 4): (906.67e6 + 377.14e6) / 201326592}
 
 
 def pass_bytes(ncells, s):
@@ -586,9 +589,8 @@ def main():
     # mixed precision with nx a multiple of 8: the finest FP32 level in
     # colour-split storage (one colour pass streams the other colour's x)
     split = mixed_main and N % 8 == 0 and int(args.size.split(",")[0]) % 8 == 0
-    kname = ("k_rbgs_split (finest FP32 level in colour-split storage" if split else
-             "k_rbgs<float, fine> (finest level" if mixed_main else "k_rbgs<double> (finest level") + \
-        ", one colour pass)"
+    kname = SPLIT_PASS if split else \
+        ("k_rbgs<float, fine>" if mixed_main else "k_rbgs<double>") + " (finest level, one colour pass)"
     tpc = TRAFFIC_BYTES_PER_CELL.get((kname, sz))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

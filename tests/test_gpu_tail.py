@@ -52,8 +52,10 @@ def test_tail_equals_per_level_launches(precision, which, opts, tail):
 
 @pytest.mark.parametrize("precision", [ibm.IBM_FP64, ibm.IBM_MIXED])
 def test_tail_poisson_matches_oracle(precision):
+    """A 24^3 sphere case: levels of 13824, 1728 and 216 cells, the last two in
+    the tail (small enough for the oracle's direct 3D solve)."""
     import torch
-    case = synth.wing_case(64, 48, 40, n_chord=30, n_span=10)
+    case = synth.sphere_case(n=24, radius=0.45, level=3)
     T = geom.body_tables(case.ndim, case.xf, case.yf, case.zf, case.verts, case.elems)
     g = flow.Grid(case.ndim, case.xf, case.yf, case.zf)
     rng = np.random.default_rng(17)
