@@ -110,7 +110,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->ghost_maxit = 100;
     o->precision = IBM_FP64;
     o->outer = IBM_OUTER_FGMRES;
-    o->band_sweeps = 3;
+    o->band_sweeps = 6;
     o->band_omega = 0.85;
     o->mixed_inner_rtol = 1e-4;
     o->mg_interp = 1;
@@ -125,7 +125,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->helm_check_first = 6;
     o->helm_omega = 1.0;
     o->fine_split = 1;
-    o->band_width = 2;
+    o->band_width = 3;
     o->tail_cells = 0;
     return IBM_OK;
 }
