@@ -149,8 +149,10 @@ typedef struct {
                            test, >= 1; later tests follow at s + max(2, s / 4) sweeps
                            (s the sweep count of the previous test), so that a solve
                            needing n sweeps takes O(log n) tests. Each test costs
-                           about one and a half sweeps in FP64; default 6, the count
-                           the 3D wing's components need at helm_rtol 1e-12 */
+                           about two sweeps in FP64; default 6, the count the 3D
+                           wing's components need at helm_rtol 1e-12 on its
+                           201M-cell grid (4 on the 25.2M-cell grid, where 4
+                           saves 4% of the step) */
     double helm_omega;  /* Helmholtz red-black relaxation factor: 0 = automatic,
                            2 / (1 + sqrt(1 - rho^2)) with rho the grid's bound on the
                            Jacobi spectral radius (Young's optimum for a red-black
