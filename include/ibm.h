@@ -168,6 +168,19 @@ typedef struct {
                            FLUID cells within band_width faces of one, 1..4; read
                            when the cells are classified (ibm_classify_cells,
                            ibm_move_body) */
+    int poisson_hist;   /* pairs (solution, projected right-hand side) of earlier
+                           pressure solves kept on the device, 0..16: each step
+                           starts its Poisson solve from the combination of the
+                           stored solutions whose right-hand sides best fit the
+                           new one in the least-squares sense (a projection onto
+                           earlier solutions, which contains the polynomial
+                           extrapolation of the last pressures); 0 = the
+                           extrapolation alone. Cleared by ibm_classify_cells and
+                           ibm_move_body (the operator changes), kept by
+                           ibm_set_field (the pairs stay solutions of the same
+                           operator); a checkpoint that must restart bit for bit
+                           saves IBM_FIELD_P_HIST_*. Costs 16 bytes per cell and
+                           pair */
     int tail_cells;     /* multigrid levels below the finest with at most tail_cells
                            cells run as one persistent launch per V-cycle (a
                            cluster of up to 8 blocks walks their passes with
@@ -228,11 +241,17 @@ enum {
     IBM_FIELD_RHS = 14,                                   /* last Poisson right-hand side, N */
     IBM_FIELD_STEP = 15,                                  /* int64 step counter, 1 value */
     IBM_FIELD_P_PREV = 16,                                /* pressure of the step before, N */
-    IBM_FIELD_P_PREV2 = 17                                /* pressure two steps before, N. The Poisson
+    IBM_FIELD_P_PREV2 = 17,                               /* pressure two steps before, N. The Poisson
                                                              initial guess is P on the first three
                                                              steps, 2 P - P_PREV on the fourth, then
                                                              3 P - 3 P_PREV + P_PREV2 (both are part
-                                                             of a checkpoint) */
+                                                             of a checkpoint), unless the guess
+                                                             history (poisson_hist) holds a pair */
+    IBM_FIELD_P_HIST_X = 18,   /* Poisson guess history (poisson_hist > 0): the stored
+                                  solutions, poisson_hist x N doubles (slot-major) */
+    IBM_FIELD_P_HIST_B = 19,   /* their projected right-hand sides, poisson_hist x N */
+    IBM_FIELD_P_HIST_CTL = 20  /* pairs held, next slot and the Gram matrix of the
+                                  stored right-hand sides: 2 + poisson_hist^2 doubles */
 };
 
 /* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
@@ -240,7 +259,7 @@ enum {
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 6, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6, helm_omega 1, fine_split 1, band_width 3, tail_cells 0. */
+   helm_check_first 6, helm_omega 1, fine_split 1, band_width 3, poisson_hist 8, tail_cells 0. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -95,7 +95,9 @@ typedef struct {
 } ibm_server_stats;
 
 /* Device footprint estimate of one case (bytes), an upper bound on what the
-   library allocates for that grid, precision and total body element count. */
+   library allocates for that grid, precision and total body element count
+   with the default options (a Poisson guess history of 8 pairs; the server
+   adds the difference for a request whose options keep more). */
 size_t ibm_case_bytes(int ndim, int nx, int ny, int nz, int precision, int64_t nelems_total);
 
 /* Start the slots' worker threads on opts->device. IBM_ERR_ARG for a bad

@@ -9,6 +9,7 @@
 #include <map>
 #include <new>
 #include <utility>
+#include <vector>
 
 using namespace ibm;
 
@@ -126,6 +127,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->helm_omega = 1.0;
     o->fine_split = 1;
     o->band_width = 3;
+    o->poisson_hist = 8;
     o->tail_cells = 0;
     return IBM_OK;
 }
@@ -167,6 +169,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->fine_split != 0 && o->fine_split != 1) { why = "fine_split must be 0 or 1"; return false; }
     if (o->band_width < 1 || o->band_width > 4) { why = "band_width must be in [1, 4]"; return false; }
     if (o->tail_cells < 0) { why = "tail_cells must be >= 0"; return false; }
+    if (o->poisson_hist < 0 || o->poisson_hist > 16) { why = "poisson_hist must be in [0, 16]"; return false; }
     if (o->inner_iters > 1 && o->smooth_omega != 1.0) { why = "smooth_omega must be 1 when inner_iters > 1"; return false; }
     return true;
 }
@@ -823,6 +826,12 @@ static ibm_status field_ptr(Ctx *c, int field, void **p, size_t *bytes) {
     case IBM_FIELD_RHS: *p = c->b; *bytes = nb; return IBM_OK;
     case IBM_FIELD_P_PREV: *p = c->p_prev; *bytes = nb; return IBM_OK;
     case IBM_FIELD_P_PREV2: *p = c->p_prev2; *bytes = nb; return IBM_OK;
+    case IBM_FIELD_P_HIST_X: case IBM_FIELD_P_HIST_B:
+        if (c->opts.poisson_hist <= 0) return c->fail(IBM_ERR_ARG, "the Poisson guess history is off (poisson_hist 0)");
+        IBM_TRY(hist_prepare(c));
+        *p = field == IBM_FIELD_P_HIST_X ? c->hist_x : c->hist_b;
+        *bytes = nb * (size_t)c->opts.poisson_hist;
+        return IBM_OK;
     default: return c->fail(IBM_ERR_ARG, "unknown field id");
     }
 }
@@ -866,8 +875,42 @@ static ibm_status host_copy(Ctx *c, void *dst, const void *src, size_t nb, bool 
     return IBM_OK;
 }
 
+// the guess history's control values as doubles: pairs held, next slot,
+// the Gram matrix (poisson_hist^2, row-major)
+static ibm_status hist_ctl_io(Ctx *c, void *buf, int is_device, size_t bytes, bool to_ctx) {
+    const int L = c->opts.poisson_hist;
+    if (L <= 0) return c->fail(IBM_ERR_ARG, "the Poisson guess history is off (poisson_hist 0)");
+    if (bytes != sizeof(double) * (size_t)(2 + L * L)) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
+    IBM_TRY(hist_prepare(c));
+    HistCtl h{};
+    IBM_CUDA(c, cudaMemcpyAsync(&h, c->hist_ctl, sizeof(HistCtl), cudaMemcpyDeviceToHost, c->s));
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    std::vector<double> v((size_t)(2 + L * L));
+    if (to_ctx) {
+        if (is_device) IBM_CUDA(c, cudaMemcpy(v.data(), buf, bytes, cudaMemcpyDeviceToHost));
+        else memcpy(v.data(), buf, bytes);
+        if (!(v[0] >= 0 && v[0] <= L && v[1] >= 0 && v[1] < L && v[0] == (int)v[0] && v[1] == (int)v[1]))
+            return c->fail(IBM_ERR_ARG, "history control values out of range");
+        h.count = (int)v[0];
+        h.slot = (int)v[1];
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) h.G[i * HIST_MAX + j] = v[2 + (size_t)i * L + j];
+        IBM_CUDA(c, cudaMemcpyAsync(c->hist_ctl, &h, sizeof(HistCtl), cudaMemcpyHostToDevice, c->s));
+        IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    } else {
+        v[0] = h.count;
+        v[1] = h.slot;
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) v[2 + (size_t)i * L + j] = h.G[i * HIST_MAX + j];
+        if (is_device) IBM_CUDA(c, cudaMemcpy(buf, v.data(), bytes, cudaMemcpyHostToDevice));
+        else memcpy(buf, v.data(), bytes);
+    }
+    return IBM_OK;
+}
+
 extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_device, size_t bytes) {
     if (!c || !dst) return IBM_ERR_ARG;
+    if (field == IBM_FIELD_P_HIST_CTL) return hist_ctl_io(c, dst, is_device, bytes, false);
     if (field == IBM_FIELD_STEP) {
         if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
         int64_t v = c->nstep + (c->have_nold ? 0 : 0);
@@ -887,6 +930,7 @@ extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_dev
 
 extern "C" ibm_status ibm_set_field(ibm_ctx *c, int field, const void *src, int is_device, size_t bytes) {
     if (!c || !src) return IBM_ERR_ARG;
+    if (field == IBM_FIELD_P_HIST_CTL) return hist_ctl_io(c, const_cast<void *>(src), is_device, bytes, true);
     if (field == IBM_FIELD_STEP) {
         if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
         int64_t v = 0;

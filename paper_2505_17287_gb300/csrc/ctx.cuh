@@ -5,6 +5,18 @@
 
 namespace ibm {
 
+// device control block of the Poisson guess history (solver.cu): pairs in
+// the ring, next slot, Gram matrix of the stored right-hand sides, this
+// step's dots and coefficients, and the FLUID mean of its right-hand side
+constexpr int HIST_MAX = 16;
+struct HistCtl {
+    int count, slot;
+    double G[HIST_MAX * HIST_MAX];
+    double d[HIST_MAX + 1];
+    double c[HIST_MAX];
+    double mean;
+};
+
 template <typename T>
 struct MGHier {
     std::vector<MGLevel<T>> lv;
@@ -158,6 +170,11 @@ struct Ctx {
     float **Vdev32 = nullptr, **Zdev32 = nullptr;
     float *w32 = nullptr, *r32 = nullptr, *d32 = nullptr, *b32 = nullptr;
     int m32_cap = 0;
+    // Poisson guess history: hist_cap pairs of N doubles (solutions, projected
+    // right-hand sides), this step's projected right-hand side, HistCtl
+    int hist_cap = 0, hist_len = 0;   // allocated pairs; pair count of the history held
+    double *hist_x = nullptr, *hist_b = nullptr, *hist_bp = nullptr;
+    void *hist_ctl = nullptr;
     // near-body band for the preconditioner's local relaxation
     int64_t nband = 0;
     int64_t *band = nullptr;      // cell index
@@ -229,6 +246,13 @@ ibm_status kt_flush(Ctx *c);
 
 // solver.cu
 ibm_status mg_build(Ctx *c);
+// Poisson guess history (solver.cu): storage, reset, the projection guess
+// for a right-hand side (after the extrapolated guess is in phi), and the
+// pair of a finished solve
+ibm_status hist_prepare(Ctx *c);
+ibm_status hist_reset(Ctx *c);
+ibm_status hist_guess(Ctx *c, const double *rhs, double *phi);
+ibm_status hist_store(Ctx *c, const double *phi);
 ibm_status poisson_solve(Ctx *c, const double *rhs, double *phi, double rtol, int maxit,
                          ibm_solve_stats *st);
 ibm_status fluid_mean(Ctx *c, const double *x, bool ghosts_too, double *mean_host);

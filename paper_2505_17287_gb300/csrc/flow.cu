@@ -850,6 +850,7 @@ static ibm_status helmholtz(Ctx *c, int q, int *sweeps) {
 ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     const int nc = c->ndim;
     const double dt = c->desc.dt, alpha = dt / (2.0 * c->desc.Re);
+    IBM_TRY(hist_prepare(c));
     IBM_CUDA(c, cudaEventRecord(c->ev0, c->s));
     CFields3 u{{c->u[0], c->u[1], nc == 3 ? c->u[2] : c->u[1]}};
     CFields3 F{{c->F[0], c->F[1], nc == 3 ? c->F[2] : c->F[1]}};
@@ -878,11 +879,13 @@ ibm_status flow_step(Ctx *c, ibm_step_stats *st) {
     IBM_LAUNCHED(c);
     ++c->nlaunch, k_phi_guess<<<c->nelem, 256, 0, c->s>>>(c->N, c->p, c->p_prev, c->p_prev2, phi_order(c));
     IBM_LAUNCHED(c);
+    IBM_TRY(hist_guess(c, braw, c->p));
     IBM_CUDA(c, cudaEventRecord(c->ev2, c->s));
     ibm_solve_stats ps{};
     ibm_status s = poisson_solve(c, braw, c->p, c->opts.rtol, c->opts.max_outer, &ps);
     if (s == IBM_ERR_NOT_CONVERGED) status = s;
     else if (s != IBM_OK) return s;
+    IBM_TRY(hist_store(c, c->p));
     IBM_CUDA(c, cudaEventRecord(c->ev3, c->s));
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
@@ -1264,7 +1267,9 @@ static ibm_status flow_step_capture(Ctx *c) {
     IBM_LAUNCHED(c);
     ++c->nlaunch, k_phi_guess<<<c->nelem, 256, 0, c->s>>>(c->N, c->p, c->p_prev, c->p_prev2, phi_order(c));
     IBM_LAUNCHED(c);
+    IBM_TRY(hist_guess(c, braw, c->p));
     IBM_TRY(poisson_solve_dev(c, braw, c->p, c->opts.rtol, c->opts.max_outer));
+    IBM_TRY(hist_store(c, c->p));
     for (int a = 0; a < nc; ++a) {
         const int64_t nf = a == 0 ? c->NFx : (a == 1 ? c->NFy : c->NFz);
         const unsigned nb = (unsigned)((nf + 255) / 256 > 152 * 32 ? 152 * 32 : (nf + 255) / 256);
@@ -1306,6 +1311,7 @@ static uint64_t graph_key(Ctx *c) {
 static ibm_status capture_step(Ctx *c, cudaGraphExec_t *out) {
     IBM_TRY(helm_prepare(c));
     IBM_TRY(poisson_dev_prepare(c));
+    IBM_TRY(hist_prepare(c));
     if (!c->hctl) {
         c->hctl = dev_alloc(c, sizeof(HelmCtl));
         if (!c->hctl) return c->fail(IBM_ERR_OOM, "control block allocation failed");

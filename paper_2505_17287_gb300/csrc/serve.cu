@@ -278,6 +278,7 @@ extern "C" size_t ibm_case_bytes(int ndim, int nx, int ny, int nz, int precision
         per_cell += 33 * 4 + 60 * coarse + 48;  // FP32 basis, FP32 hierarchy, FP32 operator
     else
         per_cell += 33 * 8 + 90 * coarse;       // FP64 basis and hierarchy
+    per_cell += 8 + 16 * 8;                   // Poisson guess history, default 8 pairs
     const double body = 256.0 * (double)nelems_total;
     return (size_t)(1.25 * (per_cell * n + body)) + ((size_t)64 << 20);
 }
@@ -375,6 +376,8 @@ extern "C" ibm_status ibm_server_submit(ibm_server *s, const ibm_request *r, int
     q->r.rhs = nullptr;
     const int prec = q->has_opts ? q->opts.precision : g.precision;
     q->est = ibm_case_bytes(g.ndim, g.nx, g.ny, nz, prec, ne_total);
+    if (q->has_opts && q->opts.poisson_hist > 8)   // a longer guess history than the estimate's 8 pairs
+        q->est += (size_t)(1.25 * 16.0 * (q->opts.poisson_hist - 8) * (double)N);
     q->res.bytes_estimate = q->est;
     q->res.cells = N;
     {

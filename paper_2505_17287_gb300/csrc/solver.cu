@@ -2331,6 +2331,7 @@ ibm_status compact_flags(Ctx *c, const uint8_t *flags, int64_t **out, int64_t *c
 ibm_status mg_build(Ctx *c) {
     const int L = (int)c->lg.size();
     ++c->mg_gen;
+    IBM_TRY(hist_reset(c));
     std::vector<double *> ox(L), oy(L), oz(L);
     for (int l = 0; l < L; ++l) {
         const int64_t n = (int64_t)c->lg[l].nx * c->lg[l].ny * c->lg[l].nz;
@@ -3675,6 +3676,176 @@ ibm_status step_stats_read(Ctx *c, ibm_step_stats *st) {
         c->fail(IBM_ERR_NOT_CONVERGED, "a solve in the step reached its iteration limit");
         return IBM_ERR_NOT_CONVERGED;
     }
+    return IBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Poisson initial guess from earlier solves (least-squares projection)
+// ---------------------------------------------------------------------------
+//
+// The pressure operator of a body at rest is the same at every step, so the
+// solutions x_i of the last L steps and their projected right-hand sides
+// b_i = P rhs_i are pairs with A x_i = b_i (to the solve tolerance). For a
+// new right-hand side b the guess x0 = sum c_i x_i with c minimising
+// || P b - sum c_i b_i ||_2 leaves that least-squares residual (Fischer's
+// projection onto earlier solutions, 1998); it contains the polynomial
+// extrapolation of the last pressures. The pairs sit in a ring of L slots;
+// the Gram matrix G_ij = (b_i, b_j) is updated as a pair enters (its dots
+// are the ones the guess of that step computed), and the normal equations
+// (G + eps I) c = (b_i, P b) are solved by Cholesky in one thread. All of it
+// runs on the device, so the captured step graph holds it as well.
+
+template <typename T>
+static inline const MdotFn<T> *mdot_fns() {
+    return mdot_table<T>(std::make_integer_sequence<int, 17>());
+}
+
+// rhs - mean on FLUID cells, 0 elsewhere (the solver's P rhs)
+__global__ void k_hist_bp(int64_t n, const uint8_t *__restrict__ type, const double *__restrict__ rhs,
+                          const HistCtl *__restrict__ H, double *__restrict__ bp) {
+    const double m = H->mean;
+    GRID_STRIDE(c, n) bp[c] = type[c] == FLUID ? rhs[c] - m : 0.0;
+}
+
+// c over the m active slots (0 elsewhere, and everywhere if the factorisation
+// meets a non-positive pivot)
+__global__ void k_hist_solve(HistCtl *H, int L) {
+    const int m = H->count;
+    for (int i = 0; i < HIST_MAX; ++i) H->c[i] = 0.0;
+    if (m == 0) return;
+    double a[HIST_MAX * HIST_MAX], y[HIST_MAX];
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) dmax = fmax(dmax, H->G[i * HIST_MAX + i]);
+    if (!(dmax > 0.0)) return;
+    const double eps = 1e-12 * dmax;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) a[i * HIST_MAX + j] = H->G[i * HIST_MAX + j] + (i == j ? eps : 0.0);
+    // Cholesky a = R^T R (upper R in place)
+    for (int k = 0; k < m; ++k) {
+        double piv = a[k * HIST_MAX + k];
+        for (int q = 0; q < k; ++q) piv -= a[q * HIST_MAX + k] * a[q * HIST_MAX + k];
+        if (!(piv > 0.0)) return;
+        const double r = sqrt(piv);
+        a[k * HIST_MAX + k] = r;
+        for (int j = k + 1; j < m; ++j) {
+            double v = a[k * HIST_MAX + j];
+            for (int q = 0; q < k; ++q) v -= a[q * HIST_MAX + k] * a[q * HIST_MAX + j];
+            a[k * HIST_MAX + j] = v / r;
+        }
+    }
+    for (int i = 0; i < m; ++i) {   // R^T y = d
+        double v = H->d[i];
+        for (int q = 0; q < i; ++q) v -= a[q * HIST_MAX + i] * y[q];
+        y[i] = v / a[i * HIST_MAX + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {   // R c = y
+        double v = y[i];
+        for (int q = i + 1; q < m; ++q) v -= a[i * HIST_MAX + q] * H->c[q];
+        H->c[i] = v / a[i * HIST_MAX + i];
+    }
+    (void)L;
+}
+
+// phi = sum over the active slots of c_i X_i (phi untouched with no pairs)
+__global__ void k_hist_guess(int64_t n, const HistCtl *__restrict__ H, const double *__restrict__ X,
+                             double *__restrict__ phi) {
+    const int m = H->count;
+    if (m == 0) return;
+    GRID_STRIDE(c, n) {
+        double v = 0.0;
+        for (int i = 0; i < m; ++i) v += H->c[i] * X[(int64_t)i * n + c];
+        phi[c] = v;
+    }
+}
+
+// the pair of this step into the current slot
+__global__ void k_hist_insert(int64_t n, const HistCtl *__restrict__ H, const double *__restrict__ phi,
+                              const double *__restrict__ bp, double *__restrict__ X, double *__restrict__ B) {
+    const int64_t off = (int64_t)H->slot * n;
+    GRID_STRIDE(c, n) {
+        X[off + c] = phi[c];
+        B[off + c] = bp[c];
+    }
+}
+
+// Gram row and column of the new pair; advance the ring
+__global__ void k_hist_advance(HistCtl *H, int L) {
+    const int k = H->slot;
+    for (int i = 0; i < L; ++i) {
+        if (i == k) continue;
+        H->G[k * HIST_MAX + i] = H->d[i];
+        H->G[i * HIST_MAX + k] = H->d[i];
+    }
+    H->G[k * HIST_MAX + k] = H->d[L];
+    H->slot = (k + 1) % L;
+    H->count = H->count < L ? H->count + 1 : L;
+}
+
+// ring storage for opts.poisson_hist pairs (allocated outside any capture;
+// a new size starts an empty history)
+ibm_status hist_prepare(Ctx *c) {
+    const int L = c->opts.poisson_hist;
+    if (L <= c->hist_cap) {
+        // a history kept for another pair count starts over
+        if (L != c->hist_len) {
+            IBM_TRY(hist_reset(c));
+            c->hist_len = L;
+        }
+        return IBM_OK;
+    }
+    dev_free(c, c->hist_x);
+    dev_free(c, c->hist_b);
+    c->hist_x = c->hist_b = nullptr;
+    c->hist_cap = 0;
+    const size_t nb = sizeof(double) * (size_t)c->N * (size_t)L;
+    c->hist_x = (double *)dev_alloc(c, nb);
+    c->hist_b = (double *)dev_alloc(c, nb);
+    if (!c->hist_bp) c->hist_bp = (double *)dev_alloc(c, sizeof(double) * (size_t)c->N);
+    if (!c->hist_ctl) c->hist_ctl = dev_alloc(c, sizeof(HistCtl));
+    if (!c->hist_x || !c->hist_b || !c->hist_bp || !c->hist_ctl) return c->fail(IBM_ERR_OOM, "Poisson history allocation failed");
+    // zero vectors: the dots of unused slots are 0
+    IBM_CUDA(c, cudaMemsetAsync(c->hist_b, 0, nb, c->s));
+    IBM_CUDA(c, cudaMemsetAsync(c->hist_x, 0, nb, c->s));
+    IBM_CUDA(c, cudaMemsetAsync(c->hist_ctl, 0, sizeof(HistCtl), c->s));
+    c->hist_cap = L;
+    c->hist_len = L;
+    return IBM_OK;
+}
+
+// forget the pairs (the operator changed)
+ibm_status hist_reset(Ctx *c) {
+    if (c->hist_ctl) IBM_CUDA(c, cudaMemsetAsync(c->hist_ctl, 0, sizeof(HistCtl), c->s));
+    return IBM_OK;
+}
+
+// phi = the projection guess for rhs, if the history holds a pair
+ibm_status hist_guess(Ctx *c, const double *rhs, double *phi) {
+    const int L = c->opts.poisson_hist;
+    if (L <= 0) return IBM_OK;
+    if (L > c->hist_cap || L != c->hist_len) return c->fail(IBM_ERR_STATE, "Poisson history not prepared");
+    HistCtl *H = reinterpret_cast<HistCtl *>(c->hist_ctl);
+    KL(-1, k_fluid_volsum, c->nred, RED_THREADS, c->g, c->type, rhs, c->part);
+    IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, &H->mean));
+    KL(-1, k_hist_bp, c->nelem, 256, c->N, c->type, rhs, H, c->hist_bp);
+    VPtrs<double> vp{};
+    for (int i = 0; i < L; ++i) vp.p[i] = c->hist_b + (size_t)i * c->N;
+    vp.p[L] = c->hist_bp;
+    KL(-1, mdot_fns<double>()[L], mdot_blocks<double>(c), RED_THREADS, c->N, c->hist_bp, vp, c->part);
+    IBM_TRY(finalize(c, c->part, mdot_blocks<double>(c), L + 1, 1.0, H->d));
+    KL(-1, k_hist_solve, 1, 1, H, L);
+    KL(-1, k_hist_guess, c->nelem, 256, c->N, H, c->hist_x, phi);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
+}
+
+// this step's pair (phi the solution of hist_guess's right-hand side)
+ibm_status hist_store(Ctx *c, const double *phi) {
+    const int L = c->opts.poisson_hist;
+    if (L <= 0) return IBM_OK;
+    HistCtl *H = reinterpret_cast<HistCtl *>(c->hist_ctl);
+    KL(-1, k_hist_insert, c->nelem, 256, c->N, H, phi, c->hist_bp, c->hist_x, c->hist_b);
+    KL(-1, k_hist_advance, 1, 1, H, L);
+    IBM_LAUNCHED(c);
     return IBM_OK;
 }
 

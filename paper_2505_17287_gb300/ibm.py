@@ -28,7 +28,7 @@ IBM_FP64, IBM_MIXED = 0, 1
 IBM_OUTER_BICGSTAB, IBM_OUTER_FGMRES = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "p": 3, "face_u": 4, "face_v": 5, "face_w": 6, "nold_u": 7, "nold_v": 8,
           "nold_w": 9, "type": 10, "ustar_u": 11, "ustar_v": 12, "ustar_w": 13, "rhs": 14, "step": 15,
-          "p_prev": 16, "p_prev2": 17}
+          "p_prev": 16, "p_prev2": 17, "p_hist_x": 18, "p_hist_b": 19, "p_hist_ctl": 20}
 
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p)
 FREE_FN = CFUNCTYPE(None, c_void_p, c_void_p)
@@ -51,7 +51,7 @@ class ibm_solver_opts(Structure):
                 ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
                 ("smooth_omega", c_double), ("reorth_eta", c_double),
                 ("helm_check_first", c_int), ("helm_omega", c_double), ("fine_split", c_int),
-                ("band_width", c_int), ("tail_cells", c_int)]
+                ("band_width", c_int), ("poisson_hist", c_int), ("tail_cells", c_int)]
 
 
 class ibm_table_info(Structure):
@@ -411,8 +411,16 @@ class Solver:
         t["type"] = t["type"].reshape(self.shape)
         return t
 
+    def hist_pairs(self):
+        o = getattr(self, "_opts", None) or ibm_default_opts()
+        return int(o.poisson_hist)
+
     def field_size(self, name):
         nz, ny, nx = self.shape
+        if name in ("p_hist_x", "p_hist_b"):
+            return (self.hist_pairs(),) + self.shape
+        if name == "p_hist_ctl":
+            return (2 + self.hist_pairs() ** 2,)
         if name == "face_u":
             return (nz, ny, nx + 1)
         if name == "face_v":
@@ -439,9 +447,13 @@ class Solver:
         return ibm_set_field(self.ctx, FIELDS[name], a.ctypes.data, 0, a.nbytes)
 
     def state_names(self):
+        """Fields of a checkpoint that restarts bit for bit (the Poisson guess
+        history included when it is on)."""
         names = ["u", "v", "p", "p_prev", "p_prev2", "face_u", "face_v", "nold_u", "nold_v"]
         if self.ndim == 3:
             names += ["w", "face_w", "nold_w"]
+        if self.hist_pairs() > 0:
+            names += ["p_hist_x", "p_hist_b", "p_hist_ctl"]
         return names + ["step"]
 
     def get_state(self):
