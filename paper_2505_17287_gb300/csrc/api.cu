@@ -826,12 +826,6 @@ static ibm_status field_ptr(Ctx *c, int field, void **p, size_t *bytes) {
     case IBM_FIELD_RHS: *p = c->b; *bytes = nb; return IBM_OK;
     case IBM_FIELD_P_PREV: *p = c->p_prev; *bytes = nb; return IBM_OK;
     case IBM_FIELD_P_PREV2: *p = c->p_prev2; *bytes = nb; return IBM_OK;
-    case IBM_FIELD_P_HIST_X: case IBM_FIELD_P_HIST_B:
-        if (c->opts.poisson_hist <= 0) return c->fail(IBM_ERR_ARG, "the Poisson guess history is off (poisson_hist 0)");
-        IBM_TRY(hist_prepare(c));
-        *p = field == IBM_FIELD_P_HIST_X ? c->hist_x : c->hist_b;
-        *bytes = nb * (size_t)c->opts.poisson_hist;
-        return IBM_OK;
     default: return c->fail(IBM_ERR_ARG, "unknown field id");
     }
 }
@@ -875,6 +869,31 @@ static ibm_status host_copy(Ctx *c, void *dst, const void *src, size_t nb, bool 
     return IBM_OK;
 }
 
+// the guess history's stored vectors, slot-major without the slots'
+// padding (each slot is N doubles in the caller's buffer)
+static ibm_status hist_vec_io(Ctx *c, int field, void *buf, int is_device, size_t bytes, bool to_ctx) {
+    const int L = c->opts.poisson_hist;
+    if (L <= 0) return c->fail(IBM_ERR_ARG, "the Poisson guess history is off (poisson_hist 0)");
+    const size_t nb = sizeof(double) * (size_t)c->N;
+    if (bytes != nb * (size_t)L) return c->fail(IBM_ERR_ARG, "byte count does not match the field size");
+    IBM_TRY(hist_prepare(c));
+    double *base = field == IBM_FIELD_P_HIST_X ? c->hist_x : c->hist_b;
+    for (int i = 0; i < L; ++i) {
+        double *slot = base + (size_t)i * (size_t)c->hist_ld;
+        uint8_t *user = (uint8_t *)buf + (size_t)i * nb;
+        if (is_device) {
+            IBM_CUDA(c, cudaMemcpyAsync(to_ctx ? (void *)slot : (void *)user, to_ctx ? (const void *)user : (const void *)slot,
+                                        nb, cudaMemcpyDeviceToDevice, c->s));
+        } else if (to_ctx) {
+            IBM_TRY(host_copy(c, slot, user, nb, true));
+        } else {
+            IBM_TRY(host_copy(c, user, slot, nb, false));
+        }
+    }
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    return IBM_OK;
+}
+
 // the guess history's control values as doubles: pairs held, next slot,
 // the Gram matrix (poisson_hist^2, row-major)
 static ibm_status hist_ctl_io(Ctx *c, void *buf, int is_device, size_t bytes, bool to_ctx) {
@@ -911,6 +930,7 @@ static ibm_status hist_ctl_io(Ctx *c, void *buf, int is_device, size_t bytes, bo
 extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_device, size_t bytes) {
     if (!c || !dst) return IBM_ERR_ARG;
     if (field == IBM_FIELD_P_HIST_CTL) return hist_ctl_io(c, dst, is_device, bytes, false);
+    if (field == IBM_FIELD_P_HIST_X || field == IBM_FIELD_P_HIST_B) return hist_vec_io(c, field, dst, is_device, bytes, false);
     if (field == IBM_FIELD_STEP) {
         if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
         int64_t v = c->nstep + (c->have_nold ? 0 : 0);
@@ -931,6 +951,8 @@ extern "C" ibm_status ibm_get_field(ibm_ctx *c, int field, void *dst, int is_dev
 extern "C" ibm_status ibm_set_field(ibm_ctx *c, int field, const void *src, int is_device, size_t bytes) {
     if (!c || !src) return IBM_ERR_ARG;
     if (field == IBM_FIELD_P_HIST_CTL) return hist_ctl_io(c, const_cast<void *>(src), is_device, bytes, true);
+    if (field == IBM_FIELD_P_HIST_X || field == IBM_FIELD_P_HIST_B)
+        return hist_vec_io(c, field, const_cast<void *>(src), is_device, bytes, true);
     if (field == IBM_FIELD_STEP) {
         if (bytes != sizeof(int64_t)) return c->fail(IBM_ERR_ARG, "step counter is one int64");
         int64_t v = 0;

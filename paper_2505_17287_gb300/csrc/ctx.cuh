@@ -173,6 +173,7 @@ struct Ctx {
     // Poisson guess history: hist_cap pairs of N doubles (solutions, projected
     // right-hand sides), this step's projected right-hand side, HistCtl
     int hist_cap = 0, hist_len = 0;   // allocated pairs; pair count of the history held
+    int64_t hist_ld = 0;              // slot stride (N rounded up to 32 doubles)
     double *hist_x = nullptr, *hist_b = nullptr, *hist_bp = nullptr;
     void *hist_ctl = nullptr;
     // near-body band for the preconditioner's local relaxation

@@ -3746,22 +3746,23 @@ __global__ void k_hist_solve(HistCtl *H, int L) {
     (void)L;
 }
 
-// phi = sum over the active slots of c_i X_i (phi untouched with no pairs)
-__global__ void k_hist_guess(int64_t n, const HistCtl *__restrict__ H, const double *__restrict__ X,
+// phi = sum over the active slots of c_i X_i (phi untouched with no pairs);
+// slot i starts at X + i ld
+__global__ void k_hist_guess(int64_t n, int64_t ld, const HistCtl *__restrict__ H, const double *__restrict__ X,
                              double *__restrict__ phi) {
     const int m = H->count;
     if (m == 0) return;
     GRID_STRIDE(c, n) {
         double v = 0.0;
-        for (int i = 0; i < m; ++i) v += H->c[i] * X[(int64_t)i * n + c];
+        for (int i = 0; i < m; ++i) v += H->c[i] * X[(int64_t)i * ld + c];
         phi[c] = v;
     }
 }
 
 // the pair of this step into the current slot
-__global__ void k_hist_insert(int64_t n, const HistCtl *__restrict__ H, const double *__restrict__ phi,
+__global__ void k_hist_insert(int64_t n, int64_t ld, const HistCtl *__restrict__ H, const double *__restrict__ phi,
                               const double *__restrict__ bp, double *__restrict__ X, double *__restrict__ B) {
-    const int64_t off = (int64_t)H->slot * n;
+    const int64_t off = (int64_t)H->slot * ld;
     GRID_STRIDE(c, n) {
         X[off + c] = phi[c];
         B[off + c] = bp[c];
@@ -3797,7 +3798,10 @@ ibm_status hist_prepare(Ctx *c) {
     dev_free(c, c->hist_b);
     c->hist_x = c->hist_b = nullptr;
     c->hist_cap = 0;
-    const size_t nb = sizeof(double) * (size_t)c->N * (size_t)L;
+    // each slot starts on a 256-byte boundary: the multi-dot reads its
+    // columns with 16-byte loads
+    c->hist_ld = (c->N + 31) / 32 * 32;
+    const size_t nb = sizeof(double) * (size_t)c->hist_ld * (size_t)L;
     c->hist_x = (double *)dev_alloc(c, nb);
     c->hist_b = (double *)dev_alloc(c, nb);
     if (!c->hist_bp) c->hist_bp = (double *)dev_alloc(c, sizeof(double) * (size_t)c->N);
@@ -3828,12 +3832,14 @@ ibm_status hist_guess(Ctx *c, const double *rhs, double *phi) {
     IBM_TRY(finalize(c, c->part, c->nred, 1, 1.0 / c->fluid_vol, &H->mean));
     KL(-1, k_hist_bp, c->nelem, 256, c->N, c->type, rhs, H, c->hist_bp);
     VPtrs<double> vp{};
-    for (int i = 0; i < L; ++i) vp.p[i] = c->hist_b + (size_t)i * c->N;
+    for (int i = 0; i < L; ++i) vp.p[i] = c->hist_b + (size_t)i * c->hist_ld;
     vp.p[L] = c->hist_bp;
+    for (int i = 0; i <= L; ++i)
+        if (!al16(vp.p[i])) return c->fail(IBM_ERR_STATE, "Poisson history column not 16-byte aligned");
     KL(-1, mdot_fns<double>()[L], mdot_blocks<double>(c), RED_THREADS, c->N, c->hist_bp, vp, c->part);
     IBM_TRY(finalize(c, c->part, mdot_blocks<double>(c), L + 1, 1.0, H->d));
     KL(-1, k_hist_solve, 1, 1, H, L);
-    KL(-1, k_hist_guess, c->nelem, 256, c->N, H, c->hist_x, phi);
+    KL(-1, k_hist_guess, c->nelem, 256, c->N, c->hist_ld, H, c->hist_x, phi);
     IBM_LAUNCHED(c);
     return IBM_OK;
 }
@@ -3843,7 +3849,7 @@ ibm_status hist_store(Ctx *c, const double *phi) {
     const int L = c->opts.poisson_hist;
     if (L <= 0) return IBM_OK;
     HistCtl *H = reinterpret_cast<HistCtl *>(c->hist_ctl);
-    KL(-1, k_hist_insert, c->nelem, 256, c->N, H, phi, c->hist_bp, c->hist_x, c->hist_b);
+    KL(-1, k_hist_insert, c->nelem, 256, c->N, c->hist_ld, H, phi, c->hist_bp, c->hist_x, c->hist_b);
     KL(-1, k_hist_advance, 1, 1, H, L);
     IBM_LAUNCHED(c);
     return IBM_OK;
