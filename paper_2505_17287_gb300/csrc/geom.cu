@@ -330,15 +330,49 @@ __device__ void closest_on_seg(const double *p, const double *a, const double *b
     q[2] = 0.0;
 }
 
-// body intercept: one thread per ghost, elements staged through shared memory
+// per element: a point on it (the centroid) and its bounding box, 9 doubles
+// (centroid, low corner, high corner)
+__global__ void k_elem_boxes(int ndim, int64_t ne, const double *__restrict__ verts, const int32_t *__restrict__ elems,
+                             double *__restrict__ box) {
+    const int nvpe = ndim == 2 ? 2 : 3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, s[3] = {0, 0, 0};
+        for (int k = 0; k < nvpe; ++k) {
+            const int64_t v = elems[nvpe * e + k];
+            for (int d = 0; d < 3; ++d) {
+                const double x = verts[3 * v + d];
+                lo[d] = fmin(lo[d], x);
+                hi[d] = fmax(hi[d], x);
+                s[d] += x;
+            }
+        }
+        for (int d = 0; d < 3; ++d) {
+            box[9 * e + d] = s[d] / nvpe;
+            box[9 * e + 3 + d] = lo[d];
+            box[9 * e + 6 + d] = hi[d];
+        }
+    }
+}
+
+// body intercept: one thread per ghost, elements staged through shared
+// memory. The closest point is the one of the first element (in element
+// order) with the smallest squared distance, as in a search over every
+// element; elements that cannot hold it are skipped: with U the smallest
+// squared distance to an element's centroid (a point of the element, so an
+// upper bound of the minimum) and b the best distance so far, an element
+// whose bounding box lies farther than min(U, b) (1 + 1e-6) is farther than
+// the minimum beyond any rounding of the evaluated distances, and an element
+// the full search would not take.
 constexpr int ELEM_TILE = 128;
 
 __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny, const double *__restrict__ xc,
                                                         const double *__restrict__ yc, const double *__restrict__ zc,
                                                         int64_t ng, const int64_t *__restrict__ gidx,
                                                         const double *__restrict__ verts, int64_t ne,
-                                                        const int32_t *__restrict__ elems, double *__restrict__ bi) {
+                                                        const int32_t *__restrict__ elems,
+                                                        const double *__restrict__ box, double *__restrict__ bi) {
     __shared__ double ev[ELEM_TILE][9];
+    __shared__ double eb[ELEM_TILE][9];
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool active = g < ng;
     double p[3] = {0, 0, 0};
@@ -351,6 +385,22 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
         p[2] = ndim == 2 ? 0.0 : zc[k];
     }
     const int nvpe = ndim == 2 ? 2 : 3;
+    // upper bound from the centroids
+    double U = INFINITY;
+    for (int64_t e0 = 0; e0 < ne; e0 += ELEM_TILE) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < ELEM_TILE * 3; r += blockDim.x) {
+            const int64_t e = e0 + r / 3;
+            if (e < ne) eb[r / 3][r % 3] = box[9 * e + r % 3];
+        }
+        __syncthreads();
+        if (!active) continue;
+        const int cnt = (int)min((int64_t)ELEM_TILE, ne - e0);
+        for (int r = 0; r < cnt; ++r) {
+            const double d0 = eb[r][0] - p[0], d1 = eb[r][1] - p[1], d2 = eb[r][2] - p[2];
+            U = fmin(U, d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    }
     double best = INFINITY, q[3] = {0, 0, 0};
     for (int64_t e0 = 0; e0 < ne; e0 += ELEM_TILE) {
         __syncthreads();
@@ -364,10 +414,20 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
                 ev[r / nvpe][3 * corner + 2] = verts[3 * v + 2];
             }
         }
+        for (int r = threadIdx.x; r < ELEM_TILE * 6; r += blockDim.x) {
+            const int64_t e = e0 + r / 6;
+            if (e < ne) eb[r / 6][3 + r % 6] = box[9 * e + 3 + r % 6];
+        }
         __syncthreads();
         if (!active) continue;
         const int cnt = (int)min((int64_t)ELEM_TILE, ne - e0);
         for (int r = 0; r < cnt; ++r) {
+            double ad = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double o = fmax(fmax(eb[r][3 + d] - p[d], p[d] - eb[r][6 + d]), 0.0);
+                ad += o * o;
+            }
+            if (ad > fmin(U, best) * (1.0 + 1e-6)) continue;
             double qq[3];
             if (ndim == 2) closest_on_seg(p, ev[r], ev[r] + 3, qq);
             else closest_on_tri(p, ev[r], ev[r] + 3, ev[r] + 6, qq);
@@ -381,6 +441,15 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
         bi[3 * g + 1] = q[1];
         bi[3 * g + 2] = q[2];
     }
+}
+
+// element boxes of the current vertex positions (scratch owned by the caller)
+static ibm_status elem_boxes(Ctx *c, double **box) {
+    *box = (double *)dev_alloc(c, sizeof(double) * 9 * (size_t)(c->ne > 0 ? c->ne : 1));
+    if (!*box) return c->fail(IBM_ERR_OOM, "element box allocation failed");
+    ++c->nlaunch, k_elem_boxes<<<(unsigned)((c->ne + 255) / 256), 256, 0, c->s>>>(c->ndim, c->ne, c->d_verts, c->d_elems, *box);
+    IBM_LAUNCHED(c);
+    return IBM_OK;
 }
 
 // LU with partial pivoting; 1 when a pivot is below 1e-12 max|M|
@@ -716,13 +785,17 @@ ibm_status geom_body_velocity(Ctx *c, int64_t n, const double *pts, double *out)
 ibm_status geom_fresh_tables(Ctx *c, int64_t nf, const int64_t *fidx, double *bi, uint8_t *kind, int64_t *sidx,
                              double *w, double *wb) {
     if (nf <= 0) return IBM_OK;
+    double *box = nullptr;
+    IBM_TRY(elem_boxes(c, &box));
     ++c->nlaunch, k_body_intercept<<<(unsigned)((nf + 127) / 128), 128, 0, c->s>>>(c->ndim, c->nx, c->ny, c->xc, c->yc, c->zc, nf,
-                                                                                  fidx, c->d_verts, c->ne, c->d_elems, bi);
+                                                                                  fidx, c->d_verts, c->ne, c->d_elems, box, bi);
     IBM_LAUNCHED(c);
     ++c->nlaunch, k_fresh_tables<<<(unsigned)((nf + 63) / 64), 64, 0, c->s>>>(c->ndim, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
                                                                              c->dx, c->dy, c->dz, c->type, nf, fidx, bi,
                                                                              kind, sidx, w, wb);
     IBM_LAUNCHED(c);
+    IBM_CUDA(c, cudaStreamSynchronize(c->s));
+    dev_free(c, box);
     return IBM_OK;
 }
 
@@ -797,9 +870,13 @@ ibm_status geom_classify(Ctx *c) {
         ++c->nlaunch, k_write_ghosts<<<(unsigned)nb, CHUNK, 0, c->s>>>(c->N, c->type, off, c->gidx);
         IBM_LAUNCHED(c);
         const unsigned gb = (unsigned)((c->ng + 127) / 128);
+        double *box = nullptr;
+        IBM_TRY(elem_boxes(c, &box));
         ++c->nlaunch, k_body_intercept<<<gb, 128, 0, c->s>>>(nd, c->nx, c->ny, c->xc, c->yc, c->zc, c->ng, c->gidx, c->d_verts,
-                                               c->ne, c->d_elems, c->bi);
+                                               c->ne, c->d_elems, box, c->bi);
         IBM_LAUNCHED(c);
+        IBM_CUDA(c, cudaStreamSynchronize(c->s));
+        dev_free(c, box);
         TabOut o{c->bi, c->nrm, c->ipt, c->dist, c->wv, c->wp, c->bv, c->bp, c->base, c->sidx, c->kind, c->cmask};
         ++c->nlaunch, k_ghost_tables<<<(unsigned)((c->ng + 63) / 64), 64, 0, c->s>>>(nd, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
                                                                        c->dx, c->dy, c->dz, c->type, c->ng, c->gidx, o);
