@@ -354,16 +354,19 @@ __global__ void k_elem_boxes(int ndim, int64_t ne, const double *__restrict__ ve
     }
 }
 
-// body intercept: one thread per ghost, elements staged through shared
-// memory. The closest point is the one of the first element (in element
-// order) with the smallest squared distance, as in a search over every
-// element; elements that cannot hold it are skipped: with U the smallest
-// squared distance to an element's centroid (a point of the element, so an
-// upper bound of the minimum) and b the best distance so far, an element
-// whose bounding box lies farther than min(U, b) (1 + 1e-6) is farther than
-// the minimum beyond any rounding of the evaluated distances, and an element
-// the full search would not take.
+// body intercept: one warp per ghost (four per block), elements staged
+// through shared memory and shared out over the lanes. The closest point is
+// the one of the first element (in element order) with the smallest squared
+// distance, as in a search over every element: each lane keeps the first
+// minimum of its elements (visited in element order) and the warp takes the
+// smallest distance, the lowest element on ties. Elements that cannot hold
+// the minimum are skipped: with U the smallest squared distance to an
+// element's centroid (a point of the element, so an upper bound of the
+// minimum) and b the lane's best so far, an element whose bounding box lies
+// farther than min(U, b) (1 + 1e-6) is farther than the minimum beyond any
+// rounding of the evaluated distances, and one the full search would not take.
 constexpr int ELEM_TILE = 128;
+constexpr int BI_WARPS = 4;
 
 __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny, const double *__restrict__ xc,
                                                         const double *__restrict__ yc, const double *__restrict__ zc,
@@ -373,7 +376,8 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
                                                         const double *__restrict__ box, double *__restrict__ bi) {
     __shared__ double ev[ELEM_TILE][9];
     __shared__ double eb[ELEM_TILE][9];
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = blockIdx.x * (int64_t)BI_WARPS + (threadIdx.x >> 5);
     const bool active = g < ng;
     double p[3] = {0, 0, 0};
     if (active) {
@@ -396,12 +400,14 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
         __syncthreads();
         if (!active) continue;
         const int cnt = (int)min((int64_t)ELEM_TILE, ne - e0);
-        for (int r = 0; r < cnt; ++r) {
+        for (int r = lane; r < cnt; r += 32) {
             const double d0 = eb[r][0] - p[0], d1 = eb[r][1] - p[1], d2 = eb[r][2] - p[2];
             U = fmin(U, d0 * d0 + d1 * d1 + d2 * d2);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) U = fmin(U, __shfl_xor_sync(0xffffffffu, U, o));
     double best = INFINITY, q[3] = {0, 0, 0};
+    int64_t bidx = ne;
     for (int64_t e0 = 0; e0 < ne; e0 += ELEM_TILE) {
         __syncthreads();
         for (int r = threadIdx.x; r < ELEM_TILE * nvpe; r += blockDim.x) {
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
         __syncthreads();
         if (!active) continue;
         const int cnt = (int)min((int64_t)ELEM_TILE, ne - e0);
-        for (int r = 0; r < cnt; ++r) {
+        for (int r = lane; r < cnt; r += 32) {
             double ad = 0.0;
             for (int d = 0; d < 3; ++d) {
                 const double o = fmax(fmax(eb[r][3 + d] - p[d], p[d] - eb[r][6 + d]), 0.0);
@@ -433,10 +439,27 @@ __global__ void __launch_bounds__(128) k_body_intercept(int ndim, int nx, int ny
             else closest_on_tri(p, ev[r], ev[r] + 3, ev[r] + 6, qq);
             double dv[3] = {qq[0] - p[0], qq[1] - p[1], qq[2] - p[2]};
             const double dd = dot3(dv, dv);
-            if (dd < best) { best = dd; q[0] = qq[0]; q[1] = qq[1]; q[2] = qq[2]; }
+            if (dd < best) {
+                best = dd;
+                bidx = e0 + r;
+                q[0] = qq[0]; q[1] = qq[1]; q[2] = qq[2];
+            }
         }
     }
-    if (active) {
+    // the warp's first minimum
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bidx, o);
+        const double o0 = __shfl_xor_sync(0xffffffffu, q[0], o);
+        const double o1 = __shfl_xor_sync(0xffffffffu, q[1], o);
+        const double o2 = __shfl_xor_sync(0xffffffffu, q[2], o);
+        if (ob < best || (ob == best && oi < bidx)) {
+            best = ob;
+            bidx = oi;
+            q[0] = o0; q[1] = o1; q[2] = o2;
+        }
+    }
+    if (active && lane == 0) {
         bi[3 * g + 0] = q[0];
         bi[3 * g + 1] = q[1];
         bi[3 * g + 2] = q[2];
@@ -787,7 +810,7 @@ ibm_status geom_fresh_tables(Ctx *c, int64_t nf, const int64_t *fidx, double *bi
     if (nf <= 0) return IBM_OK;
     double *box = nullptr;
     IBM_TRY(elem_boxes(c, &box));
-    ++c->nlaunch, k_body_intercept<<<(unsigned)((nf + 127) / 128), 128, 0, c->s>>>(c->ndim, c->nx, c->ny, c->xc, c->yc, c->zc, nf,
+    ++c->nlaunch, k_body_intercept<<<(unsigned)((nf + BI_WARPS - 1) / BI_WARPS), 128, 0, c->s>>>(c->ndim, c->nx, c->ny, c->xc, c->yc, c->zc, nf,
                                                                                   fidx, c->d_verts, c->ne, c->d_elems, box, bi);
     IBM_LAUNCHED(c);
     ++c->nlaunch, k_fresh_tables<<<(unsigned)((nf + 63) / 64), 64, 0, c->s>>>(c->ndim, c->nx, c->ny, c->nz, c->xc, c->yc, c->zc,
@@ -869,7 +892,7 @@ ibm_status geom_classify(Ctx *c) {
     if (c->ng > 0) {
         ++c->nlaunch, k_write_ghosts<<<(unsigned)nb, CHUNK, 0, c->s>>>(c->N, c->type, off, c->gidx);
         IBM_LAUNCHED(c);
-        const unsigned gb = (unsigned)((c->ng + 127) / 128);
+        const unsigned gb = (unsigned)((c->ng + BI_WARPS - 1) / BI_WARPS);
         double *box = nullptr;
         IBM_TRY(elem_boxes(c, &box));
         ++c->nlaunch, k_body_intercept<<<gb, 128, 0, c->s>>>(nd, c->nx, c->ny, c->xc, c->yc, c->zc, c->ng, c->gidx, c->d_verts,
