@@ -90,6 +90,9 @@ def parse():
                     help="wing grid of the Poisson solver comparison ('' to skip)")
     ap.add_argument("--ellipsoids", type=int, default=0,
                     help="steps of the 208M-cell ellipsoid array to time per precision (0: skip)")
+    ap.add_argument("--moving", default="384,256,256",
+                    help="wing grid of the moving-body leg: the wing pitching about its span axis, "
+                         "moved and reclassified every step ('' to skip)")
     ap.add_argument("--ensemble", type=int, default=64,
                     help="cases of the seeded 2D ensemble to run, 50 steps each (0: skip)")
     ap.add_argument("--ref-size", default="128,96,96",
@@ -445,6 +448,61 @@ def ensemble_leg(ncases):
                         "dt = 0.2 h, 50 steps, Poisson rtol 1e-10"}
 
 
+def moving_leg(size, steps, warmup, omega=2.0):
+    """The wing pitching about its span axis (y) through its centroid at
+    omega rad/s, mixed precision: every step is ibm_move_body (rigid
+    rotation by omega dt, reclassification, fresh cells, ghost rows with the
+    body velocity) followed by ibm_step(1). Mcell-steps/s of the pair, and the
+    time of each part."""
+    import numpy as np
+    import torch
+    from paper_2505_17287_gb300 import ibm
+    case = wing_case(size)
+    s = ibm.Solver(case, precision=ibm.IBM_MIXED)
+    s.set_opts(precision=ibm.IBM_MIXED)
+    v0, e = case.verts, case.elems
+    s.set_body(v0, e)
+    s.classify()
+    c0 = v0.mean(0)
+    n = 0
+
+    def move_step():
+        nonlocal n
+        n += 1
+        a = omega * case.dt * n
+        R = np.array([[np.cos(a), 0.0, np.sin(a)], [0.0, 1.0, 0.0], [-np.sin(a), 0.0, np.cos(a)]])
+        info = s.move_body((v0 - c0) @ R.T + c0, (0.0, 0.0, 0.0), (0.0, omega, 0.0), tuple(c0))
+        t1 = torch.cuda.Event(enable_timing=True)
+        t1.record()
+        return info, t1, s.step(1)
+
+    for _ in range(warmup):
+        move_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    move_ms, outs = 0.0, []
+    e0.record()
+    for _ in range(steps):
+        m0 = torch.cuda.Event(enable_timing=True)
+        m0.record()
+        info, m1, r = move_step()
+        outs.append(r)
+        torch.cuda.synchronize()
+        move_ms += m0.elapsed_time(m1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"grid": size.replace(",", "x"), "cells": case.ncells, "triangles": int(e.shape[0]),
+           "value": case.ncells * steps / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps,
+           "move_ms_per_step": move_ms / steps, "poisson_outer_per_step": sum(r["poisson_outer"] for r in outs) / steps,
+           "ok": all(r["status"] == ibm.IBM_OK for r in outs), "n_ghost": info["n_ghost"],
+           "motion": f"pitching about the span axis at {omega} rad/s, dt {case.dt}",
+           "precision": "mixed"}
+    s.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def wing_leg(size, steps, warmup):
     """Extra leg: the wing on another grid, FP64 and mixed from the same
     saved state (Mcell-steps/s and the Poisson speed-up)."""
@@ -676,6 +734,9 @@ def main():
         result["cpu_baseline"] = cpu_base
     if rank == 0 and args.wing25m:
         result["wing_" + args.wing25m.replace(",", "x")] = wing_leg(args.wing25m, args.steps, args.warmup)
+    if rank == 0 and args.moving:
+        torch.cuda.empty_cache()
+        result["moving_" + args.moving.replace(",", "x")] = moving_leg(args.moving, args.steps, args.warmup)
     if rank == 0 and args.ellipsoids > 0:
         result["ellipsoid_array"] = ellipsoid_leg(args.ellipsoids)
     if rank == 0 and args.compare:
