@@ -191,6 +191,9 @@ typedef struct {
                            faster (2D 256x128 cylinder step 2.28 ms without the
                            tail, 2.42-2.58 ms with it). Needs mg_interp 1 and
                            three levels or more */
+    int nu_coarse;      /* red-black sweeps before and after the coarse-grid correction on
+                           the multigrid levels below the finest, 1..8; 0 = nu1 and nu2
+                           there too */
 } ibm_solver_opts;
 
 typedef struct {
@@ -254,12 +257,13 @@ enum {
                                   stored right-hand sides: 2 + poisson_hist^2 doubles */
 };
 
-/* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 = nu2 = 2,
+/* Defaults: rtol 1e-10, max_outer 400, inner_iters 1, nu1 2, nu2 1 (nu_coarse 3 on the
+   levels below the finest),
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
    band_sweeps 6, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
-   helm_check_first 6, helm_omega 1, fine_split 1, band_width 3, poisson_hist 8, tail_cells 0. */
+   helm_check_first 6, helm_omega 1, fine_split 1, band_width 3, poisson_hist 8, tail_cells 0, nu_coarse 3. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);
 
 /* Create a context for one grid (Section 2.1: non-uniform Cartesian grid).

@@ -103,7 +103,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->restart = 16;
     o->inner_iters = 1;
     o->nu1 = 2;
-    o->nu2 = 2;
+    o->nu2 = 1;
     o->coarse_sweeps = 32;
     o->helm_rtol = 1e-12;
     o->helm_maxit = 500;
@@ -129,6 +129,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->band_width = 3;
     o->poisson_hist = 8;
     o->tail_cells = 0;
+    o->nu_coarse = 3;
     return IBM_OK;
 }
 
@@ -170,6 +171,7 @@ static bool opts_ok(const ibm_solver_opts *o, std::string &why) {
     if (o->band_width < 1 || o->band_width > 4) { why = "band_width must be in [1, 4]"; return false; }
     if (o->tail_cells < 0) { why = "tail_cells must be >= 0"; return false; }
     if (o->poisson_hist < 0 || o->poisson_hist > 16) { why = "poisson_hist must be in [0, 16]"; return false; }
+    if (o->nu_coarse < 0 || o->nu_coarse > 8) { why = "nu_coarse must be in [0, 8]"; return false; }
     if (o->inner_iters > 1 && o->smooth_omega != 1.0) { why = "smooth_omega must be 1 when inner_iters > 1"; return false; }
     return true;
 }

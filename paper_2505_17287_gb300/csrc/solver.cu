@@ -2482,7 +2482,9 @@ template <typename T>
 static ibm_status launch_tail(Ctx *c, MGHier<T> &H, int l0, int ncta) {
     const int L = (int)H.lv.size();
     const TailLv<T> *A = reinterpret_cast<const TailLv<T> *>(H.tail);
-    const int nu1 = c->opts.nu1, nu2 = c->opts.nu2, cs = c->opts.coarse_sweeps;
+    // (every tail level lies below the finest)
+    const int nu1 = c->opts.nu_coarse > 0 ? c->opts.nu_coarse : c->opts.nu1;
+    const int nu2 = c->opts.nu_coarse > 0 ? c->opts.nu_coarse : c->opts.nu2, cs = c->opts.coarse_sweeps;
     const double w = c->opts.smooth_omega;
     auto kern = w != 1.0 ? k_vtail<T, true> : k_vtail<T, false>;
     kt_begin(c, K_TAIL);
@@ -2513,6 +2515,9 @@ template <typename T>
 static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
     const int L = (int)H.lv.size();
     const int nu1 = c->opts.nu1, nu2 = c->opts.nu2, cs = c->opts.coarse_sweeps;
+    // sweeps on the levels below the finest
+    const int nuc1 = c->opts.nu_coarse > 0 ? c->opts.nu_coarse : nu1;
+    const int nuc2 = c->opts.nu_coarse > 0 ? c->opts.nu_coarse : nu2;
     const int bx = c->opts.tile_x;
     if (L == 1) {
         KL(-1, k_coarse_solve<T>, 1, COARSE_MAX, H.lv[0], f0, x0, cs);
@@ -2541,7 +2546,8 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
             }
         }
         if (!(l == 0 && sp)) {
-            for (int s = 0; s < nu1; ++s) {
+            const int n1 = l == 0 ? nu1 : nuc1;
+            for (int s = 0; s < n1; ++s) {
                 IBM_TRY(rbgs(c, H, l, f, x, 0, s == 0 ? (l == 0 ? 2 : 1) : 0));
                 IBM_TRY(rbgs(c, H, l, f, x, 1));
             }
@@ -2629,7 +2635,7 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
                 continue;
             }
         }
-        for (int s = 0; s < nu2; ++s) {
+        for (int s = 0; s < (l == 0 ? nu2 : nuc2); ++s) {
             IBM_TRY(rbgs(c, H, l, f, x, 1));
             IBM_TRY(rbgs(c, H, l, f, x, 0));
         }
@@ -2644,9 +2650,9 @@ static ibm_status vcycle(Ctx *c, MGHier<T> &H, const T *f0, T *x0) {
 template <typename T>
 static ibm_status vcycle_graph(Ctx *c, MGHier<T> &H, T *out) {
     const ibm_solver_opts &o = c->opts;
-    const uint64_t key = (((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
+    const uint64_t key = ((((((c->mg_gen * 64 + (uint64_t)o.nu1) * 64 + (uint64_t)o.nu2) * 4096 +
                            (uint64_t)o.coarse_sweeps) * 1024 + (uint64_t)o.tile_x) * 4 + (uint64_t)o.mg_interp * 2 +
-                         (uint64_t)o.fine_split) * 1000003 + (uint64_t)o.tail_cells + 1;
+                         (uint64_t)o.fine_split) * 1000003 + (uint64_t)o.tail_cells) * 16 + (uint64_t)o.nu_coarse + 1;
     auto drop_all = [&]() -> ibm_status {
         IBM_CUDA(c, cudaStreamSynchronize(c->s));
         for (int i = 0; i < MGHier<T>::NVG; ++i) {

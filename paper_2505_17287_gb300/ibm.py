@@ -51,7 +51,8 @@ class ibm_solver_opts(Structure):
                 ("precond", c_int), ("srj_sweeps", c_int), ("srj_lmin", c_double), ("helm_solver", c_int),
                 ("smooth_omega", c_double), ("reorth_eta", c_double),
                 ("helm_check_first", c_int), ("helm_omega", c_double), ("fine_split", c_int),
-                ("band_width", c_int), ("poisson_hist", c_int), ("tail_cells", c_int)]
+                ("band_width", c_int), ("poisson_hist", c_int), ("tail_cells", c_int),
+                ("nu_coarse", c_int)]
 
 
 class ibm_table_info(Structure):

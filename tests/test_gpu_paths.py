@@ -246,7 +246,7 @@ def _mixed_fields(case, nsteps, **opts):
 
 
 @pytest.mark.parametrize("opts", [{}, {"smooth_omega": 1.15}, {"nu1": 1, "nu2": 3}, {"graph": 0},
-                                  {"inner_iters": 2}])
+                                  {"inner_iters": 2, "nu1": 2, "nu2": 2}])
 @pytest.mark.parametrize("which", ["wing", "cylinder"])
 def test_split_level0_equals_cell_ordered(which, opts):
     """The finest FP32 multigrid level in colour-split storage (fine_split 1)

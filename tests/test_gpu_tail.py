@@ -35,7 +35,7 @@ def _cases():
 
 CASES = [(p, w, o, ALL) for p in (ibm.IBM_FP64, ibm.IBM_MIXED) for w in ("cylinder", "wing")
          for o in ({}, {"smooth_omega": 1.15})]
-CASES += [(ibm.IBM_MIXED, "wing", o, 2048) for o in ({"nu1": 1, "nu2": 3}, {"graph": 0}, {"inner_iters": 2})]
+CASES += [(ibm.IBM_MIXED, "wing", o, 2048) for o in ({"nu1": 1, "nu2": 3}, {"graph": 0}, {"inner_iters": 2, "nu1": 2, "nu2": 2})]
 
 
 @pytest.mark.parametrize("precision,which,opts,tail", CASES)
