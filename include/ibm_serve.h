@@ -124,9 +124,10 @@ ibm_status ibm_server_destroy(ibm_server *srv);
 
 /* Autotuner (no counterpart in the paper): builds the case (desc, bodies,
    on desc's stream and allocator), then for each of the ncand option sets
-   restores the same impulsive-start state, takes one untimed step (which
-   also captures any CUDA graph the options ask for), restores the state
-   again and times `steps` fractional steps with CUDA events on the stream.
+   restores the same impulsive-start state with an empty Poisson guess
+   history, takes one untimed step (which also captures any CUDA graph the
+   options ask for), restores the state again and times `steps` fractional
+   steps with CUDA events on the stream.
    ms_per_step[i] (host, ncand values) receives candidate i's device time
    per step, or a negative value if it failed (IBM_ERR_ARG options,
    non-convergence); *best the index of the fastest. IBM_ERR_ARG for bad

@@ -501,20 +501,28 @@ extern "C" ibm_status ibm_tune(const ibm_grid_desc *desc, int nbodies, const dou
             st = IBM_ERR_CUDA;
             break;
         }
-        auto restore = [&]() {
+        // every candidate starts from the same state with an empty Poisson
+        // guess history (pairs from an earlier candidate's solves of the same
+        // steps would make the later ones look faster)
+        auto restore = [&](int hist) {
             ibm_status r = IBM_OK;
             for (size_t f = 0; f < fields.size() && r == IBM_OK; ++f)
                 r = ibm_set_field(ctx, fields[f].first, saved[f].data(), 0, sizeof(double) * fields[f].second);
             const int64_t zero = 0;
             if (r == IBM_OK) r = ibm_set_field(ctx, IBM_FIELD_STEP, &zero, 0, sizeof(int64_t));
+            if (r == IBM_OK && hist > 0) {
+                const std::vector<double> empty((size_t)(2 + hist * hist), 0.0);
+                r = ibm_set_field(ctx, IBM_FIELD_P_HIST_CTL, empty.data(), 0, sizeof(double) * empty.size());
+            }
             return r;
         };
         int bi = -1;
         for (int i = 0; i < ncand; ++i) {
             ms_per_step[i] = -1.0;
             if (ibm_set_opts(ctx, &cand[i]) != IBM_OK) continue;
-            if (restore() != IBM_OK || ibm_step(ctx, 1, nullptr) != IBM_OK) continue;
-            if (restore() != IBM_OK) continue;
+            const int hist = cand[i].poisson_hist;
+            if (restore(hist) != IBM_OK || ibm_step(ctx, 1, nullptr) != IBM_OK) continue;
+            if (restore(hist) != IBM_OK) continue;
             if (cudaEventRecord(e0, s) != cudaSuccess) break;
             const ibm_status r = ibm_step(ctx, steps, nullptr);
             if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;

@@ -11,8 +11,9 @@ run (the request-loop path): the cases go through include/ibm_serve.h,
 `slots` at a time, each slot a host worker thread driving its case.
 
 Options are picked per size class (cell count rounded to a power of two) by
-the library's autotuner, which times candidate multigrid tile widths and
-smoother sweep counts on the first case of each class.
+the library's autotuner, which times candidate multigrid tile widths,
+smoother sweep counts (finest and coarse levels) and relaxation factors on the
+first case of each class.
 """
 from __future__ import annotations
 
@@ -28,19 +29,24 @@ def size_class(case) -> int:
     return int(round(math.log2(case.ncells)))
 
 
-def candidates(precision=ibm.IBM_MIXED, tiles=(32, 64, 128, 256), nus=(1, 2), omegas=(1.0, 1.1)):
+def candidates(precision=ibm.IBM_MIXED, tiles=(32, 64, 128, 256), nus=(1, 2), omegas=(1.0, 1.1),
+               nu_coarses=(0, 3)):
     """Option sets the autotuner chooses from: multigrid row-tile width x
     smoother sweeps per V-cycle half x smoother relaxation factor (over-
-    relaxation helps uniform grids, not strongly stretched ones), all with the
-    V-cycle graph; the last one is the library default without the graph
-    (the reference point)."""
+    relaxation helps uniform grids, not strongly stretched ones) x sweeps on
+    the levels below the finest (0: the same as the finest; more pay on large
+    3D grids, fewer launches on small 2D ones), all with the V-cycle graph;
+    the last one is the library default without the graph (the reference
+    point)."""
     out = []
     for t in tiles:
         for nu in nus:
             for om in omegas:
-                o = ibm.ibm_default_opts()
-                o.precision, o.tile_x, o.nu1, o.nu2, o.graph, o.smooth_omega = precision, t, nu, nu, 1, om
-                out.append(o)
+                for nc in nu_coarses:
+                    o = ibm.ibm_default_opts()
+                    o.precision, o.tile_x, o.nu1, o.nu2, o.graph, o.smooth_omega = precision, t, nu, nu, 1, om
+                    o.nu_coarse = nc
+                    out.append(o)
     o = ibm.ibm_default_opts()
     o.precision, o.graph = precision, 0
     out.append(o)
@@ -61,7 +67,8 @@ def tune(cases, precision=ibm.IBM_MIXED, steps=3):
 
 
 def describe(o):
-    return {"tile_x": o.tile_x, "nu": o.nu1, "omega": o.smooth_omega, "graph": o.graph}
+    return {"tile_x": o.tile_x, "nu": o.nu1, "nu2": o.nu2, "nu_coarse": o.nu_coarse, "omega": o.smooth_omega,
+            "graph": o.graph}
 
 
 def run(cases, slots=12, precision=ibm.IBM_MIXED, tuned=None):
