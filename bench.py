@@ -90,6 +90,8 @@ def parse():
                     help="wing grid of the Poisson solver comparison ('' to skip)")
     ap.add_argument("--ellipsoids", type=int, default=0,
                     help="steps of the 208M-cell ellipsoid array to time per precision (0: skip)")
+    ap.add_argument("--no-cylinder", action="store_true",
+                    help="skip the 2D cylinder leg (256x128, 20 steps: the workload of the CPU baseline)")
     ap.add_argument("--moving", default="384,256,256",
                     help="wing grid of the moving-body leg: the wing pitching about its span axis, "
                          "moved and reclassified every step ('' to skip)")
@@ -448,6 +450,39 @@ def ensemble_leg(ncases):
                         "dt = 0.2 h, 50 steps, Poisson rtol 1e-10"}
 
 
+def cylinder_leg():
+    """The 2D cylinder workload as configured (256x128, Re 100, dt 0.005, 20
+    steps from the impulsive start, the CPU baseline's sample), in FP64 and
+    mixed precision, each step one captured graph with device-side loop
+    control (opts graph=2) on a stream of its own; the 20 steps are timed
+    after an untimed run of the same 20 steps (graph capture and allocation)."""
+    import torch
+    from paper_2505_17287_gb300 import ibm, synth
+    c = synth.cylinder_case()
+    out = {"grid": "256x128", "cells": c.ncells, "steps": c.nsteps}
+    for name, prec in (("fp64", ibm.IBM_FP64), ("mixed", ibm.IBM_MIXED)):
+        s = ibm.Solver(c, precision=prec, stream=torch.cuda.Stream())
+        s.set_opts(precision=prec, graph=2)
+        s.set_body(c.verts, c.elems)
+        s.classify()
+        init = s.get_state()
+        s.step_prepare()
+        s.step_async(c.nsteps)
+        s.step_wait()
+        s.set_state(init)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step_async(c.nsteps)
+        r = s.step_wait()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[name] = {"value": c.ncells * c.nsteps / el / 1e6, "unit": UNIT, "ms_per_step": 1e3 * el / c.nsteps,
+                     "poisson_outer_per_step": r["poisson_outer"] / max(1, r["steps"]),
+                     "ok": r["status"] == ibm.IBM_OK}
+        s.close()
+    return out
+
+
 def moving_leg(size, steps, warmup, omega=2.0):
     """The wing pitching about its span axis (y) through its centroid at
     omega rad/s, mixed precision: every step is ibm_move_body (rigid
@@ -734,6 +769,8 @@ def main():
         result["cpu_baseline"] = cpu_base
     if rank == 0 and args.wing25m:
         result["wing_" + args.wing25m.replace(",", "x")] = wing_leg(args.wing25m, args.steps, args.warmup)
+    if rank == 0 and not args.no_cylinder:
+        result["cylinder_256x128"] = cylinder_leg()
     if rank == 0 and args.moving:
         torch.cuda.empty_cache()
         result["moving_" + args.moving.replace(",", "x")] = moving_leg(args.moving, args.steps, args.warmup)
