@@ -3715,7 +3715,7 @@ __global__ void k_hist_bp(int64_t n, const uint8_t *__restrict__ type, const dou
 
 // c over the m active slots (0 elsewhere, and everywhere if the factorisation
 // meets a non-positive pivot)
-__global__ void k_hist_solve(HistCtl *H, int L) {
+__global__ void k_hist_solve(HistCtl *H) {
     const int m = H->count;
     for (int i = 0; i < HIST_MAX; ++i) H->c[i] = 0.0;
     if (m == 0) return;
@@ -3749,7 +3749,6 @@ __global__ void k_hist_solve(HistCtl *H, int L) {
         for (int q = i + 1; q < m; ++q) v -= a[i * HIST_MAX + q] * H->c[q];
         H->c[i] = v / a[i * HIST_MAX + i];
     }
-    (void)L;
 }
 
 // phi = sum over the active slots of c_i X_i (phi untouched with no pairs);
@@ -3844,7 +3843,7 @@ ibm_status hist_guess(Ctx *c, const double *rhs, double *phi) {
         if (!al16(vp.p[i])) return c->fail(IBM_ERR_STATE, "Poisson history column not 16-byte aligned");
     KL(-1, mdot_fns<double>()[L], mdot_blocks<double>(c), RED_THREADS, c->N, c->hist_bp, vp, c->part);
     IBM_TRY(finalize(c, c->part, mdot_blocks<double>(c), L + 1, 1.0, H->d));
-    KL(-1, k_hist_solve, 1, 1, H, L);
+    KL(-1, k_hist_solve, 1, 1, H);
     KL(-1, k_hist_guess, c->nelem, 256, c->N, c->hist_ld, H, c->hist_x, phi);
     IBM_LAUNCHED(c);
     return IBM_OK;
