@@ -261,7 +261,7 @@ enum {
    levels below the finest),
    coarse_sweeps 32, helm_rtol 1e-12, helm_maxit 500, ghost_tol 1e-15,
    ghost_maxit 100, precision IBM_FP64, outer IBM_OUTER_FGMRES, restart 16,
-   band_sweeps 6, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
+   band_sweeps 8, band_omega 0.85, mixed_inner_rtol 1e-4, mg_interp 1,
    tile_x 128, graph 1, precond 0, srj_sweeps 16, srj_lmin 0, helm_solver 0, smooth_omega 1, reorth_eta 0.3,
    helm_check_first 6, helm_omega 1, fine_split 1, band_width 3, poisson_hist 8, tail_cells 0, nu_coarse 3. */
 ibm_status ibm_default_opts(ibm_solver_opts *opts);

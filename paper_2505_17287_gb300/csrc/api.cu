@@ -111,7 +111,7 @@ extern "C" ibm_status ibm_default_opts(ibm_solver_opts *o) {
     o->ghost_maxit = 100;
     o->precision = IBM_FP64;
     o->outer = IBM_OUTER_FGMRES;
-    o->band_sweeps = 6;
+    o->band_sweeps = 8;
     o->band_omega = 0.85;
     o->mixed_inner_rtol = 1e-4;
     o->mg_interp = 1;

@@ -92,7 +92,7 @@ def test_create_rejects_bad_descriptor_without_gpu(lib):
     assert o.rtol == 1e-10 and o.restart == 16 and o.outer == ibm.IBM_OUTER_FGMRES
     assert o.reorth_eta == 0.3 and o.precond == 0 and o.graph == 1 and o.helm_check_first == 6 and o.helm_omega == 1.0
     assert o.fine_split == 1 and o.band_width == 3 and o.tail_cells == 0 and o.poisson_hist == 8 and o.nu_coarse == 3 and o.nu1 == 2 and o.nu2 == 1
-    assert o.band_sweeps == 6 and o.band_omega == 0.85
+    assert o.band_sweeps == 8 and o.band_omega == 0.85
 
 
 def test_server_argument_checks_without_gpu(lib):
